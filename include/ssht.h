@@ -1,0 +1,162 @@
+/*
+ * ssht.h -- C ABI of libssht, a GB300 (sm_103a) implementation of the exact spin
+ * spherical harmonic transform of J. D. McEwen, "Fast, exact (but unstable) spin
+ * spherical harmonic transforms" (arXiv:0807.4494).
+ *
+ * The transform maps spin-s coefficients sf_lm, 0 <= l < L, |m| <= l, to samples of
+ *   f(theta, phi) = sum_{l,m} sf_lm sY_lm(theta, phi)                (eqn ssht_inv, Sec. 2.3)
+ * on the paper's equiangular grid (eqns nodes_theta / nodes_phi, Sec. 3.4.1) and back.
+ * Through eqn wigner_sum_reln (Sec. 2.2) the harmonics become Fourier series on the
+ * torus whose coefficients are eqn fourier_coeff (Sec. 3.1):
+ *   F_{m m'} = (-1)^s i^{-(m+s)} sum_l sqrt((2l+1)/4pi) Delta^l_{m'm} Delta^l_{m',-s} sf_lm,
+ * with Delta^l_{m'm} = d^l_{m'm}(pi/2) obtained by the Risbo recursion (Sec. 2.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - L is the EXCLUSIVE band-limit (coefficients with l < L).  The paper's inclusive
+ *    band-limit is L-1; its torus has N = 2L-1 samples per axis.
+ *  - Coefficients: flm[b][l*l + l + m], complex interleaved (re, im), batch outermost,
+ *    b = 0 .. batch-1.  Entries with l < |s| do not exist: inputs there are ignored,
+ *    outputs there are written as 0.
+ *  - Sphere samples: f[b][t][p], complex interleaved, t = 0..L-1 (theta_t = pi(2t+1)/(2L-1),
+ *    the last ring is theta = pi), p = 0..2L-2 (phi_p = pi(2p+1)/(2L-1)).
+ *  - Element type: plans of precision SSHT_FP64 take and return double pairs
+ *    (16 bytes per complex value); every other precision takes and returns float pairs
+ *    (8 bytes per complex value).
+ *  - Data pointers may be device memory or host memory (pinned or pageable); host
+ *    buffers are staged through plan-owned device memory.  The caller owns all data
+ *    buffers.  Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) when all pointers are device pointers; with host pointers a call
+ *    returns once its host output has been written.
+ *  - Errors: every entry point returns 0 on success or a negative SSHT_E* code and
+ *    records a message retrievable with ssht_last_error() (per host thread).  Nothing
+ *    aborts the process.  Kernel-side failures (a grid barrier that exceeded its spin
+ *    limit) are latched in the plan and reported by ssht_plan_check().
+ *  - A plan is bound to the CUDA device that was current when it was created and must
+ *    be used with that device current.  One plan must not be used concurrently from
+ *    two host threads or on two streams at once (it owns one workspace).
+ */
+#ifndef SSHT_H
+#define SSHT_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SSHT_API __attribute__((visibility("default")))
+#else
+#define SSHT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSHT_OK 0
+#define SSHT_EINVAL (-1)       /* bad argument (band-limit, spin, batch, null pointer, ...) */
+#define SSHT_ENOMEM (-2)       /* device or host allocation failed */
+#define SSHT_ECUDA (-3)        /* a CUDA runtime or cuFFT call failed */
+#define SSHT_ETIMEOUT (-4)     /* a device-side wait hit its iteration limit */
+#define SSHT_EUNSUPPORTED (-5) /* valid request that this build does not implement */
+
+/* Arithmetic of the O(L^3) contraction.  The Delta recursion is FP64 in every mode. */
+typedef enum {
+  SSHT_FP64 = 0,   /* FP64 everywhere (CUDA cores); double I/O                          */
+  SSHT_FP32 = 1,   /* FP32 contraction on CUDA cores with FP64 Delta; float I/O          */
+  SSHT_TF32X3 = 2, /* contraction on tcgen05 tensor cores, 3xTF32 split products         */
+  SSHT_BF16X6 = 3  /* contraction on tcgen05 tensor cores, 3-way BF16 split, 6 products  */
+} ssht_precision;
+
+/* Where the Delta^l table lives. */
+typedef enum {
+  SSHT_DELTA_RECOMPUTE = 0, /* the recursion runs inside every transform call            */
+  SSHT_DELTA_CACHE = 1      /* the recursion runs once at plan creation; calls reuse it  */
+} ssht_delta_mode;
+
+typedef struct {
+  int L;          /* exclusive band-limit, 1 <= L <= 2048                      */
+  int s;          /* spin, |s| < L                                              */
+  int batch;      /* number of fields per call, 1 <= batch <= 65535            */
+  int precision;  /* ssht_precision                                            */
+  int delta_mode; /* ssht_delta_mode                                           */
+  int flags;      /* reserved, must be 0                                       */
+} ssht_plan_desc;
+
+typedef struct ssht_plan_s* ssht_plan_t;
+
+/* Create an FP64 plan with the Delta recursion run in every call.
+ * out: receives the plan; L, s, batch as in ssht_plan_desc.
+ * Allocates the plan's device workspace (see ssht_plan_workspace_bytes) and cuFFT plans. */
+SSHT_API int ssht_plan(ssht_plan_t* out, int L, int s, int batch);
+
+/* Create a plan from a descriptor (precision and Delta mode).  With SSHT_DELTA_CACHE the
+ * recursion runs here, synchronously, and its table stays resident in device memory. */
+SSHT_API int ssht_plan_ex(ssht_plan_t* out, const ssht_plan_desc* desc);
+
+/* Release every resource of a plan (NULL is accepted).  Synchronises the device. */
+SSHT_API int ssht_plan_destroy(ssht_plan_t plan);
+
+/* Device bytes owned by the plan (workspace, Delta table, cuFFT work areas). */
+SSHT_API int ssht_plan_workspace_bytes(ssht_plan_t plan, size_t* bytes);
+
+/* Inverse transform, eqn ssht_inv (Sec. 3.4.3 of the paper): for each field, F_{m m'}
+ * for m' >= 0 by eqn fourier_coeff, F_{m,-m'} = (-1)^{m+s} F_{m m'} (eqn Ffourier_sym),
+ * then the torus samples by eqn idft_spatial, keeping the L rings with theta <= pi.
+ * flm: [batch][L*L] complex in; f: [batch][L][2L-1] complex out. */
+SSHT_API int ssht_inverse(ssht_plan_t plan, const void* flm, void* f, void* stream);
+
+/* Forward transform, eqn ssht_fwd, by exact quadrature on the torus: per-m parity
+ * extension of the samples to theta in [0, 2pi) (Sec. 3.2), the torus DFT (eqn
+ * dft_spatial), the sin(theta) weight convolution G_{mm'} = 2pi sum_{m''} F_{mm''} w(m''-m'),
+ * w(p) = int_0^pi sin(t) e^{ipt} dt, and the projection
+ *   sf_lm = (-1)^s i^{m+s} sqrt((2l+1)/4pi) sum_{|m'|<=l} Delta^l_{m'm} Delta^l_{m',-s} G_{mm'}.
+ * Exact (up to rounding) for band-limited f; the paper's own forward (a triangular solve,
+ * eqn matrix_fwd) is unstable beyond L ~ 32 and is not used here.
+ * f: [batch][L][2L-1] complex in; flm: [batch][L*L] complex out. */
+SSHT_API int ssht_forward(ssht_plan_t plan, const void* f, void* flm, void* stream);
+
+/* Adjoint of ssht_inverse: flm = A^H g where A is the linear map of ssht_inverse
+ * (sum over the L x (2L-1) samples of g times conj(sY_lm); no quadrature weight).
+ * g: [batch][L][2L-1] complex in; flm: [batch][L*L] complex out. */
+SSHT_API int ssht_adjoint(ssht_plan_t plan, const void* g, void* flm, void* stream);
+
+/* The table of Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 2.2, Risbo recursion) for
+ * 0 <= l < L and 0 <= m', m <= l (the non-negative quadrant the paper precomputes, Sec. 4.1),
+ * FP64, entry (l, m', m) at offset(l) + m'(l+1) + m with offset(l) = l(l+1)(2l+1)/6.
+ * out: device or host buffer of L(L+1)(2L+1)/6 doubles. */
+SSHT_API int ssht_wigner_delta(ssht_plan_t plan, double* out, void* stream);
+
+/* Wait for the plan's outstanding work and report a latched kernel-side failure
+ * (SSHT_ETIMEOUT) or a CUDA error; clears the latched status. */
+SSHT_API int ssht_plan_check(ssht_plan_t plan);
+
+/* Stages of a transform, for ssht_plan_profile_read. */
+#define SSHT_STAGE_DELTA 0      /* Risbo recursion of Delta^l (and the spin column)       */
+#define SSHT_STAGE_INVERSE 1    /* inverse contraction (eqn fourier_coeff)                */
+#define SSHT_STAGE_PROJECT 2    /* forward / adjoint contraction (harmonic projection)    */
+#define SSHT_STAGE_FFT 3        /* torus DFTs (cuFFT) and the weight convolution FFTs     */
+#define SSHT_STAGE_TORUS 4      /* extension, phase, transpose and weight-product kernels */
+#define SSHT_STAGE_PACK 5       /* operand packing for the tensor-core contraction        */
+#define SSHT_NUM_STAGES 6
+
+/* Enable (1) or disable (0) per-stage timing: each stage of each later call is bracketed by
+ * CUDA events recorded on the call's stream.  Enabling resets the accumulated times. */
+SSHT_API int ssht_plan_profile(ssht_plan_t plan, int enable);
+
+/* Accumulated per-stage device time in milliseconds (ms[i], i < nstages <= SSHT_NUM_STAGES)
+ * and number of stage executions (count[i]) since profiling was enabled; synchronises the
+ * device.  launches (may be NULL) receives the number of kernels this library launched for
+ * the plan since it was created (cuFFT's kernels are not counted). */
+SSHT_API int ssht_plan_profile_read(ssht_plan_t plan, double* ms, long long* count, int nstages,
+                                    long long* launches);
+
+/* Message describing the last error on the calling host thread ("" if none). */
+SSHT_API const char* ssht_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+SSHT_API int ssht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSHT_H */

@@ -1,0 +1,623 @@
+// C ABI of libssht (declared in include/ssht.h): plans, workspaces, the order of the
+// stages of each transform, host-pointer staging and error reporting.
+#include "ssht_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace ssht;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+const char* cufft_name(cufftResult r) {
+  switch (r) {
+    case CUFFT_SUCCESS: return "CUFFT_SUCCESS";
+    case CUFFT_INVALID_PLAN: return "CUFFT_INVALID_PLAN";
+    case CUFFT_ALLOC_FAILED: return "CUFFT_ALLOC_FAILED";
+    case CUFFT_INVALID_VALUE: return "CUFFT_INVALID_VALUE";
+    case CUFFT_INTERNAL_ERROR: return "CUFFT_INTERNAL_ERROR";
+    case CUFFT_EXEC_FAILED: return "CUFFT_EXEC_FAILED";
+    case CUFFT_SETUP_FAILED: return "CUFFT_SETUP_FAILED";
+    case CUFFT_INVALID_SIZE: return "CUFFT_INVALID_SIZE";
+    default: return "cuFFT error";
+  }
+}
+
+#define SSHT_CUDA(x, what)                                                                         \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess) {                                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,                      \
+                  std::string(what) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                              \
+  } while (0)
+
+#define SSHT_FFT(x, what)                                                                          \
+  do {                                                                                             \
+    cufftResult r_ = (x);                                                                          \
+    if (r_ != CUFFT_SUCCESS) {                                                                     \
+      return fail(r_ == CUFFT_ALLOC_FAILED ? SSHT_ENOMEM : SSHT_ECUDA,                             \
+                  std::string(what) + ": " + cufft_name(r_));                                      \
+    }                                                                                              \
+  } while (0)
+
+// Smallest 2^a 3^b 5^c 7^d >= n (a length cuFFT handles with its fast radices).
+int good_fft_size(int n) {
+  for (int m = n > 1 ? n : 1;; ++m) {
+    int r = m;
+    for (int p : {2, 3, 5, 7})
+      while (r % p == 0) r /= p;
+    if (r == 1) return m;
+  }
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct ssht_plan_s {
+  int device = 0;
+  Dims d{};
+  int s = 0, B = 0, precision = 0, delta_mode = 0;
+  bool f64 = true;
+  size_t elem = 16;  // bytes per complex element of the I/O and workspaces
+  DeltaWork delta;
+  double* U = nullptr;
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  void* W3 = nullptr;
+  void* khat = nullptr;
+  void* ph = nullptr;       // phase table, element precision
+  double2* ph64 = nullptr;  // phase table, FP64
+  cufftHandle fft_phi = 0, fft_theta = 0, fft_conv = 0;
+  bool have_phi = false, have_theta = false, have_conv = false;
+  void* stage_in = nullptr;
+  size_t stage_in_bytes = 0;
+  void* stage_out = nullptr;
+  size_t stage_out_bytes = 0;
+  bool delta_ready = false;
+  size_t bytes = 0;
+  // profiling: events bracketing each stage, folded into per-stage totals on read
+  struct Ev {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Ev> evs;
+  double prof_ms[SSHT_NUM_STAGES] = {};
+  long long prof_n[SSHT_NUM_STAGES] = {};
+  long long launches = 0;
+
+  size_t coeff_bytes() const { return (size_t)B * d.L * d.L * elem; }
+  size_t grid_bytes() const { return (size_t)B * d.L * d.N * elem; }
+};
+
+namespace {
+
+void fold_events(ssht_plan_t p) {
+  for (auto& e : p->evs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      p->prof_ms[e.stage] += ms;
+      p->prof_n[e.stage] += 1;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->evs.clear();
+}
+
+// Brackets one stage with events on the call's stream while profiling is enabled.
+struct StageScope {
+  ssht_plan_t p;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageScope(ssht_plan_t p_, int stage_, cudaStream_t st_) : p(p_), stage(stage_), st(st_) {
+    if (p->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  ~StageScope() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(b, st);
+    p->evs.push_back({stage, a, b});
+    if (p->evs.size() > 8192) fold_events(p);
+  }
+};
+
+int dalloc(ssht_plan_t p, void** ptr, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(SSHT_ENOMEM, std::string("cudaMalloc ") + what + " (" + std::to_string(bytes) + " bytes): " +
+                                 cudaGetErrorString(e));
+  }
+  p->bytes += bytes;
+  return 0;
+}
+
+int exec_fft(const ssht_plan_t p, cufftHandle h, void* in, void* out, int dir, cudaStream_t st) {
+  StageScope sc(p, SSHT_STAGE_FFT, st);
+  if (p->f64) {
+    SSHT_FFT(cufftExecZ2Z(h, (cufftDoubleComplex*)in, (cufftDoubleComplex*)out, dir), "cufftExecZ2Z");
+  } else {
+    SSHT_FFT(cufftExecC2C(h, (cufftComplex*)in, (cufftComplex*)out, dir), "cufftExecC2C");
+  }
+  return 0;
+}
+
+int make_fft(ssht_plan_t p, cufftHandle* h, bool* have, int n, size_t batch, const char* what) {
+  if (batch > (size_t)0x7fffffff) return fail(SSHT_EUNSUPPORTED, std::string(what) + ": batch too large");
+  int nn = n;
+  SSHT_FFT(cufftPlanMany(h, 1, &nn, nullptr, 1, n, nullptr, 1, n, p->f64 ? CUFFT_Z2Z : CUFFT_C2C, (int)batch), what);
+  *have = true;
+  size_t ws = 0;
+  if (cufftGetSize(*h, &ws) == CUFFT_SUCCESS) p->bytes += ws;
+  return 0;
+}
+
+int set_streams(ssht_plan_t p, cudaStream_t st) {
+  if (p->have_phi) SSHT_FFT(cufftSetStream(p->fft_phi, st), "cufftSetStream");
+  if (p->have_theta) SSHT_FFT(cufftSetStream(p->fft_theta, st), "cufftSetStream");
+  if (p->have_conv) SSHT_FFT(cufftSetStream(p->fft_conv, st), "cufftSetStream");
+  return 0;
+}
+
+int run_delta(ssht_plan_t p, cudaStream_t st) {
+  StageScope sc(p, SSHT_STAGE_DELTA, st);
+  SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
+  SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, st), "spin column launch");
+  p->launches += 2;
+  return 0;
+}
+
+int ensure_delta(ssht_plan_t p, cudaStream_t st) {
+  if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
+  int rc = run_delta(p, st);
+  if (rc) return rc;
+  if (p->delta_mode == SSHT_DELTA_CACHE) p->delta_ready = true;
+  return 0;
+}
+
+int check_device(ssht_plan_t p) {
+  int cur = -1;
+  SSHT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+  if (cur != p->device)
+    return fail(SSHT_EINVAL, "plan was created on device " + std::to_string(p->device) + " but device " +
+                                 std::to_string(cur) + " is current");
+  return 0;
+}
+
+int stage_buffer(ssht_plan_t p, void** buf, size_t* have, size_t need, const char* what) {
+  if (*have >= need) return 0;
+  if (*buf) {
+    cudaFree(*buf);
+    p->bytes -= *have;
+    *buf = nullptr;
+    *have = 0;
+  }
+  int rc = dalloc(p, buf, need, what);
+  if (rc) return rc;
+  *have = need;
+  return 0;
+}
+
+// Resolve input/output pointers: host buffers go through plan-owned staging memory.
+struct IO {
+  const void* in_dev;
+  void* out_dev;
+  void* out_host;
+  size_t out_bytes;
+};
+
+int io_begin(ssht_plan_t p, const void* in, size_t in_bytes, void* out, size_t out_bytes, cudaStream_t st, IO* io) {
+  if (!in || !out) return fail(SSHT_EINVAL, "null data pointer");
+  io->out_host = nullptr;
+  io->out_bytes = out_bytes;
+  if (is_device_pointer(in)) {
+    io->in_dev = in;
+  } else {
+    int rc = stage_buffer(p, &p->stage_in, &p->stage_in_bytes, in_bytes, "input staging");
+    if (rc) return rc;
+    SSHT_CUDA(cudaMemcpyAsync(p->stage_in, in, in_bytes, cudaMemcpyHostToDevice, st), "input copy to device");
+    io->in_dev = p->stage_in;
+  }
+  if (is_device_pointer(out)) {
+    io->out_dev = out;
+  } else {
+    int rc = stage_buffer(p, &p->stage_out, &p->stage_out_bytes, out_bytes, "output staging");
+    if (rc) return rc;
+    io->out_dev = p->stage_out;
+    io->out_host = out;
+  }
+  return 0;
+}
+
+int io_end(ssht_plan_t p, const IO& io, cudaStream_t st) {
+  (void)p;
+  if (io.out_host) {
+    SSHT_CUDA(cudaMemcpyAsync(io.out_host, io.out_dev, io.out_bytes, cudaMemcpyDeviceToHost, st),
+              "output copy to host");
+    SSHT_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+  }
+  SSHT_CUDA(cudaGetLastError(), "kernel launch");
+  return 0;
+}
+
+template <typename T>
+int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
+  const Dims& d = p->d;
+  int rc = ensure_delta(p, st);
+  if (rc) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_INVERSE, st);
+    SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, st),
+              "inverse contraction");
+    p->launches += 1;
+  }
+  rc = exec_fft(p, p->fft_theta, p->W1, p->W2, CUFFT_INVERSE, st);
+  if (rc) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(inv_theta_to_phi<T>(d, p->B, p->W2, p->W1, p->ph, st), "theta-to-phi transpose");
+    p->launches += 1;
+  }
+  return exec_fft(p, p->fft_phi, p->W1, f, CUFFT_INVERSE, st);
+}
+
+// Shared front of the forward transform (mode 0) and the adjoint (mode 1): phi DFT,
+// extension (or zero rings) into the theta-DFT input, theta DFT in place in W1.
+template <typename T>
+int analysis_front(ssht_plan_t p, const void* f, int mode, cudaStream_t st) {
+  const Dims& d = p->d;
+  int rc = exec_fft(p, p->fft_phi, const_cast<void*>(f), p->W2, CUFFT_FORWARD, st);
+  if (rc) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(fwd_phi_to_theta<T>(d, p->s, p->B, mode, p->W2, p->W1, p->ph, st), "phi-to-theta extension");
+    p->launches += 1;
+  }
+  return exec_fft(p, p->fft_theta, p->W1, p->W1, CUFFT_FORWARD, st);
+}
+
+template <typename T>
+int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
+  const Dims& d = p->d;
+  int rc = analysis_front<T>(p, f, 0, st);
+  if (rc) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(fwd_theta_to_conv<T>(d, p->B, p->W1, p->W3, p->ph, st), "weight convolution input");
+    p->launches += 1;
+  }
+  if ((rc = exec_fft(p, p->fft_conv, p->W3, p->W3, CUFFT_FORWARD, st))) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(conv_multiply<T>(d, p->B, p->W3, p->khat, st), "weight convolution product");
+    p->launches += 1;
+  }
+  if ((rc = exec_fft(p, p->fft_conv, p->W3, p->W3, CUFFT_INVERSE, st))) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(conv_to_project<T>(d, p->B, p->W3, p->W1, st), "weight convolution output");
+    p->launches += 1;
+  }
+  if ((rc = ensure_delta(p, st))) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "forward contraction");
+    p->launches += 1;
+  }
+  return 0;
+}
+
+template <typename T>
+int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
+  const Dims& d = p->d;
+  int rc = analysis_front<T>(p, g, 1, st);
+  if (rc) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_TORUS, st);
+    SSHT_CUDA(adj_theta_fold<T>(d, p->s, p->B, p->W1, p->W2, p->ph, st), "adjoint fold");
+    p->launches += 1;
+  }
+  if ((rc = ensure_delta(p, st))) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W2, flm, st), "adjoint contraction");
+    p->launches += 1;
+  }
+  return 0;
+}
+
+void release(ssht_plan_t p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  for (auto& e : p->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (p->have_phi) cufftDestroy(p->fft_phi);
+  if (p->have_theta) cufftDestroy(p->fft_theta);
+  if (p->have_conv) cufftDestroy(p->fft_conv);
+  void* ptrs[] = {p->delta.table, p->delta.slab[0], p->delta.slab[1], p->delta.sqrt_tab, p->delta.barrier,
+                  p->delta.status, p->U, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
+  if (!out || !desc) return fail(SSHT_EINVAL, "null argument");
+  *out = nullptr;
+  const int L = desc->L, s = desc->s, B = desc->batch;
+  if (L < 1 || L > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
+  if (s <= -L || s >= L) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
+  if (B < 1 || B > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
+  if (desc->flags != 0) return fail(SSHT_EINVAL, "flags must be 0");
+  if (desc->delta_mode != SSHT_DELTA_RECOMPUTE && desc->delta_mode != SSHT_DELTA_CACHE)
+    return fail(SSHT_EINVAL, "unknown Delta mode");
+  if (desc->precision != SSHT_FP64 && desc->precision != SSHT_FP32 && desc->precision != SSHT_TF32X3 &&
+      desc->precision != SSHT_BF16X6)
+    return fail(SSHT_EINVAL, "unknown precision");
+  if (desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6)
+    return fail(SSHT_EUNSUPPORTED, "tensor-core precisions are not built in this library version");
+
+  ssht_plan_t p = new (std::nothrow) ssht_plan_s();
+  if (!p) return fail(SSHT_ENOMEM, "host allocation of the plan");
+  int rc = 0;
+  cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce != cudaSuccess) {
+    release(p);
+    return fail(SSHT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  }
+  p->d.L = L;
+  p->d.Lp = L - 1;
+  p->d.N = 2 * L - 1;
+  p->d.M = good_fft_size(4 * L - 3);
+  p->s = s;
+  p->B = B;
+  p->precision = desc->precision;
+  p->delta_mode = desc->delta_mode;
+  p->f64 = desc->precision == SSHT_FP64;
+  p->elem = p->f64 ? 16 : 8;
+  const Dims& d = p->d;
+
+  auto bail = [&](int code) {
+    release(p);
+    return code;
+  };
+  ce = delta_setup(p->delta, L, p->device);
+  if (ce != cudaSuccess) {
+    release(p);
+    return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                std::string("Delta recursion setup: ") + cudaGetErrorString(ce));
+  }
+  p->bytes += delta_offset(L) * 8 + 2 * tri(L + 1) * 8;
+  if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
+  const size_t torus = (size_t)B * d.N * d.N * p->elem;
+  if ((rc = dalloc(p, &p->W1, torus, "torus workspace 1"))) return bail(rc);
+  if ((rc = dalloc(p, &p->W2, torus, "torus workspace 2"))) return bail(rc);
+  if ((rc = dalloc(p, &p->W3, (size_t)B * d.N * d.M * p->elem, "convolution workspace"))) return bail(rc);
+  if ((rc = dalloc(p, &p->khat, (size_t)d.M * p->elem, "weight spectrum"))) return bail(rc);
+  if ((rc = dalloc(p, &p->ph, (size_t)(2 * d.N - 1) * p->elem, "phase table"))) return bail(rc);
+  if ((rc = dalloc(p, (void**)&p->ph64, (size_t)(2 * d.N - 1) * sizeof(double2), "phase table"))) return bail(rc);
+
+  // Phase table e^{i pi k / N}, |k| < N, computed in FP64 on the host.
+  {
+    std::vector<double2> h(2 * d.N - 1);
+    std::vector<float2> hf(2 * d.N - 1);
+    const double pi = 3.14159265358979323846;
+    for (int k = -(d.N - 1); k <= d.N - 1; ++k) {
+      // reduce the angle to [-pi/2, pi/2]-ish before cos/sin for accuracy: k/N in (-1, 1)
+      const double a = pi * (double)k / (double)d.N;
+      h[k + d.N - 1] = make_double2(std::cos(a), std::sin(a));
+      hf[k + d.N - 1] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    ce = cudaMemcpy(p->ph64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(p->ph, p->f64 ? (const void*)h.data() : (const void*)hf.data(), h.size() * p->elem,
+                      cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(SSHT_ECUDA, std::string("phase table upload: ") + cudaGetErrorString(ce));
+    }
+  }
+  if ((rc = make_fft(p, &p->fft_phi, &p->have_phi, d.N, (size_t)B * d.L, "cuFFT phi plan"))) return bail(rc);
+  if ((rc = make_fft(p, &p->fft_theta, &p->have_theta, d.N, (size_t)B * d.N, "cuFFT theta plan"))) return bail(rc);
+  if ((rc = make_fft(p, &p->fft_conv, &p->have_conv, d.M, (size_t)B * d.N, "cuFFT convolution plan"))) return bail(rc);
+
+  // Weight spectrum: FFT of the even part of w(p) = int_0^pi sin(t) e^{ipt} dt.
+  {
+    cufftHandle k1;
+    int nn = d.M;
+    cufftResult r = cufftPlan1d(&k1, nn, p->f64 ? CUFFT_Z2Z : CUFFT_C2C, 1);
+    if (r != CUFFT_SUCCESS) {
+      release(p);
+      return fail(SSHT_ECUDA, std::string("cuFFT weight plan: ") + cufft_name(r));
+    }
+    ce = p->f64 ? make_weight_kernel<double>(d, p->khat, 0) : make_weight_kernel<float>(d, p->khat, 0);
+    if (ce == cudaSuccess) {
+      r = p->f64 ? cufftExecZ2Z(k1, (cufftDoubleComplex*)p->khat, (cufftDoubleComplex*)p->khat, CUFFT_FORWARD)
+                 : cufftExecC2C(k1, (cufftComplex*)p->khat, (cufftComplex*)p->khat, CUFFT_FORWARD);
+    }
+    cudaError_t se = cudaDeviceSynchronize();
+    cufftDestroy(k1);
+    if (ce != cudaSuccess || r != CUFFT_SUCCESS || se != cudaSuccess) {
+      release(p);
+      return fail(SSHT_ECUDA, "weight spectrum setup failed");
+    }
+  }
+  if (p->delta_mode == SSHT_DELTA_CACHE) {
+    if ((rc = run_delta(p, 0))) return bail(rc);
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(SSHT_ECUDA, std::string("Delta recursion: ") + cudaGetErrorString(ce));
+    }
+    int st = 0;
+    cudaMemcpy(&st, p->delta.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (st != 0) {
+      release(p);
+      return fail(SSHT_ETIMEOUT, "Delta recursion grid barrier timed out");
+    }
+    p->delta_ready = true;
+  }
+  *out = p;
+  g_last_error.clear();
+  return SSHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssht_plan(ssht_plan_t* out, int L, int s, int batch) {
+  ssht_plan_desc d{L, s, batch, SSHT_FP64, SSHT_DELTA_RECOMPUTE, 0};
+  return create(out, &d);
+}
+
+int ssht_plan_ex(ssht_plan_t* out, const ssht_plan_desc* desc) { return create(out, desc); }
+
+int ssht_plan_destroy(ssht_plan_t plan) {
+  release(plan);
+  return SSHT_OK;
+}
+
+int ssht_plan_workspace_bytes(ssht_plan_t plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(SSHT_EINVAL, "null argument");
+  *bytes = plan->bytes;
+  return SSHT_OK;
+}
+
+int ssht_inverse(ssht_plan_t p, const void* flm, void* f, void* stream) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = set_streams(p, st))) return rc;
+  IO io;
+  if ((rc = io_begin(p, flm, p->coeff_bytes(), f, p->grid_bytes(), st, &io))) return rc;
+  rc = p->f64 ? inverse_impl<double>(p, io.in_dev, io.out_dev, st) : inverse_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (rc) return rc;
+  return io_end(p, io, st);
+}
+
+int ssht_forward(ssht_plan_t p, const void* f, void* flm, void* stream) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = set_streams(p, st))) return rc;
+  IO io;
+  if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
+  rc = p->f64 ? forward_impl<double>(p, io.in_dev, io.out_dev, st) : forward_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (rc) return rc;
+  return io_end(p, io, st);
+}
+
+int ssht_adjoint(ssht_plan_t p, const void* g, void* flm, void* stream) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = set_streams(p, st))) return rc;
+  IO io;
+  if ((rc = io_begin(p, g, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
+  rc = p->f64 ? adjoint_impl<double>(p, io.in_dev, io.out_dev, st) : adjoint_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (rc) return rc;
+  return io_end(p, io, st);
+}
+
+int ssht_wigner_delta(ssht_plan_t p, double* out, void* stream) {
+  if (!p || !out) return fail(SSHT_EINVAL, "null argument");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = ensure_delta(p, st))) return rc;
+  const size_t bytes = delta_offset(p->d.L) * sizeof(double);
+  if (is_device_pointer(out)) {
+    SSHT_CUDA(cudaMemcpyAsync(out, p->delta.table, bytes, cudaMemcpyDeviceToDevice, st), "Delta table copy");
+  } else {
+    SSHT_CUDA(cudaMemcpyAsync(out, p->delta.table, bytes, cudaMemcpyDeviceToHost, st), "Delta table copy");
+    SSHT_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+  }
+  SSHT_CUDA(cudaGetLastError(), "kernel launch");
+  return SSHT_OK;
+}
+
+int ssht_plan_check(ssht_plan_t p) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  int rc = check_device(p);
+  if (rc) return rc;
+  SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
+  int st = 0;
+  SSHT_CUDA(cudaMemcpy(&st, p->delta.status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (st != 0) {
+    cudaMemset(p->delta.status, 0, sizeof(int));
+    if (p->delta_mode == SSHT_DELTA_CACHE) p->delta_ready = false;
+    return fail(SSHT_ETIMEOUT, "a Delta recursion grid barrier exceeded its spin limit");
+  }
+  return SSHT_OK;
+}
+
+int ssht_plan_profile(ssht_plan_t p, int enable) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  int rc = check_device(p);
+  if (rc) return rc;
+  SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
+  for (auto& e : p->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->evs.clear();
+  for (int i = 0; i < SSHT_NUM_STAGES; ++i) {
+    p->prof_ms[i] = 0.0;
+    p->prof_n[i] = 0;
+  }
+  p->prof = enable != 0;
+  return SSHT_OK;
+}
+
+int ssht_plan_profile_read(ssht_plan_t p, double* ms, long long* count, int nstages, long long* launches) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  if (nstages < 0 || nstages > SSHT_NUM_STAGES || (nstages > 0 && (!ms || !count)))
+    return fail(SSHT_EINVAL, "bad stage buffers");
+  int rc = check_device(p);
+  if (rc) return rc;
+  SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
+  fold_events(p);
+  for (int i = 0; i < nstages; ++i) {
+    ms[i] = p->prof_ms[i];
+    count[i] = p->prof_n[i];
+  }
+  if (launches) *launches = p->launches;
+  return SSHT_OK;
+}
+
+const char* ssht_last_error(void) { return g_last_error.c_str(); }
+
+int ssht_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Delta^l = d^l(pi/2) for l = 0 .. L-1 by the Risbo recursion (the recursion the paper
+// uses, Sec. 2.2), FP64, on the symmetry-reduced octant 0 <= n <= m <= l.
+//
+// One half step couples d^{j-1/2} with the spin-1/2 matrix [[p,-q],[q,p]], p = q = 1/sqrt2:
+//   d^j_{mn} = p/(2j) [ sqrt(j+m) ( sqrt(j+n) X(m-1/2, n-1/2) - sqrt(j-n) X(m-1/2, n+1/2) )
+//                     + sqrt(j-m) ( sqrt(j+n) X(m+1/2, n-1/2) + sqrt(j-n) X(m+1/2, n+1/2) ) ]
+// with X = d^{j-1/2} (zero outside |index| <= j - 1/2).  Entries outside the stored octant
+// are read through the symmetry relations
+//   d_{mn} = (-1)^{m-n} d_{nm}            (transpose; from eqn wignerd_sym3, any j),
+//   d_{mn} = (-1)^{m-n} d_{-m,-n}         (eqn wignerd_sym1),
+//   Delta^l_{m,-n} = (-1)^{l+m} Delta^l_{mn}  (eqn wignerd_sym1 with eqn wignerd_sym2, integer l).
+//
+// Storage.  Integer degree l: octant slab Y[m(m+1)/2 + n], 0 <= n <= m <= l.
+// Half-integer degree l+1/2: rows a = A + 1/2 (A = 0..l), columns b = B - 1/2 (B = 0..A+1),
+// i.e. the octant plus the column b = -1/2, at A(A+3)/2 + B.
+//
+// Parallel layout.  One cooperative persistent grid walks l.  For the step l -> l+1 the
+// rows of the new integer slab are split over the CTAs by equal entry counts.  A CTA that
+// owns integer rows [r0, r1) first computes the half-integer rows [r0-1, r1-1] it needs
+// (one row is also computed by its neighbour) into shared memory, then its integer rows,
+// which it writes to the next octant buffer and, in both orientations, to the quadrant
+// table.  So each degree costs one grid barrier.  The barrier spins at most one second,
+// then latches a status bit and every CTA leaves the kernel.
+#include "ssht_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace ssht {
+namespace {
+
+constexpr int kThreads = 512;
+
+struct RisboParams {
+  int L;
+  double* table;
+  double* slab0;
+  double* slab1;
+  const double* sq;         // sqrt(k)
+  unsigned int* counter;    // [0] barrier counter, [1] abort flag (reset before launch)
+  int* status;              // latched status bits
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier with a one-second spin limit.  Returns false if this CTA must stop.
+__device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+    int good = 1;
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int spins = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++spins & 63u) == 0u) {
+        if (*(volatile unsigned int*)(counter + 1) != 0u) { good = 0; break; }
+        if (globaltimer_ns() - t0 > 1000000000ull) {
+          atomicOr(status, kStatusBarrierTimeout);
+          atomicExch(counter + 1, 1u);
+          good = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__host__ __device__ __forceinline__ long long tri_ll(long long m) { return m * (m + 1) / 2; }
+__host__ __device__ __forceinline__ long long hoff_ll(long long A) { return A * (A + 3) / 2; }
+
+// Largest m with tri(m) <= e.
+__device__ __forceinline__ int tri_row(long long e) {
+  int m = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (m > 0 && tri_ll(m) > e) --m;
+  while (tri_ll(m + 1) <= e) ++m;
+  return m;
+}
+
+// Largest A with hoff(A) <= i.
+__device__ __forceinline__ int hoff_row(long long i) {
+  int A = (int)((sqrtf(8.0f * (float)i + 9.0f) - 3.0f) * 0.5f);
+  if (A < 0) A = 0;
+  while (A > 0 && hoff_ll(A) > i) --A;
+  while (hoff_ll(A + 1) <= i) ++A;
+  return A;
+}
+
+// Smallest m with tri(m) >= x (row where the CTA's share starts).
+__host__ __device__ __forceinline__ int share_row(long long x, int rows) {
+  int m = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  if (m < 0) m = 0;
+  if (m > rows) m = rows;
+  while (m > 0 && tri_ll(m - 1) >= x) --m;
+  while (m < rows && tri_ll(m) < x) ++m;
+  return m;
+}
+
+__host__ __device__ __forceinline__ void cta_rows(int lp, int cta, int nb, int* r0, int* r1) {
+  const long long S = tri_ll(lp + 1);
+  *r0 = share_row(S * cta / nb, lp + 1);
+  *r1 = share_row(S * (cta + 1) / nb, lp + 1);
+}
+
+// Integer slab of degree l, any (m, n) with 0 <= m <= l+1 and -1 <= n <= m+1.
+__device__ __forceinline__ double yget(const double* __restrict__ Y, int l, int m, int n) {
+  double sg = 1.0;
+  if (n == -1) {
+    if (m == 0) {  // Delta_{0,-1} = (-1)^l Delta_{0,1} = (-1)^{l+1} Delta_{1,0}
+      sg = (l & 1) ? 1.0 : -1.0;
+      m = 1;
+      n = 0;
+    } else {       // Delta_{m,-1} = (-1)^{l+m} Delta_{m,1}
+      sg = ((l + m) & 1) ? -1.0 : 1.0;
+      n = 1;
+    }
+  }
+  if (n > m) {     // transpose
+    if ((n - m) & 1) sg = -sg;
+    const int t = m; m = n; n = t;
+  }
+  if (m > l) return 0.0;
+  return sg * Y[tri_ll(m) + n];
+}
+
+// Half-integer slab of degree l+1/2 held in shared memory from row Alo on,
+// any (A, B) with -1 <= A <= l+1 and 0 <= B <= A+2.
+__device__ __forceinline__ double xget(const double* __restrict__ X, int l, long long hbase, int A, int B) {
+  double sg = 1.0;
+  if (A == -1) {   // a = -1/2
+    if (B == 0) {  // (-1/2,-1/2) = (1/2,1/2)
+      A = 0; B = 1;
+    } else {       // (-1/2,1/2) = -(1/2,-1/2)
+      A = 0; B = 0; sg = -1.0;
+    }
+  }
+  if (B > A + 1) { // b > a: transpose (a,b) -> (b,a), sign (-1)^{a-b}
+    if ((B - A - 1) & 1) sg = -sg;
+    const int nA = B - 1, nB = A + 1;
+    A = nA; B = nB;
+  }
+  if (A > l) return 0.0;
+  return sg * X[hoff_ll(A) + B - hbase];
+}
+
+__global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P) {
+  extern __shared__ double hs[];
+  const int nb = gridDim.x;
+  const int cta = blockIdx.x;
+  if (cta == 0 && threadIdx.x == 0) {
+    P.slab0[0] = 1.0;
+    P.table[0] = 1.0;
+  }
+  unsigned int phase = 1;
+  if (!grid_barrier(P.counter, phase * nb, P.status)) return;
+  for (int l = 0; l + 1 < P.L; ++l) {
+    const double* __restrict__ Y = (l & 1) ? P.slab1 : P.slab0;
+    double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
+    const int lp = l + 1;
+    int r0, r1;
+    cta_rows(lp, cta, nb, &r0, &r1);
+    if (r0 < r1) {
+      const int Alo = r0 > 0 ? r0 - 1 : 0;
+      const int Ahi = (r1 - 1 < l) ? r1 - 1 : l;
+      const long long hbase = hoff_ll(Alo);
+      const int hcount = (int)(hoff_ll(Ahi + 1) - hbase);
+      // Half step l -> l + 1/2 (2j = 2l + 1).  j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.
+      const double sc = 0.70710678118654752440 / (double)(2 * l + 1);
+      for (int i = threadIdx.x; i < hcount; i += blockDim.x) {
+        const int A = hoff_row(hbase + i);
+        const int B = (int)(hbase + i - hoff_ll(A));
+        const double x1 = yget(Y, l, A, B - 1);
+        const double x2 = yget(Y, l, A, B);
+        const double x3 = yget(Y, l, A + 1, B - 1);
+        const double x4 = yget(Y, l, A + 1, B);
+        const double sb = P.sq[l + B], smb = P.sq[l + 1 - B];
+        const double t1 = fma(-smb, x2, sb * x1);
+        const double t2 = fma(smb, x4, sb * x3);
+        hs[i] = fma(P.sq[l + A + 1], t1, P.sq[l - A] * t2) * sc;
+      }
+      __syncthreads();
+      // Integer step l + 1/2 -> lp (2j = 2 lp).
+      const double sc2 = 0.70710678118654752440 / (double)(2 * lp);
+      double* __restrict__ T = P.table + (size_t)((long long)lp * (lp + 1) * (2 * lp + 1) / 6);
+      const long long e0 = tri_ll(r0), e1 = tri_ll(r1);
+      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int m = tri_row(e);
+        const int n = (int)(e - tri_ll(m));
+        const double x1 = xget(hs, l, hbase, m - 1, n);
+        const double x2 = xget(hs, l, hbase, m - 1, n + 1);
+        const double x3 = xget(hs, l, hbase, m, n);
+        const double x4 = xget(hs, l, hbase, m, n + 1);
+        const double sb = P.sq[lp + n], smb = P.sq[lp - n];
+        const double t1 = fma(-smb, x2, sb * x1);
+        const double t2 = fma(smb, x4, sb * x3);
+        const double v = fma(P.sq[lp + m], t1, P.sq[lp - m] * t2) * sc2;
+        Yn[e] = v;
+        T[(size_t)m * (lp + 1) + n] = v;
+        if (n != m) T[(size_t)n * (lp + 1) + m] = ((m - n) & 1) ? -v : v;
+      }
+    }
+    ++phase;
+    if (!grid_barrier(P.counter, phase * nb, P.status)) return;
+  }
+}
+
+// U[tri(l) + m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s} for l >= |s|, 0 otherwise.
+__global__ void spin_column_kernel(const double* __restrict__ table, int L, int s, double* __restrict__ U) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tri_ll(L)) return;
+  int l = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+  while (l > 0 && tri_ll(l) > e) --l;
+  while (tri_ll(l + 1) <= e) ++l;
+  const int mp = (int)(e - tri_ll(l));
+  const int as = s < 0 ? -s : s;
+  double v = 0.0;
+  if (l >= as) {
+    const double* T = table + (size_t)((long long)l * (l + 1) * (2 * l + 1) / 6);
+    const double d = T[(size_t)mp * (l + 1) + as];
+    // Delta_{m',-s}: for s <= 0 the column -s >= 0 is stored; for s > 0 use eqn wignerd_sym6.
+    v = (s > 0 && ((l + mp) & 1)) ? -d : d;
+    v *= sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
+  }
+  U[e] = v;
+}
+
+}  // namespace
+
+static size_t risbo_smem_doubles(int L, int nb) {
+  long long best = 1;
+  for (int l = 0; l + 1 < L; ++l) {
+    const int lp = l + 1;
+    for (int c = 0; c < nb; ++c) {
+      int r0, r1;
+      cta_rows(lp, c, nb, &r0, &r1);
+      if (r0 >= r1) continue;
+      const int Alo = r0 > 0 ? r0 - 1 : 0;
+      const int Ahi = std::min(r1 - 1, l);
+      best = std::max(best, hoff_ll(Ahi + 1) - hoff_ll(Alo));
+    }
+  }
+  return (size_t)best;
+}
+
+cudaError_t delta_setup(DeltaWork& w, int L, int device) {
+  cudaError_t e;
+  int sms = 0, per_sm = 0, smem_optin = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) return e;
+  w.threads = kThreads;
+  w.blocks = sms;  // one CTA per SM
+  w.smem = risbo_smem_doubles(L, w.blocks) * sizeof(double);
+  if ((int)w.smem > smem_optin) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.slab[0], tri(L + 1) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.slab[1], tri(L + 1) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.sqrt_tab, (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.barrier, 4 * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
+  std::vector<double> sq(2 * (size_t)L + 4);
+  for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
+  return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  RisboParams P;
+  P.L = L;
+  P.table = w.table;
+  P.slab0 = w.slab[0];
+  P.slab1 = w.slab[1];
+  P.sq = w.sqrt_tab;
+  P.counter = w.barrier;
+  P.status = w.status;
+  void* args[] = {&P};
+  return cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(w.blocks), dim3(w.threads), args, w.smem, st);
+}
+
+cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cudaStream_t st) {
+  const long long n = tri_ll(L);
+  const int threads = 256;
+  spin_column_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(table, L, s, U);
+  return cudaGetLastError();
+}
+
+}  // namespace ssht

@@ -1,0 +1,93 @@
+// Internal declarations of libssht (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/ssht.h"
+
+namespace ssht {
+
+// Device status word bits (latched by kernels, read by ssht_plan_check).
+enum : int { kStatusOk = 0, kStatusBarrierTimeout = 1 };
+
+// Sizes derived from the exclusive band-limit L.
+struct Dims {
+  int L;   // exclusive band-limit
+  int Lp;  // L - 1, the paper's inclusive band-limit
+  int N;   // 2L - 1 torus samples per axis
+  int M;   // length of the zero-padded weight convolution, >= 4L - 3
+};
+
+inline size_t delta_offset(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
+inline size_t tri(long long l) { return (size_t)(l * (l + 1) / 2); }
+
+// ---------------------------------------------------------------------------
+// Delta recursion (delta.cu)
+// ---------------------------------------------------------------------------
+struct DeltaWork {
+  double* table = nullptr;        // quadrant table, delta_offset(L) doubles
+  double* slab[2] = {nullptr, nullptr};  // octant buffers, tri(L) doubles each
+  double* sqrt_tab = nullptr;     // sqrt(k), k = 0 .. 2L + 2
+  unsigned int* barrier = nullptr;  // grid barrier counter
+  int* status = nullptr;          // latched status word
+  int blocks = 0;                 // cooperative grid size
+  int threads = 0;
+  size_t smem = 0;
+};
+
+cudaError_t delta_setup(DeltaWork& w, int L, int device);
+cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st);
+// U[l][m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s}, l < L, 0 <= m' <= l, at tri(l) + m'.
+cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// SIMT contractions (contract_simt.cu); T is double or float
+// ---------------------------------------------------------------------------
+// Inverse: writes the theta-DFT input E[b][m + Lp][k], k = m' mod N, of the extended,
+// phase-shifted F (eqn fourier_coeff, eqn Ffourier_sym, eqn idft_spatial phase).
+template <typename T>
+cudaError_t contract_inverse_simt(const Dims& d, int s, int B, const double* table, const double* U,
+                                  const void* flm, void* E, const double2* ph, cudaStream_t st);
+// Projection: flm[b][l*l+l+m] = (-1)^s i^{m+s} c_l sum_{m'>=0} Delta_{m'm} Delta_{m',-s} H[b][m+Lp][m']
+template <typename T>
+cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* table, const double* U,
+                                  const void* H, void* flm, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Torus kernels (torus.cu)
+// ---------------------------------------------------------------------------
+// g[b][m+Lp][t] (theta-synthesis output, N per row) -> h[b][t][m mod N] * e^{i pi m / N}, t < L.
+template <typename T>
+cudaError_t inv_theta_to_phi(const Dims& d, int B, const void* g, void* h, const void* ph, cudaStream_t st);
+// X[b][t][k] (phi-DFT of the samples) -> ext[b][m+Lp][t'] (theta-DFT input).
+// mode 0: forward (per-m parity extension, factor e^{-i pi m/N}/N);
+// mode 1: adjoint (zero rings t' >= L, factor e^{-i pi m/N}).
+template <typename T>
+cudaError_t fwd_phi_to_theta(const Dims& d, int s, int B, int mode, const void* X, void* ext, const void* ph,
+                             cudaStream_t st);
+// Fk[b][m+Lp][k'] (theta-DFT) -> zero-padded conv input cx[b][m+Lp][j], j = m'' mod M,
+// value F_{m m''} = Fk[k'(m'')] e^{-i pi m''/N} / N.
+template <typename T>
+cudaError_t fwd_theta_to_conv(const Dims& d, int B, const void* Fk, void* cx, const void* ph, cudaStream_t st);
+// Pointwise product of the conv spectrum with the weight spectrum (real kernel, length M).
+template <typename T>
+cudaError_t conv_multiply(const Dims& d, int B, void* cx, const void* khat, cudaStream_t st);
+// Conv output y[b][m+Lp][j] -> H[b][m+Lp][m'] = c_{m'} y[m'] / M, m' in [0, Lp], c_0 = 2pi, else 4pi.
+template <typename T>
+cudaError_t conv_to_project(const Dims& d, int B, const void* y, void* H, cudaStream_t st);
+// Adjoint: Fk (theta-DFT of the zero-padded rings) -> folded H[b][m+Lp][m'], m' in [0, Lp]:
+// H'_{m m'} + (-1)^{m+s} H'_{m,-m'} (m' > 0), H'_{m 0} (m' = 0), H'_{m m'} = Fk[k'(m')] e^{-i pi m'/N}.
+template <typename T>
+cudaError_t adj_theta_fold(const Dims& d, int s, int B, const void* Fk, void* H, const void* ph, cudaStream_t st);
+// Weight kernel kappa[p mod M] = w_e(p) = 2/(1-p^2) for even |p| <= 2Lp (0 otherwise); its FFT is
+// the spectrum used by conv_multiply.  The phase table ph[k + N - 1] = e^{i pi k/N}, |k| < N, is
+// complex in the element precision T (double2 or float2).
+template <typename T>
+cudaError_t make_weight_kernel(const Dims& d, void* kappa, cudaStream_t st);
+
+}  // namespace ssht

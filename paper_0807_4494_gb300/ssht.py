@@ -1,0 +1,261 @@
+"""Python binding of libssht (see include/ssht.h).  Argument marshalling only: every step of
+every transform runs in the CUDA library; there is no CPU path.  If the library is missing
+the first call raises.
+
+Low-level functions carry the C names (``ssht_plan``, ``ssht_inverse``, ...) and take raw
+pointers; ``Plan`` wraps them for torch tensors (device memory and streams come from torch).
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libssht.so")
+
+FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
+RECOMPUTE, CACHE = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
+ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
+          -5: "SSHT_EUNSUPPORTED"}
+EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspace_bytes", "ssht_inverse",
+           "ssht_forward", "ssht_adjoint", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
+           "ssht_plan_profile_read", "ssht_last_error", "ssht_version")
+STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
+
+
+class SshtError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s (%s): %s" % (what, ERRORS.get(code, code), _lib().ssht_last_error().decode()))
+        self.code = code
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("s", ctypes.c_int), ("batch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("delta_mode", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libssht.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i = ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "ssht_plan": ([ctypes.POINTER(vp), i, i, i], i),
+            "ssht_plan_ex": ([ctypes.POINTER(vp), ctypes.POINTER(PlanDesc)], i),
+            "ssht_plan_destroy": ([vp], i),
+            "ssht_plan_workspace_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i),
+            "ssht_inverse": ([vp, vp, vp, vp], i),
+            "ssht_forward": ([vp, vp, vp, vp], i),
+            "ssht_adjoint": ([vp, vp, vp, vp], i),
+            "ssht_wigner_delta": ([vp, vp, vp], i),
+            "ssht_plan_check": ([vp], i),
+            "ssht_plan_profile": ([vp, i], i),
+            "ssht_plan_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), i,
+                                        ctypes.POINTER(ctypes.c_longlong)], i),
+            "ssht_last_error": ([], ctypes.c_char_p),
+            "ssht_version": ([], i),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise SshtError(rc, what)
+
+
+# ---- C-named wrappers (raw pointers as ints) -------------------------------------------------
+
+def ssht_plan(L, s, batch):
+    h = ctypes.c_void_p()
+    _check(_lib().ssht_plan(ctypes.byref(h), L, s, batch), "ssht_plan")
+    return h
+
+
+def ssht_plan_ex(L, s, batch, precision=FP64, delta_mode=RECOMPUTE):
+    h = ctypes.c_void_p()
+    d = PlanDesc(L, s, batch, precision, delta_mode, 0)
+    _check(_lib().ssht_plan_ex(ctypes.byref(h), ctypes.byref(d)), "ssht_plan_ex")
+    return h
+
+
+def ssht_plan_destroy(h):
+    return _lib().ssht_plan_destroy(h)
+
+
+def ssht_inverse(h, flm_ptr, f_ptr, stream=0):
+    _check(_lib().ssht_inverse(h, flm_ptr, f_ptr, stream), "ssht_inverse")
+
+
+def ssht_forward(h, f_ptr, flm_ptr, stream=0):
+    _check(_lib().ssht_forward(h, f_ptr, flm_ptr, stream), "ssht_forward")
+
+
+def ssht_adjoint(h, g_ptr, flm_ptr, stream=0):
+    _check(_lib().ssht_adjoint(h, g_ptr, flm_ptr, stream), "ssht_adjoint")
+
+
+def ssht_wigner_delta(h, out_ptr, stream=0):
+    _check(_lib().ssht_wigner_delta(h, out_ptr, stream), "ssht_wigner_delta")
+
+
+def ssht_plan_check(h):
+    _check(_lib().ssht_plan_check(h), "ssht_plan_check")
+
+
+def ssht_plan_profile(h, enable):
+    _check(_lib().ssht_plan_profile(h, int(bool(enable))), "ssht_plan_profile")
+
+
+def ssht_plan_profile_read(h):
+    """Returns ({stage: (ms, count)}, launches) since profiling was enabled."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    launches = ctypes.c_longlong()
+    _check(_lib().ssht_plan_profile_read(h, ms, cnt, n, ctypes.byref(launches)), "ssht_plan_profile_read")
+    return {name: (ms[k], cnt[k]) for k, name in enumerate(STAGES)}, launches.value
+
+
+def ssht_plan_workspace_bytes(h):
+    n = ctypes.c_size_t()
+    _check(_lib().ssht_plan_workspace_bytes(h, ctypes.byref(n)), "ssht_plan_workspace_bytes")
+    return n.value
+
+
+def ssht_last_error():
+    return _lib().ssht_last_error().decode()
+
+
+def ssht_version():
+    return _lib().ssht_version()
+
+
+# ---- torch-facing plan --------------------------------------------------------------------
+
+class Plan:
+    """A transform plan for ``batch`` fields of band-limit ``L`` (exclusive) and spin ``s``.
+
+    Tensors: coefficients ``[batch, L*L]``, samples ``[batch, L, 2L-1]`` (complex128 for
+    precision ``fp64``, complex64 otherwise), on the plan's CUDA device or on the host.
+    """
+
+    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute"):
+        self.L, self.s, self.batch = int(L), int(s), int(batch)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.delta_mode = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
+        self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            ssht_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def N(self):
+        return 2 * self.L - 1
+
+    def coeff_shape(self):
+        return (self.batch, self.L * self.L)
+
+    def grid_shape(self):
+        return (self.batch, self.L, self.N)
+
+    def _arg(self, t, shape, name):
+        if t.dtype != self.dtype:
+            raise TypeError("%s must be %s, got %s" % (name, self.dtype, t.dtype))
+        if tuple(t.shape) != shape and not (self.batch == 1 and tuple(t.shape) == shape[1:]):
+            raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.is_cuda and t.device != self.device:
+            raise ValueError("%s is on %s, the plan on %s" % (name, t.device, self.device))
+        return t.data_ptr()
+
+    def _out(self, out, ref, ref_shape, shape):
+        if out is None:
+            batched = ref.dim() == len(ref_shape)
+            out = torch.empty(shape if batched else shape[1:], dtype=self.dtype, device=ref.device)
+        return out
+
+    @staticmethod
+    def _stream(stream, t):
+        if stream is not None:
+            return int(stream)
+        return torch.cuda.current_stream().cuda_stream if t.is_cuda else 0
+
+    def inverse(self, flm, out=None, stream=None):
+        out = self._out(out, flm, self.coeff_shape(), self.grid_shape())
+        ssht_inverse(self._h, self._arg(flm, self.coeff_shape(), "flm"), self._arg(out, self.grid_shape(), "f"),
+                     self._stream(stream, flm))
+        return out
+
+    def forward(self, f, out=None, stream=None):
+        out = self._out(out, f, self.grid_shape(), self.coeff_shape())
+        ssht_forward(self._h, self._arg(f, self.grid_shape(), "f"), self._arg(out, self.coeff_shape(), "flm"),
+                     self._stream(stream, f))
+        return out
+
+    def adjoint(self, g, out=None, stream=None):
+        out = self._out(out, g, self.grid_shape(), self.coeff_shape())
+        ssht_adjoint(self._h, self._arg(g, self.grid_shape(), "g"), self._arg(out, self.coeff_shape(), "flm"),
+                     self._stream(stream, g))
+        return out
+
+    def wigner_delta(self, out=None, stream=None):
+        n = self.L * (self.L + 1) * (2 * self.L + 1) // 6
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=self.device)
+        if out.dtype != torch.float64 or out.numel() != n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of %d elements" % n)
+        ssht_wigner_delta(self._h, out.data_ptr(), self._stream(stream, out))
+        return out
+
+    def check(self):
+        ssht_plan_check(self._h)
+
+    def workspace_bytes(self):
+        return ssht_plan_workspace_bytes(self._h)
+
+    def profile(self, enable=True):
+        ssht_plan_profile(self._h, enable)
+
+    def profile_read(self):
+        return ssht_plan_profile_read(self._h)
+
+
+class InverseFunction(torch.autograd.Function):
+    """Differentiable inverse transform; the backward pass is ssht_adjoint (A^H of the linear map),
+    which recomputes Delta^l instead of storing anything from the forward pass."""
+
+    @staticmethod
+    def forward(ctx, flm, plan):
+        ctx.plan = plan
+        return plan.inverse(flm.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_f):
+        return ctx.plan.adjoint(grad_f.contiguous()), None
+
+
+def inverse(flm, plan):
+    """Inverse transform with autograd support."""
+    return InverseFunction.apply(flm, plan)
