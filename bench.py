@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark: spin SHT transforms/s (forward + inverse) at L = 1024, s = 2, B = 64 fields.
+
+One step = one inverse transform of B fields (coefficients -> the L x (2L-1) sphere grid) followed
+by one forward transform of that grid (-> coefficients), through the C ABI of libssht on inputs
+already resident in HBM (each field's coefficients are larger than nothing fits in L2: the batch
+is 0.5 GB of coefficients and 1.1 GB of samples, so every step streams from HBM).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ssht|reference]
+
+Under torchrun (N > 1) every rank transforms its own B fields (weak scaling, no collective on
+the data path); the time is the maximum over ranks.  Rank 0 prints one JSON line.
+``--impl reference`` times the CPU oracle (the plain FP64 implementation under oracle/) on the
+host cores, one field of the same workload per step, on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin SHT transforms/s (fwd+inv) at L=1024 s=2 B=64; rel err vs FP64 oracle"
+DEFAULT_L, DEFAULT_S, DEFAULT_B = 1024, 2, 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ssht", choices=["ssht", "reference"])
+    ap.add_argument("--L", type=int, default=DEFAULT_L)
+    ap.add_argument("--s", type=int, default=DEFAULT_S)
+    ap.add_argument("--batch", type=int, default=DEFAULT_B)
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--delta-mode", default="recompute", choices=["recompute", "cache"])
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cache-line", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed helpers
+# ---------------------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier(device_ids=[device.index] if device is not None and device.type == "cuda" else None)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------------------------
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, bf16, src = 6800.0, 1900.0, "fallback"
+    if os.path.exists(path):
+        j = json.load(open(path))
+        hbm, bf16, src = float(j.get("hbm_gbs", hbm)), float(j.get("bf16_tflops", bf16)), "measured"
+    sms, clk = 152, 2.07e9
+    return {
+        "hbm_gbs": (hbm, src),
+        "bf16_tflops": (bf16, src),
+        # Not in MEASURED_PEAKS.json: derived from unit counts and the maximum SM clock.
+        "fp64_tflops": (sms * 2 * 2 * clk / 1e12, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"),
+        "fp32_tflops": (sms * 128 * 2 * clk / 1e12, "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+        "tf32_tflops": (bf16 / 2.0, src + " bf16 x nominal tf32/bf16 ratio 1/2"),
+    }
+
+
+def contraction_macs(L, s):
+    """Complex x real multiply-adds of one field and one direction: sum_{l>=|s|} (2l+1)(l+1)."""
+    l = np.arange(abs(s), L, dtype=np.float64)
+    return float(np.sum((2 * l + 1) * (l + 1)))
+
+
+def recursion_updates(L):
+    """Element updates of one octant Risbo sweep: half slabs (l+1)(l+4)/2 and integer slabs
+    (l+2)(l+3)/2 for l = 0 .. L-2."""
+    l = np.arange(0, max(L - 1, 0), dtype=np.float64)
+    return float(np.sum((l + 1) * (l + 4) / 2 + (l + 2) * (l + 3) / 2))
+
+
+def source_hash(*files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, files):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        j = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not j or j.get("source_hash") != source_hash(*files):
+        return None
+    return j.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------------------------
+# the ssht arm
+# ---------------------------------------------------------------------------------------------
+
+def run_ssht(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0807_4494_gb300 import inputs, ssht
+
+    L, s, B = args.L, args.s, args.batch
+    prec = args.precision
+    if prec == "auto":
+        prec = "fp32"
+    plan = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode)
+    cdt = plan.dtype
+    flm_np = inputs.coeffs(L, s, B, seed=rank * B, spectrum="cmb")
+    flm = torch.from_numpy(flm_np).to(cdt).to(device)
+    grid = torch.empty(plan.grid_shape(), dtype=cdt, device=device)
+    back = torch.empty(plan.coeff_shape(), dtype=cdt, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.inverse(flm, out=grid)
+        plan.forward(grid, out=back)
+
+    sampler = ClockSampler(device.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    plan.profile(True)
+    _, launches0 = plan.profile_read()
+    barrier(world, device)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, device)
+    ms_local = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    stages, launches1 = plan.profile_read()
+    plan.profile(False)
+    plan.check()
+    ms = max_over_ranks(ms_local, world, device)
+    value = world * B * args.steps / (ms / 1e3)
+    ms_step = ms / args.steps
+
+    # roundtrip error over the whole batch, and the oracle check on sampled fields
+    rt = float((back - flm).abs().max() / flm.abs().max())
+    check = None
+    if rank == 0 and not args.no_check:
+        from oracle import transforms as T
+        fields = sorted({0, B - 1})
+        g = grid.cpu().numpy()
+        b_out = back.cpu().numpy()
+        e_inv, e_fwd = 0.0, 0.0
+        for b in fields:
+            f_or = T.inverse(flm_np[b], L, s)
+            e_inv = max(e_inv, float(np.abs(g[b] - f_or).max() / np.abs(f_or).max()))
+            fw_or = T.forward(g[b].astype(np.complex128), L, s)
+            e_fwd = max(e_fwd, float(np.abs(b_out[b] - fw_or).max() / np.abs(fw_or).max()))
+        check = {"inverse": e_inv, "forward": e_fwd, "roundtrip": rt, "fields_checked": fields,
+                 "measure": "max|x - oracle| / max|oracle|"}
+
+    # roofline of the dominant kernel of this library (cuFFT is excluded: library code)
+    pk = peaks()
+    own = {k: v for k, v in stages.items() if k != "fft" and v[1] > 0}
+    dom = max(own, key=lambda k: own[k][0]) if own else None
+    roof = None
+    if dom:
+        ms_d, n_d = own[dom]
+        per_launch_s = ms_d / n_d / 1e3
+        if dom == "delta":
+            flops = 10.0 * recursion_updates(L)
+            ach = flops / per_launch_s / 1e12
+            peak, src = pk["fp64_tflops"]
+            roof = {"bound": "alu", "kernel": "risbo_kernel (FP64)", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                    "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
+                    "work_per_launch": "%.3g flops = 10 x %.3g octant updates" % (flops, recursion_updates(L))}
+        elif dom in ("inverse", "project"):
+            flops = 4.0 * B * contraction_macs(L, s)
+            ach = flops / per_launch_s / 1e12
+            key = "fp64_tflops" if prec == "fp64" else "fp32_tflops"
+            peak, src = pk[key]
+            roof = {"bound": "alu", "kernel": dom + " contraction (SIMT " + prec + ")", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                    "traffic": None,
+                    "work_per_launch": "%.3g flops = 4 x B x %.3g MACs" % (flops, contraction_macs(L, s))}
+        else:
+            roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": pk["hbm_gbs"][0], "unit": "GB/s",
+                    "frac": None, "traffic": None}
+    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1] > 0}
+
+    # end to end through the C ABI with host buffers: H2D of the coefficients, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
+        h_in.copy_(flm.cpu())
+        h_out = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
+
+        def step_host():
+            plan.inverse(h_in, out=grid)        # host -> device inside the call
+            plan.forward(grid, out=h_out)       # device -> host inside the call
+        for _ in range(max(1, args.warmup)):
+            step_host()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        nrep = max(3, args.steps // 5)
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            step_host()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        el = max_over_ranks(time.perf_counter() - t0, world, device)
+        nbytes = B * L * L * h_in.element_size()
+        e2e = {"value": world * B * nrep / el, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": nrep}
+
+    # the plan-time Delta cache (the paper's timing protocol: precomputed Delta in memory)
+    cache_line = None
+    if not args.no_cache_line and args.delta_mode == "recompute":
+        t0 = time.perf_counter()
+        cplan = ssht.Plan(L, s, B, precision=prec, delta_mode="cache")
+        build_s = time.perf_counter() - t0
+
+        def cstep():
+            cplan.inverse(flm, out=grid)
+            cplan.forward(grid, out=back)
+        for _ in range(args.warmup):
+            cstep()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            cstep()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = max_over_ranks(c0.elapsed_time(c1), world, device)
+        cache_line = {"value": world * B * args.steps / (cms / 1e3), "unit": "transforms/s",
+                      "ms_per_step": cms / args.steps, "plan_build_s": build_s}
+        cplan.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(L, s, flm_np[0])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec) + " (Delta recursion f64)",
+            "data": "synthetic: sf_lm ~ CN(0, 1/(l+1)^2) (Re, Im each N(0, 1/(2(l+1)^2))), seeds rank*B .. rank*B+B-1",
+            "config": {"workload": "L=%d s=%d B=%d fwd+inv per step" % (L, s, B), "L": L, "s": s, "batch": B,
+                       "precision": prec, "delta_mode": args.delta_mode, "parallelism": "dp%d (independent fields)" % world,
+                       "l2": "inputs larger than L2 (%.2f GB of coefficients, %.2f GB of samples per step)" % (
+                           flm.numel() * flm.element_size() / 1e9, grid.numel() * grid.element_size() / 1e9)},
+            "rel_err": check,
+            "roofline": roof,
+            "stage_ms_per_step": stage_ms,
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": int(launches1 - launches0),
+            "delta_cache": cache_line,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(L, s, flm1):
+    """The oracle, as it stands, on the host cores: one field of the workload, inverse + forward."""
+    from oracle import transforms as T
+    t0 = time.perf_counter()
+    f = T.inverse(flm1, L, s)
+    T.forward(f, L, s)
+    el = time.perf_counter() - t0
+    return {"value": 1.0 / el, "unit": "transforms/s", "cores": T.num_threads(), "kind": "oracle",
+            "sample": "1 field of the L=%d s=%d workload (field 0), inverse + forward, FP64, %.1f s" % (L, s, el)}
+
+
+# ---------------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import _lib
+    from oracle import transforms as T
+    from paper_0807_4494_gb300 import inputs
+    _lib.build()
+    L, s = args.L, args.s
+    flm = inputs.coeffs(L, s, 1, seed=0, spectrum="cmb")[0]
+
+    def step():
+        f = T.inverse(flm, L, s)
+        T.forward(f, L, s)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: field 0 of the workload",
+        "config": {"workload": "L=%d s=%d B=%d fwd+inv per step" % (L, s, args.batch), "L": L, "s": s,
+                   "batch": args.batch, "sample": "1 field per step"},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "kind": "oracle", "cores": T.num_threads(),
+                         "sample": "1 field of the workload per step (inverse + forward), FP64 C/OpenMP + numpy.fft"},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ssht(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -16,11 +16,14 @@
 //
 // Parallel layout.  One cooperative persistent grid walks l.  For the step l -> l+1 the
 // rows of the new integer slab are split over the CTAs by equal entry counts.  A CTA that
-// owns integer rows [r0, r1) first computes the half-integer rows [r0-1, r1-1] it needs
-// (one row is also computed by its neighbour) into shared memory, then its integer rows,
-// which it writes to the next octant buffer and, in both orientations, to the quadrant
-// table.  So each degree costs one grid barrier.  The barrier spins at most one second,
-// then latches a status bit and every CTA leaves the kernel.
+// owns integer rows [r0, r1) works through them in chunks [c0, c1) sized to its shared
+// memory: it copies the contiguous packed integer rows [c0-1, c1] of degree l from global
+// memory into shared memory (coalesced), computes from them the half-integer rows
+// [c0-1, c1-1] (one row is also computed by the neighbouring chunk), then the integer rows
+// [c0, c1), which it writes to the next octant buffer and, in both orientations, to the
+// quadrant table.  So each degree costs one grid barrier, and the four operands of every
+// update come from shared memory.  The barrier spins at most one second, then latches a
+// status bit and every CTA leaves the kernel.
 #include "ssht_internal.h"
 
 #include <algorithm>
@@ -118,8 +121,9 @@ __host__ __device__ __forceinline__ void cta_rows(int lp, int cta, int nb, int* 
   *r1 = share_row(S * (cta + 1) / nb, lp + 1);
 }
 
-// Integer slab of degree l, any (m, n) with 0 <= m <= l+1 and -1 <= n <= m+1.
-__device__ __forceinline__ double yget(const double* __restrict__ Y, int l, int m, int n) {
+// Integer slab of degree l staged in shared memory from row ybase on (packed rows), any (m, n)
+// with 0 <= m <= l+1 and -1 <= n <= m+1.
+__device__ __forceinline__ double yget(const double* __restrict__ Y, int l, long long ybase, int m, int n) {
   double sg = 1.0;
   if (n == -1) {
     if (m == 0) {  // Delta_{0,-1} = (-1)^l Delta_{0,1} = (-1)^{l+1} Delta_{1,0}
@@ -136,7 +140,7 @@ __device__ __forceinline__ double yget(const double* __restrict__ Y, int l, int 
     const int t = m; m = n; n = t;
   }
   if (m > l) return 0.0;
-  return sg * Y[tri_ll(m) + n];
+  return sg * Y[tri_ll(m) + n - ybase];
 }
 
 // Half-integer slab of degree l+1/2 held in shared memory from row Alo on,
@@ -159,8 +163,17 @@ __device__ __forceinline__ double xget(const double* __restrict__ X, int l, long
   return sg * X[hoff_ll(A) + B - hbase];
 }
 
-__global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P) {
-  extern __shared__ double hs[];
+// Shared-memory doubles needed to produce integer rows [c0, c1) of degree l+1 from degree l:
+// the staged integer rows [Alo, min(Ahi+1, l)] and the half rows [Alo, Ahi].
+__host__ __device__ __forceinline__ long long chunk_need(int l, int c0, int c1) {
+  const int Alo = c0 > 0 ? c0 - 1 : 0;
+  const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;
+  const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l;
+  return (tri_ll(Ytop + 1) - tri_ll(Alo)) + (hoff_ll(Ahi + 1) - hoff_ll(Alo));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long long cap) {
+  extern __shared__ double smem[];
   const int nb = gridDim.x;
   const int cta = blockIdx.x;
   if (cta == 0 && threadIdx.x == 0) {
@@ -170,42 +183,53 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P) {
   unsigned int phase = 1;
   if (!grid_barrier(P.counter, phase * nb, P.status)) return;
   for (int l = 0; l + 1 < P.L; ++l) {
-    const double* __restrict__ Y = (l & 1) ? P.slab1 : P.slab0;
+    const double* __restrict__ Yg = (l & 1) ? P.slab1 : P.slab0;
     double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
     const int lp = l + 1;
     int r0, r1;
     cta_rows(lp, cta, nb, &r0, &r1);
-    if (r0 < r1) {
-      const int Alo = r0 > 0 ? r0 - 1 : 0;
-      const int Ahi = (r1 - 1 < l) ? r1 - 1 : l;
+    const double sc = 0.70710678118654752440 / (double)(2 * l + 1);
+    const double sc2 = 0.70710678118654752440 / (double)(2 * lp);
+    double* __restrict__ T = P.table + (size_t)((long long)lp * (lp + 1) * (2 * lp + 1) / 6);
+    for (int c0 = r0; c0 < r1;) {
+      int c1 = c0 + 1;
+      while (c1 < r1 && chunk_need(l, c0, c1 + 1) <= cap) ++c1;
+      const int Alo = c0 > 0 ? c0 - 1 : 0;
+      const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;
+      const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l;
+      const long long ybase = tri_ll(Alo);
+      const int ycount = (int)(tri_ll(Ytop + 1) - ybase);
       const long long hbase = hoff_ll(Alo);
       const int hcount = (int)(hoff_ll(Ahi + 1) - hbase);
+      double* __restrict__ Ys = smem;
+      double* __restrict__ Xs = smem + ycount;
+      __syncthreads();  // the previous chunk is done with shared memory
+      // Stage the contiguous packed rows [Alo, Ytop] of the integer slab.
+      for (int i = threadIdx.x; i < ycount; i += blockDim.x) Ys[i] = Yg[ybase + i];
+      __syncthreads();
       // Half step l -> l + 1/2 (2j = 2l + 1).  j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.
-      const double sc = 0.70710678118654752440 / (double)(2 * l + 1);
       for (int i = threadIdx.x; i < hcount; i += blockDim.x) {
         const int A = hoff_row(hbase + i);
         const int B = (int)(hbase + i - hoff_ll(A));
-        const double x1 = yget(Y, l, A, B - 1);
-        const double x2 = yget(Y, l, A, B);
-        const double x3 = yget(Y, l, A + 1, B - 1);
-        const double x4 = yget(Y, l, A + 1, B);
+        const double x1 = yget(Ys, l, ybase, A, B - 1);
+        const double x2 = yget(Ys, l, ybase, A, B);
+        const double x3 = yget(Ys, l, ybase, A + 1, B - 1);
+        const double x4 = yget(Ys, l, ybase, A + 1, B);
         const double sb = P.sq[l + B], smb = P.sq[l + 1 - B];
         const double t1 = fma(-smb, x2, sb * x1);
         const double t2 = fma(smb, x4, sb * x3);
-        hs[i] = fma(P.sq[l + A + 1], t1, P.sq[l - A] * t2) * sc;
+        Xs[i] = fma(P.sq[l + A + 1], t1, P.sq[l - A] * t2) * sc;
       }
       __syncthreads();
       // Integer step l + 1/2 -> lp (2j = 2 lp).
-      const double sc2 = 0.70710678118654752440 / (double)(2 * lp);
-      double* __restrict__ T = P.table + (size_t)((long long)lp * (lp + 1) * (2 * lp + 1) / 6);
-      const long long e0 = tri_ll(r0), e1 = tri_ll(r1);
+      const long long e0 = tri_ll(c0), e1 = tri_ll(c1);
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int m = tri_row(e);
         const int n = (int)(e - tri_ll(m));
-        const double x1 = xget(hs, l, hbase, m - 1, n);
-        const double x2 = xget(hs, l, hbase, m - 1, n + 1);
-        const double x3 = xget(hs, l, hbase, m, n);
-        const double x4 = xget(hs, l, hbase, m, n + 1);
+        const double x1 = xget(Xs, l, hbase, m - 1, n);
+        const double x2 = xget(Xs, l, hbase, m - 1, n + 1);
+        const double x3 = xget(Xs, l, hbase, m, n);
+        const double x4 = xget(Xs, l, hbase, m, n + 1);
         const double sb = P.sq[lp + n], smb = P.sq[lp - n];
         const double t1 = fma(-smb, x2, sb * x1);
         const double t2 = fma(smb, x4, sb * x3);
@@ -214,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P) {
         T[(size_t)m * (lp + 1) + n] = v;
         if (n != m) T[(size_t)n * (lp + 1) + m] = ((m - n) & 1) ? -v : v;
       }
+      c0 = c1;
     }
     ++phase;
     if (!grid_barrier(P.counter, phase * nb, P.status)) return;
@@ -242,22 +267,6 @@ __global__ void spin_column_kernel(const double* __restrict__ table, int L, int 
 
 }  // namespace
 
-static size_t risbo_smem_doubles(int L, int nb) {
-  long long best = 1;
-  for (int l = 0; l + 1 < L; ++l) {
-    const int lp = l + 1;
-    for (int c = 0; c < nb; ++c) {
-      int r0, r1;
-      cta_rows(lp, c, nb, &r0, &r1);
-      if (r0 >= r1) continue;
-      const int Alo = r0 > 0 ? r0 - 1 : 0;
-      const int Ahi = std::min(r1 - 1, l);
-      best = std::max(best, hoff_ll(Ahi + 1) - hoff_ll(Alo));
-    }
-  }
-  return (size_t)best;
-}
-
 cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   cudaError_t e;
   int sms = 0, per_sm = 0, smem_optin = 0;
@@ -265,8 +274,12 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) return e;
   w.threads = kThreads;
   w.blocks = sms;  // one CTA per SM
-  w.smem = risbo_smem_doubles(L, w.blocks) * sizeof(double);
-  if ((int)w.smem > smem_optin) return cudaErrorInvalidValue;
+  // Shared memory: as much as one CTA per SM may take, leaving room for the static part.
+  w.smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
+  w.cap = (long long)(w.smem / sizeof(double));
+  // Every chunk holds at least one row: the widest single-row chunk (last degree) must fit.
+  for (int m = 0; m < L; ++m)
+    if (chunk_need(L - 2 > 0 ? L - 2 : 0, m, m + 1) > w.cap) return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
@@ -293,7 +306,8 @@ cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   P.sq = w.sqrt_tab;
   P.counter = w.barrier;
   P.status = w.status;
-  void* args[] = {&P};
+  long long cap = w.cap;
+  void* args[] = {&P, &cap};
   return cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(w.blocks), dim3(w.threads), args, w.smem, st);
 }
 

@@ -38,6 +38,7 @@ struct DeltaWork {
   int blocks = 0;                 // cooperative grid size
   int threads = 0;
   size_t smem = 0;
+  long long cap = 0;  // shared-memory doubles per CTA
 };
 
 cudaError_t delta_setup(DeltaWork& w, int L, int device);
