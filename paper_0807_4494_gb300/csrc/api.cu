@@ -18,6 +18,8 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+
+
 const char* cufft_name(cufftResult r) {
   switch (r) {
     case CUFFT_SUCCESS: return "CUFFT_SUCCESS";

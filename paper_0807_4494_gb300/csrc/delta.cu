@@ -33,7 +33,16 @@
 namespace ssht {
 namespace {
 
-constexpr int kThreads = 512;
+#ifndef SSHT_RISBO_THREADS
+#define SSHT_RISBO_THREADS 512
+#endif
+#ifndef SSHT_RISBO_UNROLL
+#define SSHT_RISBO_UNROLL 1
+#endif
+#ifndef SSHT_RISBO_MARK
+#define SSHT_RISBO_MARK(k)  // phase boundary: 1 prologue, 2 staged, 3 half step, 4 integer step, 5 barrier
+#endif
+constexpr int kThreads = SSHT_RISBO_THREADS;
 
 struct RisboParams {
   int L;
@@ -57,8 +66,10 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   return v;
 }
 
-// Grid barrier with a one-second spin limit.  Returns false if this CTA must stop.
-__device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status) {
+// Grid barrier with a one-second spin limit.  Returns false if this CTA must stop.  While
+// thread 0 waits, thread 32 (another warp) runs `side()`.
+template <typename Side>
+__device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status, Side side) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -80,6 +91,8 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* st
     }
     __threadfence();
     ok = good;
+  } else if (threadIdx.x == 32) {
+    side();
   }
   __syncthreads();
   return ok != 0;
@@ -105,62 +118,74 @@ __device__ __forceinline__ int hoff_row(long long i) {
   return A;
 }
 
-// Smallest m with tri(m) >= x (row where the CTA's share starts).
+// Work of integer rows [0, m) of a step, half rows included: row m costs (m+1) integer and
+// (m+2) half-integer updates, so C(m) = sum_{k<m} (2k+3) = m^2 + 2m.
+__host__ __device__ __forceinline__ long long row_cost(long long m) { return m * m + 2 * m; }
+
+// Smallest m with C(m) >= x.  FP32 first guess, exact integer correction (FP64 arithmetic is
+// costly on this part and is kept for the recursion itself).
 __host__ __device__ __forceinline__ int share_row(long long x, int rows) {
-  int m = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  int m = (int)(sqrtf(1.0f + (float)x) - 1.0f);
   if (m < 0) m = 0;
   if (m > rows) m = rows;
-  while (m > 0 && tri_ll(m - 1) >= x) --m;
-  while (m < rows && tri_ll(m) < x) ++m;
+  while (m > 0 && row_cost(m - 1) >= x) --m;
+  while (m < rows && row_cost(m) < x) ++m;
   return m;
 }
 
+// Rows [r0, r1) of the new integer slab of degree lp owned by CTA cta of nb, balanced on C.
 __host__ __device__ __forceinline__ void cta_rows(int lp, int cta, int nb, int* r0, int* r1) {
-  const long long S = tri_ll(lp + 1);
+  const long long S = row_cost(lp + 1);
   *r0 = share_row(S * cta / nb, lp + 1);
   *r1 = share_row(S * (cta + 1) / nb, lp + 1);
+}
+
+// v with its sign flipped when neg is set, by integer ops on the sign bit (a multiplication by
+// -1 would cost an FP64 instruction).
+__device__ __forceinline__ double flip(double v, bool neg) {
+  return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
 }
 
 // Integer slab of degree l staged in shared memory from row ybase on (packed rows), any (m, n)
 // with 0 <= m <= l+1 and -1 <= n <= m+1.
 __device__ __forceinline__ double yget(const double* __restrict__ Y, int l, long long ybase, int m, int n) {
-  double sg = 1.0;
+  bool neg = false;
   if (n == -1) {
     if (m == 0) {  // Delta_{0,-1} = (-1)^l Delta_{0,1} = (-1)^{l+1} Delta_{1,0}
-      sg = (l & 1) ? 1.0 : -1.0;
+      neg = (l & 1) == 0;
       m = 1;
       n = 0;
     } else {       // Delta_{m,-1} = (-1)^{l+m} Delta_{m,1}
-      sg = ((l + m) & 1) ? -1.0 : 1.0;
+      neg = ((l + m) & 1) != 0;
       n = 1;
     }
   }
   if (n > m) {     // transpose
-    if ((n - m) & 1) sg = -sg;
+    if ((n - m) & 1) neg = !neg;
     const int t = m; m = n; n = t;
   }
   if (m > l) return 0.0;
-  return sg * Y[tri_ll(m) + n - ybase];
+  return flip(Y[tri_ll(m) + n - ybase], neg);
 }
 
 // Half-integer slab of degree l+1/2 held in shared memory from row Alo on,
 // any (A, B) with -1 <= A <= l+1 and 0 <= B <= A+2.
 __device__ __forceinline__ double xget(const double* __restrict__ X, int l, long long hbase, int A, int B) {
-  double sg = 1.0;
+  bool neg = false;
   if (A == -1) {   // a = -1/2
     if (B == 0) {  // (-1/2,-1/2) = (1/2,1/2)
       A = 0; B = 1;
     } else {       // (-1/2,1/2) = -(1/2,-1/2)
-      A = 0; B = 0; sg = -1.0;
+      A = 0; B = 0; neg = true;
     }
   }
   if (B > A + 1) { // b > a: transpose (a,b) -> (b,a), sign (-1)^{a-b}
-    if ((B - A - 1) & 1) sg = -sg;
+    if ((B - A - 1) & 1) neg = !neg;
     const int nA = B - 1, nB = A + 1;
     A = nA; B = nB;
   }
   if (A > l) return 0.0;
-  return sg * X[hoff_ll(A) + B - hbase];
+  return flip(X[hoff_ll(A) + B - hbase], neg);
 }
 
 // Shared-memory doubles needed to produce integer rows [c0, c1) of degree l+1 from degree l:
@@ -172,8 +197,30 @@ __host__ __device__ __forceinline__ long long chunk_need(int l, int c0, int c1) 
   return (tri_ll(Ytop + 1) - tri_ll(Alo)) + (hoff_ll(Ahi + 1) - hoff_ll(Alo));
 }
 
+// 1/k to FP64 accuracy without an FP64 division: FP32 reciprocal, then two Newton steps.
+__device__ __forceinline__ double recip(double k) {
+  double r = (double)(1.0f / (float)k);
+  r = r * fma(-k, r, 2.0);
+  r = r * fma(-k, r, 2.0);
+  return r;
+}
+
+constexpr int kUnroll = SSHT_RISBO_UNROLL;  // independent updates in flight per thread
+constexpr int kRowCap = 512; // rows of pre-scaled row factors kept per chunk
+
 __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long long cap) {
   extern __shared__ double smem[];
+  __shared__ int s_rows[2];
+  __shared__ double s_scale[2];
+  // Rows and step scales p/(2j) of step l -> l + 1, computed while the previous barrier waits.
+  auto params = [&](int l) {
+    const int lp = l + 1;
+    cta_rows(lp, blockIdx.x, gridDim.x, &s_rows[0], &s_rows[1]);
+    s_scale[0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
+    s_scale[1] = 0.70710678118654752440 * recip((double)(2 * lp));
+  };
+  // row factors sqrt(j+a) p/(2j), sqrt(j-a) p/(2j) of the half step (s_ra, s_rb) and the integer step
+  __shared__ double s_ra[kRowCap + 2], s_rb[kRowCap + 2], s_ia[kRowCap + 2], s_ib[kRowCap + 2];
   const int nb = gridDim.x;
   const int cta = blockIdx.x;
   if (cta == 0 && threadIdx.x == 0) {
@@ -181,19 +228,23 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
     P.table[0] = 1.0;
   }
   unsigned int phase = 1;
-  if (!grid_barrier(P.counter, phase * nb, P.status)) return;
+  if (!grid_barrier(P.counter, phase * nb, P.status, [&] { params(0); })) return;
   for (int l = 0; l + 1 < P.L; ++l) {
     const double* __restrict__ Yg = (l & 1) ? P.slab1 : P.slab0;
     double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
     const int lp = l + 1;
-    int r0, r1;
-    cta_rows(lp, cta, nb, &r0, &r1);
-    const double sc = 0.70710678118654752440 / (double)(2 * l + 1);
-    const double sc2 = 0.70710678118654752440 / (double)(2 * lp);
+    const int r0 = s_rows[0], r1 = s_rows[1];
+    const double sc = s_scale[0], sc2 = s_scale[1];
+    SSHT_RISBO_MARK(1);
     double* __restrict__ T = P.table + (size_t)((long long)lp * (lp + 1) * (2 * lp + 1) / 6);
     for (int c0 = r0; c0 < r1;) {
-      int c1 = c0 + 1;
-      while (c1 < r1 && chunk_need(l, c0, c1 + 1) <= cap) ++c1;
+      // Largest c1 <= min(r1, c0 + kRowCap) whose chunk fits (chunk_need grows with c1).
+      int lo = c0 + 1, hi = (r1 < c0 + kRowCap) ? r1 : c0 + kRowCap;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunk_need(l, c0, mid) <= cap) lo = mid; else hi = mid - 1;
+      }
+      const int c1 = lo;
       const int Alo = c0 > 0 ? c0 - 1 : 0;
       const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;
       const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l;
@@ -204,44 +255,95 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
       double* __restrict__ Ys = smem;
       double* __restrict__ Xs = smem + ycount;
       __syncthreads();  // the previous chunk is done with shared memory
-      // Stage the contiguous packed rows [Alo, Ytop] of the integer slab.
-      for (int i = threadIdx.x; i < ycount; i += blockDim.x) Ys[i] = Yg[ybase + i];
+      // Stage the contiguous packed rows [Alo, Ytop] of the integer slab (asynchronous copies,
+      // all in flight together); pre-scale the row factors meanwhile.
+      for (int i = threadIdx.x; i < ycount; i += blockDim.x) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Ys + i);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(Yg + ybase + i) : "memory");
+      }
+      for (int A = Alo + (int)threadIdx.x; A <= Ahi; A += blockDim.x) {
+        s_ra[A - Alo] = P.sq[l + A + 1] * sc;  // j + a = l + A + 1
+        s_rb[A - Alo] = P.sq[l - A] * sc;      // j - a = l - A
+      }
+      for (int m = c0 + (int)threadIdx.x; m < c1; m += blockDim.x) {
+        s_ia[m - c0] = P.sq[lp + m] * sc2;
+        s_ib[m - c0] = P.sq[lp - m] * sc2;
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
-      // Half step l -> l + 1/2 (2j = 2l + 1).  j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.
-      for (int i = threadIdx.x; i < hcount; i += blockDim.x) {
-        const int A = hoff_row(hbase + i);
-        const int B = (int)(hbase + i - hoff_ll(A));
-        const double x1 = yget(Ys, l, ybase, A, B - 1);
-        const double x2 = yget(Ys, l, ybase, A, B);
-        const double x3 = yget(Ys, l, ybase, A + 1, B - 1);
-        const double x4 = yget(Ys, l, ybase, A + 1, B);
-        const double sb = P.sq[l + B], smb = P.sq[l + 1 - B];
-        const double t1 = fma(-smb, x2, sb * x1);
-        const double t2 = fma(smb, x4, sb * x3);
-        Xs[i] = fma(P.sq[l + A + 1], t1, P.sq[l - A] * t2) * sc;
+      SSHT_RISBO_MARK(2);
+      // Half step l -> l + 1/2 (2j = 2l + 1): j+b = l+B, j-b = l+1-B.
+      for (int base = threadIdx.x; base < hcount; base += kUnroll * blockDim.x) {
+        double x1[kUnroll], x2[kUnroll], x3[kUnroll], x4[kUnroll], sb[kUnroll], smb[kUnroll], ra[kUnroll], rb[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int i = base + u * blockDim.x;
+          const int ii = i < hcount ? i : hcount - 1;
+          const int A = hoff_row(hbase + ii);
+          const int B = (int)(hbase + ii - hoff_ll(A));
+          x1[u] = yget(Ys, l, ybase, A, B - 1);
+          x2[u] = yget(Ys, l, ybase, A, B);
+          x3[u] = yget(Ys, l, ybase, A + 1, B - 1);
+          x4[u] = yget(Ys, l, ybase, A + 1, B);
+          sb[u] = P.sq[l + B];
+          smb[u] = P.sq[l + 1 - B];
+          ra[u] = s_ra[A - Alo];
+          rb[u] = s_rb[A - Alo];
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int i = base + u * blockDim.x;
+          const double t1 = fma(-smb[u], x2[u], sb[u] * x1[u]);
+          const double t2 = fma(smb[u], x4[u], sb[u] * x3[u]);
+          const double v = fma(ra[u], t1, rb[u] * t2);
+          if (i < hcount) Xs[i] = v;
+        }
       }
       __syncthreads();
+      SSHT_RISBO_MARK(3);
       // Integer step l + 1/2 -> lp (2j = 2 lp).
-      const long long e0 = tri_ll(c0), e1 = tri_ll(c1);
-      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int m = tri_row(e);
-        const int n = (int)(e - tri_ll(m));
-        const double x1 = xget(Xs, l, hbase, m - 1, n);
-        const double x2 = xget(Xs, l, hbase, m - 1, n + 1);
-        const double x3 = xget(Xs, l, hbase, m, n);
-        const double x4 = xget(Xs, l, hbase, m, n + 1);
-        const double sb = P.sq[lp + n], smb = P.sq[lp - n];
-        const double t1 = fma(-smb, x2, sb * x1);
-        const double t2 = fma(smb, x4, sb * x3);
-        const double v = fma(P.sq[lp + m], t1, P.sq[lp - m] * t2) * sc2;
-        Yn[e] = v;
-        T[(size_t)m * (lp + 1) + n] = v;
-        if (n != m) T[(size_t)n * (lp + 1) + m] = ((m - n) & 1) ? -v : v;
+      const long long e0 = tri_ll(c0);
+      const int ecount = (int)(tri_ll(c1) - e0);
+      for (int base = threadIdx.x; base < ecount; base += kUnroll * blockDim.x) {
+        double x1[kUnroll], x2[kUnroll], x3[kUnroll], x4[kUnroll], sb[kUnroll], smb[kUnroll], ra[kUnroll], rb[kUnroll];
+        int mm[kUnroll], nn[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int i = base + u * blockDim.x;
+          const long long e = e0 + (i < ecount ? i : ecount - 1);
+          const int m = tri_row(e);
+          const int n = (int)(e - tri_ll(m));
+          mm[u] = m;
+          nn[u] = n;
+          x1[u] = xget(Xs, l, hbase, m - 1, n);
+          x2[u] = xget(Xs, l, hbase, m - 1, n + 1);
+          x3[u] = xget(Xs, l, hbase, m, n);
+          x4[u] = xget(Xs, l, hbase, m, n + 1);
+          sb[u] = P.sq[lp + n];
+          smb[u] = P.sq[lp - n];
+          ra[u] = s_ia[m - c0];
+          rb[u] = s_ib[m - c0];
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int i = base + u * blockDim.x;
+          const double t1 = fma(-smb[u], x2[u], sb[u] * x1[u]);
+          const double t2 = fma(smb[u], x4[u], sb[u] * x3[u]);
+          const double v = fma(ra[u], t1, rb[u] * t2);
+          if (i < ecount) {
+            const int m = mm[u], n = nn[u];
+            Yn[e0 + i] = v;
+            T[(size_t)m * (lp + 1) + n] = v;
+            if (n != m) T[(size_t)n * (lp + 1) + m] = flip(v, ((m - n) & 1) != 0);
+          }
+        }
       }
+      SSHT_RISBO_MARK(4);
       c0 = c1;
     }
     ++phase;
-    if (!grid_barrier(P.counter, phase * nb, P.status)) return;
+    if (!grid_barrier(P.counter, phase * nb, P.status, [&] { params(l + 1); })) return;
+    SSHT_RISBO_MARK(5);
   }
 }
 
