@@ -125,6 +125,22 @@ SSHT_API int ssht_adjoint(ssht_plan_t plan, const void* g, void* flm, void* stre
  * out: device or host buffer of L(L+1)(2L+1)/6 doubles. */
 SSHT_API int ssht_wigner_delta(ssht_plan_t plan, double* out, void* stream);
 
+/* The same Delta table as ssht_wigner_delta, for 1 <= L <= 512, computed without allocating
+ * any device memory (the paper has no counterpart; this is a service for callers that cannot
+ * allocate -- e.g. a host application that has reserved nearly all device memory for its own
+ * pool, or a latency-critical loop that must not pay for cudaMalloc and the synchronisation it
+ * can cause).  Needs no plan.  The recursion's scratch lives in a fixed array of about 2.1 MB
+ * that every GPU loading this library holds until the process exits.
+ * out: device buffer of L(L+1)(2L+1)/6 doubles, layout as in ssht_wigner_delta; the caller owns
+ * it.  L outside [1, 512] or a NULL out returns SSHT_EINVAL before any device work.
+ * The first call on a device sets that device up (looks up the address of the array and fills
+ * its square-root table) and should be made before any stream capture.  Asynchronous on
+ * `stream`.  All calls share the one array: calls whose work overlaps on the GPU (on different
+ * streams or devices' shared contexts) race and must be serialised by the caller.  If a grid
+ * barrier inside the recursion exceeds its one-second spin limit the table is left incomplete
+ * and out[0] (normally Delta^0_00 = 1) is set to NaN. */
+SSHT_API int ssht_wigner_delta_noalloc(int L, double* out, void* stream);
+
 /* Wait for the plan's outstanding work and report a latched kernel-side failure
  * (SSHT_ETIMEOUT) or a CUDA error; clears the latched status. */
 SSHT_API int ssht_plan_check(ssht_plan_t plan);

@@ -18,7 +18,13 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
 
+namespace ssht {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace ssht
+
+namespace {
 
 const char* cufft_name(cufftResult r) {
   switch (r) {

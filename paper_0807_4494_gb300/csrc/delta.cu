@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 namespace ssht {
@@ -421,3 +422,105 @@ cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cuda
 }
 
 }  // namespace ssht
+
+// ---------------------------------------------------------------------------------------------
+// Entry point that allocates no device memory (ssht_wigner_delta_noalloc).
+//
+// Some callers cannot call cudaMalloc: a host application may have reserved nearly all device
+// memory for its own pool before loading this library, or the caller may run in a latency-
+// critical loop where an allocation (and the device-wide synchronisation cudaMalloc/cudaFree
+// can cause) is not acceptable.  For them the recursion's scratch -- the two octant slabs, the
+// square-root table, the grid-barrier words and the status word -- lives in the file-scope
+// array below, sized for band-limits up to kNoAllocMaxL.  Every GPU that loads this library
+// holds the array (about 2.1 MB) until the process exits.
+// ---------------------------------------------------------------------------------------------
+namespace ssht {
+namespace {
+
+constexpr int kNoAllocMaxL = 512;
+// doubles: two octant slabs of tri(kNoAllocMaxL + 1) entries and the sqrt table (2L + 4 entries),
+// then 4 words for the barrier counter / abort flag and the status word.
+constexpr size_t kNoAllocSlab = (size_t)(kNoAllocMaxL + 1) * (kNoAllocMaxL + 2) / 2;
+constexpr size_t kNoAllocSqrt = 2 * (size_t)kNoAllocMaxL + 4;
+constexpr size_t kNoAllocDoubles = 2 * kNoAllocSlab + kNoAllocSqrt + 4;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+__global__ void noalloc_sqrt_kernel(double* sq, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) sq[k] = sqrt((double)k);
+}
+
+// Marks an incomplete table: a barrier timeout leaves NaN in out[0] (normally Delta^0_00 = 1).
+__global__ void noalloc_finish_kernel(const int* status, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *status != 0) out[0] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+std::mutex g_noalloc_mutex;
+
+struct NoAllocDevice {
+  double* base = nullptr;  // device address of g_noalloc_scratch on this device
+  bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kMaxDevices];
+
+}  // namespace
+}  // namespace ssht
+
+extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
+  using namespace ssht;
+  if (L < 1 || L > kNoAllocMaxL)
+    return set_last_error(SSHT_EINVAL, "ssht_wigner_delta_noalloc: L must be in [1, 512] (the size of its fixed scratch)");
+  if (!out) return set_last_error(SSHT_EINVAL, "ssht_wigner_delta_noalloc: null output");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: no usable current device");
+  cudaStream_t st = (cudaStream_t)stream;
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!d.ready) {
+    // Once per device, with that device current: the device address of the scratch array.
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess)
+      return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: cudaGetSymbolAddress failed");
+    d.base = (double*)p;
+    int sms = 0, smem_optin = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSHT_ECUDA;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return SSHT_ECUDA;
+    const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
+    if (cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return SSHT_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+      return SSHT_ECUDA;
+    double* sq = d.base + 2 * kNoAllocSlab;
+    noalloc_sqrt_kernel<<<(unsigned)((kNoAllocSqrt + 255) / 256), 256, 0, st>>>(sq, (int)kNoAllocSqrt);
+    if (cudaGetLastError() != cudaSuccess) return SSHT_ECUDA;
+    d.ready = true;
+  }
+  int sms = 0, smem_optin = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSHT_ECUDA;
+  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return SSHT_ECUDA;
+  const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
+  unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + kNoAllocSqrt);  // counter, abort, status
+  // The array keeps the previous call's contents: the barrier words and the status start at zero.
+  if (cudaMemsetAsync(words, 0, 4 * sizeof(double), st) != cudaSuccess) return SSHT_ECUDA;
+  RisboParams P;
+  P.L = L;
+  P.table = out;
+  P.slab0 = d.base;
+  P.slab1 = d.base + kNoAllocSlab;
+  P.sq = d.base + 2 * kNoAllocSlab;
+  P.counter = words;
+  P.status = (int*)(words + 2);
+  long long cap = (long long)(smem / sizeof(double));
+  void* args[] = {&P, &cap};
+  if (cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(sms), dim3(kThreads), args, smem, st) != cudaSuccess)
+    return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: recursion launch failed");
+  noalloc_finish_kernel<<<1, 32, 0, st>>>(P.status, out);
+  if (cudaGetLastError() != cudaSuccess) return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: launch failed");
+  return SSHT_OK;
+}

@@ -23,6 +23,9 @@ struct Dims {
   int M;   // length of the zero-padded weight convolution, >= 4L - 3
 };
 
+// Records the message returned by ssht_last_error() and returns code.
+int set_last_error(int code, const char* msg);
+
 inline size_t delta_offset(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
 inline size_t tri(long long l) { return (size_t)(l * (l + 1) / 2); }
 

@@ -20,7 +20,7 @@ ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", 
           -5: "SSHT_EUNSUPPORTED"}
 EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspace_bytes", "ssht_inverse",
            "ssht_forward", "ssht_adjoint", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
-           "ssht_plan_profile_read", "ssht_last_error", "ssht_version")
+           "ssht_plan_profile_read", "ssht_wigner_delta_noalloc", "ssht_last_error", "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
 
 
@@ -58,6 +58,7 @@ def _lib():
             "ssht_plan_profile": ([vp, i], i),
             "ssht_plan_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), i,
                                         ctypes.POINTER(ctypes.c_longlong)], i),
+            "ssht_wigner_delta_noalloc": ([i, vp, vp], i),
             "ssht_last_error": ([], ctypes.c_char_p),
             "ssht_version": ([], i),
         }
@@ -107,6 +108,13 @@ def ssht_adjoint(h, g_ptr, flm_ptr, stream=0):
 
 def ssht_wigner_delta(h, out_ptr, stream=0):
     _check(_lib().ssht_wigner_delta(h, out_ptr, stream), "ssht_wigner_delta")
+
+
+def ssht_wigner_delta_noalloc(L, out_ptr, stream=0):
+    """Delta table for L <= 512 without any device allocation (fixed scratch inside the library)."""
+    rc = _lib().ssht_wigner_delta_noalloc(int(L), out_ptr, stream)
+    if rc != 0:
+        raise SshtError(rc, "ssht_wigner_delta_noalloc")
 
 
 def ssht_plan_check(h):
