@@ -203,7 +203,7 @@ def run_ssht(args):
     L, s, B = args.L, args.s, args.batch
     prec = args.precision
     if prec == "auto":
-        prec = "fp32"
+        prec = "tf32x3" if B <= 64 else "fp32"
     plan = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode)
     cdt = plan.dtype
     flm_np = inputs.coeffs(L, s, B, seed=rank * B, spectrum="cmb")
@@ -277,6 +277,18 @@ def run_ssht(args):
                     "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
                     "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
                     "work_per_launch": "%.3g flops = 10 x %.3g octant updates" % (flops, recursion_updates(L))}
+        elif dom in ("inverse", "project") and prec in ("tf32x3",):
+            # useful flops (4 per complex x real MAC) and the issued 3xTF32 tensor flops
+            flops = 4.0 * B * contraction_macs(L, s)
+            ach = 3.0 * flops / per_launch_s / 1e12
+            peak, src = pk["tf32_tflops"]
+            roof = {"bound": "tensor", "kernel": "tc_gemm_kernel<%s> (tcgen05 kind::tf32, 3 products)" % (
+                        "true" if dom == "project" else "false"),
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                    "useful_tflops": flops / per_launch_s / 1e12,
+                    "traffic": traffic_for("tc_gemm_kernel", ["paper_0807_4494_gb300/csrc/contract_tc.cu"]),
+                    "work_per_launch": "%.3g useful flops = 4 x B x %.3g MACs; x3 issued (hi*hi, hi*lo, lo*hi)" % (
+                        flops, contraction_macs(L, s))}
         elif dom in ("inverse", "project"):
             flops = 4.0 * B * contraction_macs(L, s)
             ach = flops / per_launch_s / 1e12

@@ -101,6 +101,7 @@ struct ssht_plan_s {
   size_t stage_out_bytes = 0;
   bool delta_ready = false;
   size_t bytes = 0;
+  TcPlan* tc = nullptr;  // tensor-core contraction (precision SSHT_TF32X3)
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -200,11 +201,42 @@ int run_delta(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
+int pack_a(ssht_plan_t p, int forward, cudaStream_t st) {
+  StageScope sc(p, SSHT_STAGE_PACK, st);
+  int n = 0;
+  SSHT_CUDA(tc_pack_a(p->tc, forward, p->delta.table, p->U, st, &n), "tensor-core operand packing");
+  p->launches += n;
+  return 0;
+}
+
 int ensure_delta(ssht_plan_t p, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
   int rc = run_delta(p, st);
   if (rc) return rc;
   if (p->delta_mode == SSHT_DELTA_CACHE) p->delta_ready = true;
+  return 0;
+}
+
+// Delta (and, for the tensor-core path, the packed A operand of one direction) ready for a call.
+int ensure_operands(ssht_plan_t p, int forward, cudaStream_t st) {
+  if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
+  int rc = run_delta(p, st);
+  if (rc) return rc;
+  if (p->tc && (rc = pack_a(p, forward, st))) return rc;
+  return 0;
+}
+
+int tc_contract(ssht_plan_t p, int forward, const void* src, void* dst, cudaStream_t st) {
+  int n = 0;
+  {
+    StageScope sc(p, SSHT_STAGE_PACK, st);
+    SSHT_CUDA(tc_pack_data(p->tc, forward, src, st, &n), "tensor-core data packing");
+  }
+  {
+    StageScope sc(p, forward ? SSHT_STAGE_PROJECT : SSHT_STAGE_INVERSE, st);
+    SSHT_CUDA(tc_gemm(p->tc, forward, dst, p->ph, p->delta.status, st, &n), "tensor-core contraction");
+  }
+  p->launches += n;
   return 0;
 }
 
@@ -276,9 +308,11 @@ int io_end(ssht_plan_t p, const IO& io, cudaStream_t st) {
 template <typename T>
 int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = ensure_delta(p, st);
+  int rc = ensure_operands(p, 0, st);
   if (rc) return rc;
-  {
+  if (p->tc) {
+    if ((rc = tc_contract(p, 0, flm, p->W1, st))) return rc;
+  } else {
     StageScope sc(p, SSHT_STAGE_INVERSE, st);
     SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, st),
               "inverse contraction");
@@ -331,7 +365,8 @@ int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
     SSHT_CUDA(conv_to_project<T>(d, p->B, p->W3, p->W1, st), "weight convolution output");
     p->launches += 1;
   }
-  if ((rc = ensure_delta(p, st))) return rc;
+  if ((rc = ensure_operands(p, 1, st))) return rc;
+  if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
   {
     StageScope sc(p, SSHT_STAGE_PROJECT, st);
     SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "forward contraction");
@@ -350,7 +385,8 @@ int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
     SSHT_CUDA(adj_theta_fold<T>(d, p->s, p->B, p->W1, p->W2, p->ph, st), "adjoint fold");
     p->launches += 1;
   }
-  if ((rc = ensure_delta(p, st))) return rc;
+  if ((rc = ensure_operands(p, 1, st))) return rc;
+  if (p->tc) return tc_contract(p, 1, p->W2, flm, st);
   {
     StageScope sc(p, SSHT_STAGE_PROJECT, st);
     SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W2, flm, st), "adjoint contraction");
@@ -366,6 +402,7 @@ void release(ssht_plan_t p) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
+  if (p->tc) tc_destroy(p->tc);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
@@ -389,8 +426,10 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   if (desc->precision != SSHT_FP64 && desc->precision != SSHT_FP32 && desc->precision != SSHT_TF32X3 &&
       desc->precision != SSHT_BF16X6)
     return fail(SSHT_EINVAL, "unknown precision");
-  if (desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6)
-    return fail(SSHT_EUNSUPPORTED, "tensor-core precisions are not built in this library version");
+  if (desc->precision == SSHT_BF16X6)
+    return fail(SSHT_EUNSUPPORTED, "the split-BF16 tensor-core precision is not built in this library version");
+  if (desc->precision == SSHT_TF32X3 && B > 64)
+    return fail(SSHT_EUNSUPPORTED, "tensor-core plans take at most 64 fields per plan in this version");
 
   ssht_plan_t p = new (std::nothrow) ssht_plan_s();
   if (!p) return fail(SSHT_ENOMEM, "host allocation of the plan");
@@ -477,8 +516,18 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
       return fail(SSHT_ECUDA, "weight spectrum setup failed");
     }
   }
+  if (desc->precision == SSHT_TF32X3) {
+    ce = tc_setup(&p->tc, L, s, B, p->device);
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                  std::string("tensor-core plan: ") + cudaGetErrorString(ce));
+    }
+    p->bytes += tc_bytes(p->tc);
+  }
   if (p->delta_mode == SSHT_DELTA_CACHE) {
     if ((rc = run_delta(p, 0))) return bail(rc);
+    if (p->tc && ((rc = pack_a(p, 0, 0)) || (rc = pack_a(p, 1, 0)))) return bail(rc);
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) {
       release(p);

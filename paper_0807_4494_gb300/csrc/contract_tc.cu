@@ -1,0 +1,541 @@
+// The O(L^3) contractions on the tcgen05 tensor cores (3xTF32 split products, FP32 accumulation
+// in tensor memory), for batched transforms.
+//
+// For each m >= 0 both signs of m share one matrix (eqn wignerd_sym6 gives
+// Delta^l_{m',-m} = (-1)^{l+m'} Delta^l_{m'm}):
+//   A_m[m', l] = U_l[m'] Delta^l_{m'm},   U_l[m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s},
+// nonzero for l >= max(m, m', |s|).  With columns j = (sign, part, b) over 4B real columns:
+//   inverse (eqn fourier_coeff):  D[m', j] = sum_l A_m[m', l] V_m[l, j],
+//       V_m[l, (0, part, b)] = part(sf_{l,m}[b]),  V_m[l, (1, part, b)] = (-1)^l part(sf_{l,-m}[b]);
+//       F_{m m'} = (-1)^s i^{-(m+s)} D[m', (0, ., b)],  F_{-m, m'} = (-1)^s i^{m-s} (-1)^{m'} D[m', (1, ., b)].
+//   forward / adjoint projection:  P[l, j] = sum_{m'} A_m[m', l] Y_m[m', j],
+//       Y_m[m', (0, part, b)] = part(H_{m m'}[b]),  Y_m[m', (1, part, b)] = (-1)^{m'} part(H_{-m m'}[b]);
+//       sf_{lm} = (-1)^s i^{m+s} P[l, (0, ., b)],  sf_{l,-m} = (-1)^s i^{-m+s} (-1)^l P[l, (1, ., b)].
+// So every m is a real GEMM with M = 128-row blocks of m' (inverse) or l (forward), K = l or m'
+// in chunks of 32, N = 2H columns, H = 2B rounded up to 16 (column sign*H + 2b + part).  Operands
+// are split x = hi + lo (TF32) and the product is hi*hi + hi*lo + lo*hi (the dropped lo*lo is
+// ~2^-22 relative).
+//
+// Accumulation.  The tensor core's FP32 accumulation truncates (rounds toward zero); over the
+// 384 accumulation steps of K = 1024 that bias alone reaches ~1e-5 relative.  So each K chunk
+// accumulates into a fresh tensor-memory segment, the two small correction products first and the
+// four hi*hi products last (truncation then acts on four large steps only), and the epilogue warps
+// add every segment into FP32 running sums in registers (round to nearest).
+//
+// Operands are packed once per call (A also once per plan with the Delta cache) into 32 KB / 64 KB
+// tiles already in the K-major SWIZZLE_128B layout, so the main kernel moves them with 1-D bulk
+// copies.  Main kernel: persistent, one CTA per SM, 6 warps: warp 0 lane 0 issues the bulk copies
+// (2-stage ring of 96 KB), warp 1 lane 0 issues tcgen05.mma into one of two 128 x 256 FP32
+// accumulators in tensor memory, warps 2-5 (one per 32-lane quarter of tensor memory) read the
+// accumulator with tcgen05.ld, apply the phases and write the outputs.  Work items (m, row block)
+// are sorted by decreasing length and dealt round-robin to the CTAs.  Every wait is bounded; a
+// timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
+#include "ssht_internal.h"
+#include "tc_common.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace ssht {
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128;                    // rows per tile
+constexpr int TK = 32;                     // K per chunk (one 128-byte TF32 row)
+constexpr int A_PART = TM * TK * 4;        // 16 KB: one split part of an A tile
+constexpr int A_TILE = 2 * A_PART;         // hi then lo
+constexpr int STAGES = 2;
+constexpr int EPI_WARPS = 8;                       // two per tensor-memory lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer warp, MMA warp, epilogue warps
+constexpr long long WAIT_LIMIT = 1ll << 25;
+
+__host__ __device__ inline long long tri_ll(long long m) { return m * (m + 1) / 2; }
+__host__ __device__ inline size_t doff(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
+
+struct Item {
+  int m, i, c0, c1;     // row block i of m; K chunks [c0, c1)
+  long long atile;      // index of the A tile of chunk c0
+};
+
+struct TcArgs {
+  int L, s, B, NC;        // NC = 2H: padded columns, H = 2B rounded up to 16 (<= 128)
+  int nitems;
+  const Item* items;
+  const uint8_t* A;       // packed A tiles
+  const uint8_t* X;       // packed data tiles
+  const long long* xoff;  // per m: data tile index of chunk xc0(m)
+  const int* xc0;         // per m: first chunk stored for m
+  const float2* ph;       // e^{i pi k/N}, k in [-(N-1), N-1], at k + N - 1
+  float2* out;            // inverse: theta-DFT input E [B][N][N]; forward: flm [B][L*L]
+  int* status;
+};
+
+__device__ __forceinline__ float2 ipow_signed(int s, int k) {
+  const int r = ((k % 4) + 4) % 4;
+  float a = (r == 0) ? 1.f : (r == 2) ? -1.f : 0.f;
+  float b = (r == 1) ? 1.f : (r == 3) ? -1.f : 0.f;
+  if (s & 1) { a = -a; b = -b; }
+  return make_float2(a, b);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Packing: A tiles from the FP64 Delta table
+// ---------------------------------------------------------------------------------------------
+
+// Inverse A tile (m, i, c): rows m' = 128 i + r, columns l = 32 c + k (K-major).
+// Forward A tile (m, i, c): rows l = 128 i + r, columns m' = 32 c + k.
+template <bool FWD>
+__global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* __restrict__ items,
+                                                     const double* __restrict__ table, const double* __restrict__ U,
+                                                     uint8_t* __restrict__ A) {
+  __shared__ __align__(16) uint8_t tile[A_TILE];
+  const Item it = items[blockIdx.y];
+  const int c = it.c0 + blockIdx.x;
+  if (c >= it.c1) return;
+  const int m = it.m, Lp = L - 1, as = s < 0 ? -s : s;
+  for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) {
+    int r, k;
+    if (FWD) { k = e % TK; r = e / TK; } else { r = e % TM; k = e / TM; }
+    const int rowv = it.i * TM + r, colv = c * TK + k;
+    const int mp = FWD ? colv : rowv;
+    const int l = FWD ? rowv : colv;
+    float x = 0.f;
+    if (l <= Lp && mp <= Lp && l >= m && l >= mp && l >= as) {
+      // Delta^l_{m' m} = (-1)^{m'-m} Delta^l_{m m'}: row m of degree l, contiguous in m'
+      const double d = table[doff(l) + (size_t)m * (l + 1) + mp];
+      const double a = U[tri_ll(l) + mp] * d;
+      x = (float)(((mp - m) & 1) ? -a : a);
+    }
+    float hi, lo;
+    split_tf32(x, &hi, &lo);
+    const uint32_t o = sw128(r, k * 4);
+    *(float*)(tile + o) = hi;
+    *(float*)(tile + A_PART + o) = lo;
+  }
+  __syncthreads();
+  uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * A_TILE);
+  const uint4* src = (const uint4*)tile;
+  for (int e = threadIdx.x; e < A_TILE / 16; e += blockDim.x) dst[e] = src[e];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Packing: data tiles (rows j = (sign, part, b), K-major over 32 l or m')
+// ---------------------------------------------------------------------------------------------
+
+// Inverse data tile (m, c): V_m[l, j], l = 32 c + k.
+__global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC, const int* __restrict__ xc0,
+                                                     const long long* __restrict__ xoff,
+                                                     const float2* __restrict__ flm, uint8_t* __restrict__ X) {
+  extern __shared__ __align__(16) uint8_t tile[];
+  const int m = blockIdx.y;
+  const int c = xc0[m] + blockIdx.x;
+  const int nC = (L + TK - 1) / TK;
+  if (c >= nC) return;
+  const int as = s < 0 ? -s : s, lmin = m > as ? m : as;
+  const int part_bytes = NC * 128;
+  for (int e = threadIdx.x; e < NC * TK; e += blockDim.x) {
+    const int k = e % TK, j = e / TK;
+    const int l = c * TK + k;
+    float x = 0.f;
+    const int half = NC / 2, sign = j / half, jj = j % half, part = jj & 1, b = jj >> 1;
+    if (b < B && l < L && l >= lmin) {
+      if (!(sign && m == 0)) {
+        const float2 v = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
+        x = part ? v.y : v.x;
+        if (sign && (l & 1)) x = -x;
+      }
+    }
+    float hi, lo;
+    split_tf32(x, &hi, &lo);
+    const uint32_t o = sw128(j, k * 4);
+    *(float*)(tile + o) = hi;
+    *(float*)(tile + part_bytes + o) = lo;
+  }
+  __syncthreads();
+  uint4* dst = (uint4*)(X + (size_t)(xoff[m] + blockIdx.x) * 2 * part_bytes);
+  const uint4* src = (const uint4*)tile;
+  for (int e = threadIdx.x; e < 2 * part_bytes / 16; e += blockDim.x) dst[e] = src[e];
+}
+
+// Forward data tile (m, c): Y_m[m', j], m' = 32 c + k, from H[b][m + Lp][m'] (m' < L).
+__global__ void __launch_bounds__(256) pack_y_kernel(int L, int B, int NC, const float2* __restrict__ H,
+                                                     uint8_t* __restrict__ X) {
+  extern __shared__ __align__(16) uint8_t tile[];
+  const int m = blockIdx.y, c = blockIdx.x;
+  const int Lp = L - 1, NT = 2 * L - 1;
+  const int nC = (L + TK - 1) / TK;
+  const int part_bytes = NC * 128;
+  for (int e = threadIdx.x; e < NC * TK; e += blockDim.x) {
+    const int k = e % TK, j = e / TK;
+    const int mp = c * TK + k;
+    float x = 0.f;
+    const int half = NC / 2, sign = j / half, jj = j % half, part = jj & 1, b = jj >> 1;
+    if (b < B && mp < L) {
+      if (!(sign && m == 0)) {
+        const float2 v = H[((size_t)b * NT + (sign ? Lp - m : Lp + m)) * L + mp];
+        x = part ? v.y : v.x;
+        if (sign && (mp & 1)) x = -x;
+      }
+    }
+    float hi, lo;
+    split_tf32(x, &hi, &lo);
+    const uint32_t o = sw128(j, k * 4);
+    *(float*)(tile + o) = hi;
+    *(float*)(tile + part_bytes + o) = lo;
+  }
+  __syncthreads();
+  uint4* dst = (uint4*)(X + ((size_t)m * nC + c) * 2 * part_bytes);
+  const uint4* src = (const uint4*)tile;
+  for (int e = threadIdx.x; e < 2 * part_bytes / 16; e += blockDim.x) dst[e] = src[e];
+}
+
+// ---------------------------------------------------------------------------------------------
+// The tensor-core GEMM
+// ---------------------------------------------------------------------------------------------
+
+// Loads 4 groups of 16 columns (64 values) of this warp's 32 tensor-memory lanes, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+  uint32_t r[64];
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[16 * g + 0]), "=r"(r[16 * g + 1]), "=r"(r[16 * g + 2]), "=r"(r[16 * g + 3]),
+                   "=r"(r[16 * g + 4]), "=r"(r[16 * g + 5]), "=r"(r[16 * g + 6]), "=r"(r[16 * g + 7]),
+                   "=r"(r[16 * g + 8]), "=r"(r[16 * g + 9]), "=r"(r[16 * g + 10]), "=r"(r[16 * g + 11]),
+                   "=r"(r[16 * g + 12]), "=r"(r[16 * g + 13]), "=r"(r[16 * g + 14]), "=r"(r[16 * g + 15])
+                 : "r"(taddr + 16 * g));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int b_part = a.NC * 128;
+  const int stage_bytes = A_TILE + 2 * b_part;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], seg_full[2], seg_empty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 1) tmem_alloc(&tmem_base, 512);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&seg_full[k], 1);
+      mbar_init(&seg_empty[k], EPI_WARPS);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = tmem_base;
+  volatile int* abort = &abort_flag;
+  const int nC = (a.L + TK - 1) / TK;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: bulk copies of the A and data tiles of every chunk ----
+      int it = 0;
+      int last_use[STAGES] = {-1, -1};
+      for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+        const Item itm = a.items[w];
+        const uint8_t* Ab = a.A + (size_t)itm.atile * A_TILE;
+        for (int c = itm.c0; c < itm.c1; ++c, ++it) {
+          const int s = it % STAGES, u = it / STAGES;
+          if (!mbar_wait(&empty[s], (u & 1) ^ 1, abort, WAIT_LIMIT)) {
+            *abort = 1;
+            break;
+          }
+          uint8_t* st = smem + s * stage_bytes;
+          mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+          bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
+          const long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
+          bulk_g2s(st + A_TILE, a.X + (size_t)xt * 2 * b_part, (uint32_t)(2 * b_part), &full[s]);
+          last_use[s] = u;
+        }
+      }
+      // drain: every issued copy must have landed before the CTA leaves
+      for (int s = 0; s < STAGES; ++s)
+        if (last_use[s] >= 0) mbar_wait(&full[s], last_use[s] & 1, abort, WAIT_LIMIT);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: one tensor-memory segment per chunk, corrections first ----
+      const uint32_t idesc = idesc_tf32(TM, a.NC);
+      int it = 0;
+      for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+        const Item itm = a.items[w];
+        bool ok = true;
+        for (int c = itm.c0; c < itm.c1; ++c, ++it) {
+          const int s = it % STAGES, u = it / STAGES;
+          const int seg = it & 1, us = it >> 1;
+          if (!mbar_wait(&seg_empty[seg], (us & 1) ^ 1, abort, WAIT_LIMIT) ||
+              !mbar_wait(&full[s], u & 1, abort, WAIT_LIMIT)) {
+            *abort = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t dt = tbase + (uint32_t)(seg * 256);
+          const uint32_t sa = smem_u32(smem + s * stage_bytes);
+          const uint32_t sb = sa + A_TILE;
+#pragma unroll
+          for (int kk = 0; kk < TK / 8; ++kk) {
+            const uint32_t ko = kk * 32;
+            mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
+            mma_tf32(dt, desc_sw128(sa + A_PART + ko), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
+          }
+#pragma unroll
+          for (int kk = 0; kk < TK / 8; ++kk) {
+            const uint32_t ko = kk * 32;
+            mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&seg_full[seg]);
+        }
+        if (!ok) break;
+      }
+      mma_commit(&done_bar);
+      mbar_wait(&done_bar, 0, abort, WAIT_LIMIT);
+    }
+  } else {
+    // ---- epilogue: running sums of the segments, then phases and outputs ----
+    const int q = warp & 3;                // tensor-memory lane quarter this warp may access
+    const int h = (warp - 2) >> 2;         // column half: sign of m
+    const int r = q * 32 + lane;
+    const int L = a.L, Lp = L - 1, NT = 2 * L - 1, B = a.B, s = a.s;
+    const int H = a.NC / 2;
+    const uint32_t tq = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * H);
+    int it = 0;
+    for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+      const Item itm = a.items[w];
+      float acc[128];
+#pragma unroll
+      for (int k = 0; k < 128; ++k) acc[k] = 0.f;
+      bool ok = true;
+      for (int c = itm.c0; c < itm.c1; ++c, ++it) {
+        const int seg = it & 1, us = it >> 1;
+        if (!mbar_wait(&seg_full[seg], us & 1, abort, WAIT_LIMIT)) {
+          *abort = 1;
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t ts = tq + (uint32_t)(seg * 256);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          if (64 * g < H) {
+            float v[64];
+            tmem_ld64(ts + 64 * g, v);
+#pragma unroll
+            for (int k = 0; k < 64; ++k) acc[64 * g + k] += v[k];
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&seg_empty[seg]);
+      }
+      if (!ok) break;
+      const int m = itm.m;
+      if (h == 1 && m == 0) continue;
+      const int rowv = itm.i * TM + r;  // m' (inverse) or l (forward)
+      const bool valid = FWD ? (rowv <= Lp && rowv >= m) : (rowv <= Lp);
+      if (!valid) continue;
+      const int mm = h ? -m : m;
+      const float2 pz = FWD ? ipow_signed(s, mm + s) : ipow_signed(s, -(mm + s));
+      const float rs = (h && (rowv & 1)) ? -1.f : 1.f;  // (-1)^{m'} (inverse) or (-1)^l (forward) for -m
+#pragma unroll
+      for (int b = 0; b < 64; ++b) {
+        if (b >= B) break;
+        const float xr = rs * acc[2 * b], xi = rs * acc[2 * b + 1];
+        const float2 F = make_float2(pz.x * xr - pz.y * xi, pz.x * xi + pz.y * xr);
+        if (FWD) {
+          a.out[(size_t)b * L * L + (size_t)rowv * rowv + rowv + mm] = F;
+        } else {
+          float2* row = a.out + ((size_t)b * NT + (mm + Lp)) * NT;
+          const float2 e = a.ph[rowv + NT - 1];  // e^{i pi m'/N}
+          row[rowv] = make_float2(F.x * e.x - F.y * e.y, F.x * e.y + F.y * e.x);
+          if (rowv > 0) {
+            const float sg = ((mm + s) & 1) ? -1.f : 1.f;
+            const float2 ec = a.ph[-rowv + NT - 1];
+            row[NT - rowv] = make_float2(sg * (F.x * ec.x - F.y * ec.y), sg * (F.x * ec.y + F.y * ec.x));
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (*abort && threadIdx.x == 0) atomicOr(a.status, 2);
+  if (warp == 1) tmem_dealloc(tbase, 512);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+
+struct TcPlan {
+  int L = 0, s = 0, B = 0, NC = 0, nC = 0, nI = 0;
+  Item* items_inv = nullptr;
+  Item* items_fwd = nullptr;
+  int n_inv = 0, n_fwd = 0;
+  long long tiles_inv = 0, tiles_fwd = 0, xtiles_inv = 0, xtiles_fwd = 0;
+  uint8_t* A_inv = nullptr;
+  uint8_t* A_fwd = nullptr;
+  uint8_t* X = nullptr;  // data tiles (shared by both directions; sized for the larger)
+  long long* xoff = nullptr;
+  int* xc0 = nullptr;
+  size_t bytes = 0;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+static cudaError_t tc_alloc(void** p, size_t bytes, size_t* total) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e == cudaSuccess) *total += bytes;
+  return e;
+}
+
+cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int device) {
+  *out = nullptr;
+  if (B < 1 || B > 64) return cudaErrorInvalidValue;
+  TcPlan* p = new TcPlan();
+  p->L = L;
+  p->s = s;
+  p->B = B;
+  p->NC = 2 * (((2 * B + 15) / 16) * 16);
+  p->nC = (L + TK - 1) / TK;
+  p->nI = (L + TM - 1) / TM;
+  const int as = s < 0 ? -s : s;
+  std::vector<Item> inv, fwd;
+  std::vector<long long> xoff(L);
+  std::vector<int> xc0(L);
+  long long at = 0, ft = 0, xt = 0;
+  for (int m = 0; m < L; ++m) {
+    const int lmin = std::max(m, as);
+    xc0[m] = lmin / TK;
+    xoff[m] = xt;
+    xt += p->nC - xc0[m];
+    for (int i = 0; i < p->nI; ++i) {
+      // inverse: rows m' in block i, K = l >= max(m, m', |s|)
+      const int c0 = std::max(lmin / TK, (i * TM) / TK);
+      if (i * TM <= L - 1 && c0 < p->nC) {
+        inv.push_back({m, i, c0, p->nC, at});
+        at += p->nC - c0;
+      }
+      // forward: rows l in block i with l >= m (rows l < |s| come out as zeros), K = m' <= l
+      if ((i + 1) * TM > m && i * TM <= L - 1) {
+        const int c1 = std::min(p->nC, ((i + 1) * TM + TK - 1) / TK);
+        fwd.push_back({m, i, 0, c1, ft});
+        ft += c1;
+      }
+    }
+  }
+  auto longest_first = [](const Item& x, const Item& y) { return (x.c1 - x.c0) > (y.c1 - y.c0); };
+  std::stable_sort(inv.begin(), inv.end(), longest_first);
+  std::stable_sort(fwd.begin(), fwd.end(), longest_first);
+  p->n_inv = (int)inv.size();
+  p->n_fwd = (int)fwd.size();
+  p->tiles_inv = at;
+  p->tiles_fwd = ft;
+  p->xtiles_inv = xt;
+  p->xtiles_fwd = (long long)L * p->nC;
+  cudaError_t e;
+  const size_t xbytes = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * 2 * p->NC * 128;
+  if ((e = tc_alloc((void**)&p->items_inv, inv.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->A_fwd, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->xoff, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->xc0, L * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->items_inv, inv.data(), inv.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->items_fwd, fwd.data(), fwd.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->xoff, xoff.data(), L * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->xc0, xc0.data(), L * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  {
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) goto fail;
+    p->grid = sms;
+    p->smem = (size_t)STAGES * (A_TILE + 2 * p->NC * 128) + 1024;
+    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+    const int xsmem = 2 * p->NC * 128;
+    if ((e = cudaFuncSetAttribute(pack_v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+    if ((e = cudaFuncSetAttribute(pack_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+  }
+  *out = p;
+  return cudaSuccess;
+fail:
+  tc_destroy(p);
+  return e;
+}
+
+void tc_destroy(TcPlan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->items_inv, p->items_fwd, p->A_inv, p->A_fwd, p->X, p->xoff, p->xc0};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+size_t tc_bytes(const TcPlan* p) { return p ? p->bytes : 0; }
+
+cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double* U, cudaStream_t st, int* launches) {
+  // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
+  if (forward)
+    pack_a_kernel<true><<<dim3(p->nC, p->n_fwd), 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
+  else
+    pack_a_kernel<false><<<dim3(p->nC, p->n_inv), 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches) {
+  const int xsmem = 2 * p->NC * 128;
+  if (forward)
+    pack_y_kernel<<<dim3(p->nC, p->L), 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
+  else
+    pack_v_kernel<<<dim3(p->nC, p->L), 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff,
+                                                          (const float2*)src, p->X);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches) {
+  TcArgs a;
+  a.L = p->L;
+  a.s = p->s;
+  a.B = p->B;
+  a.NC = p->NC;
+  a.nitems = forward ? p->n_fwd : p->n_inv;
+  a.items = forward ? p->items_fwd : p->items_inv;
+  a.A = forward ? p->A_fwd : p->A_inv;
+  a.X = p->X;
+  a.xoff = p->xoff;
+  a.xc0 = p->xc0;
+  a.ph = (const float2*)ph;
+  a.out = (float2*)out;
+  a.status = status;
+  const int grid = std::min(p->grid, std::max(a.nitems, 1));
+  if (forward)
+    tc_gemm_kernel<true><<<grid, THREADS, p->smem, st>>>(a);
+  else
+    tc_gemm_kernel<false><<<grid, THREADS, p->smem, st>>>(a);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace ssht

@@ -63,6 +63,22 @@ cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* tab
                                   const void* H, void* flm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
+// Tensor-core contractions (contract_tc.cu), 3xTF32, batch of at most 64 fields per plan
+// ---------------------------------------------------------------------------
+struct TcPlan;
+cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int device);
+void tc_destroy(TcPlan* p);
+size_t tc_bytes(const TcPlan* p);
+// Pack the A operand (U_l[m'] Delta^l_{m'm}, split hi/lo) of one direction from the FP64 table.
+cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double* U, cudaStream_t st, int* launches);
+// Pack the data operand: forward = 0: V from flm (float2 [B][L*L]); forward = 1: Y from the
+// folded torus sums H (float2 [B][N][L]).
+cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches);
+// The contraction: forward = 0 writes the theta-DFT input E (float2 [B][N][N]) of the inverse;
+// forward = 1 writes flm (float2 [B][L*L]).  Timeouts set bit 2 of *status.
+cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);
+
+// ---------------------------------------------------------------------------
 // Torus kernels (torus.cu)
 // ---------------------------------------------------------------------------
 // g[b][m+Lp][t] (theta-synthesis output, N per row) -> h[b][t][m mod N] * e^{i pi m / N}, t < L.
