@@ -101,7 +101,8 @@ struct ssht_plan_s {
   size_t stage_out_bytes = 0;
   bool delta_ready = false;
   size_t bytes = 0;
-  TcPlan* tc = nullptr;  // tensor-core contraction (precision SSHT_TF32X3)
+  TcPlan* tc = nullptr;    // tensor-core contraction (precision SSHT_TF32X3)
+  DftPlan* dft = nullptr;  // odd-length torus DFTs of FP32 plans (FP64 plans use cuFFT Z2Z)
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -173,6 +174,15 @@ int exec_fft(const ssht_plan_t p, cufftHandle h, void* in, void* out, int dir, c
   } else {
     SSHT_FFT(cufftExecC2C(h, (cufftComplex*)in, (cufftComplex*)out, dir), "cufftExecC2C");
   }
+  return 0;
+}
+
+// A batch of length-N torus DFTs: the library's Bluestein kernel for FP32 plans, cuFFT for FP64.
+int run_dft(ssht_plan_t p, cufftHandle h, int sign, long long nrows, void* in, void* out, cudaStream_t st) {
+  if (p->f64) return exec_fft(p, h, in, out, sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, st);
+  StageScope sc(p, SSHT_STAGE_FFT, st);
+  SSHT_CUDA(dft_rows(p->dft, sign, nrows, in, out, st), "torus DFT");
+  p->launches += 1;
   return 0;
 }
 
@@ -318,14 +328,14 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
               "inverse contraction");
     p->launches += 1;
   }
-  rc = exec_fft(p, p->fft_theta, p->W1, p->W2, CUFFT_INVERSE, st);
+  rc = run_dft(p, p->fft_theta, +1, (long long)p->B * d.N, p->W1, p->W2, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
     SSHT_CUDA(inv_theta_to_phi<T>(d, p->B, p->W2, p->W1, p->ph, st), "theta-to-phi transpose");
     p->launches += 1;
   }
-  return exec_fft(p, p->fft_phi, p->W1, f, CUFFT_INVERSE, st);
+  return run_dft(p, p->fft_phi, +1, (long long)p->B * d.L, p->W1, f, st);
 }
 
 // Shared front of the forward transform (mode 0) and the adjoint (mode 1): phi DFT,
@@ -333,14 +343,14 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
 template <typename T>
 int analysis_front(ssht_plan_t p, const void* f, int mode, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = exec_fft(p, p->fft_phi, const_cast<void*>(f), p->W2, CUFFT_FORWARD, st);
+  int rc = run_dft(p, p->fft_phi, -1, (long long)p->B * d.L, const_cast<void*>(f), p->W2, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
     SSHT_CUDA(fwd_phi_to_theta<T>(d, p->s, p->B, mode, p->W2, p->W1, p->ph, st), "phi-to-theta extension");
     p->launches += 1;
   }
-  return exec_fft(p, p->fft_theta, p->W1, p->W1, CUFFT_FORWARD, st);
+  return run_dft(p, p->fft_theta, -1, (long long)p->B * d.N, p->W1, p->W1, st);
 }
 
 template <typename T>
@@ -403,6 +413,7 @@ void release(ssht_plan_t p) {
     cudaEventDestroy(e.b);
   }
   if (p->tc) tc_destroy(p->tc);
+  if (p->dft) dft_destroy(p->dft);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
@@ -491,8 +502,18 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
       return fail(SSHT_ECUDA, std::string("phase table upload: ") + cudaGetErrorString(ce));
     }
   }
-  if ((rc = make_fft(p, &p->fft_phi, &p->have_phi, d.N, (size_t)B * d.L, "cuFFT phi plan"))) return bail(rc);
-  if ((rc = make_fft(p, &p->fft_theta, &p->have_theta, d.N, (size_t)B * d.N, "cuFFT theta plan"))) return bail(rc);
+  if (p->f64) {
+    if ((rc = make_fft(p, &p->fft_phi, &p->have_phi, d.N, (size_t)B * d.L, "cuFFT phi plan"))) return bail(rc);
+    if ((rc = make_fft(p, &p->fft_theta, &p->have_theta, d.N, (size_t)B * d.N, "cuFFT theta plan"))) return bail(rc);
+  } else {
+    ce = dft_setup(&p->dft, d.N);
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                  std::string("torus DFT setup: ") + cudaGetErrorString(ce));
+    }
+    p->bytes += dft_bytes(p->dft);
+  }
   if ((rc = make_fft(p, &p->fft_conv, &p->have_conv, d.M, (size_t)B * d.N, "cuFFT convolution plan"))) return bail(rc);
 
   // Weight spectrum: FFT of the even part of w(p) = int_0^pi sin(t) e^{ipt} dt.

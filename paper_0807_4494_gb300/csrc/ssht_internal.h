@@ -79,6 +79,16 @@ cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t s
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);
 
 // ---------------------------------------------------------------------------
+// Odd-length DFTs of the torus rows (dft.cu), FP32, Bluestein in shared memory
+// ---------------------------------------------------------------------------
+struct DftPlan;
+cudaError_t dft_setup(DftPlan** out, int N);
+void dft_destroy(DftPlan* p);
+size_t dft_bytes(const DftPlan* p);
+// out[row][k] = sum_n in[row][n] e^{sign 2 pi i n k / N} (float2 rows of length N; in == out allowed).
+cudaError_t dft_rows(const DftPlan* p, int sign, long long nrows, const void* in, void* out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // Torus kernels (torus.cu)
 // ---------------------------------------------------------------------------
 // g[b][m+Lp][t] (theta-synthesis output, N per row) -> h[b][t][m mod N] * e^{i pi m / N}, t < L.

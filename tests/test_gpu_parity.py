@@ -160,6 +160,21 @@ def test_many_rows_fp32():
         assert rel(adj[b], T.adjoint(f_or, L, s)) < TOL32
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_headline_band_limit_two_fields(prec):
+    """L = 1024 (torus length 2047, shared-memory Bluestein with M = 4096), s = 2, CMB-like spectrum."""
+    L, s, B = 1024, 2, 2
+    flm = inputs.coeffs(L, s, B, seed=3, spectrum="cmb")
+    plan = S().Plan(L, s, B, precision=prec)
+    f = plan.inverse(dev(flm, torch.complex64))
+    back = plan.forward(f).cpu().numpy()
+    plan.check()
+    f = f.cpu().numpy()
+    f_or = T.inverse(flm[1], L, s)
+    assert rel(f[1], f_or) < 1e-6
+    assert rel(back[1], T.forward(f[1].astype(np.complex128), L, s)) < 1e-6
+
+
 def test_host_pointers_match_device_pointers():
     L, s, B = 24, 1, 2
     flm = inputs.coeffs(L, s, B, seed=5)
