@@ -102,7 +102,7 @@ struct ssht_plan_s {
   bool delta_ready = false;
   size_t bytes = 0;
   TcPlan* tc = nullptr;    // tensor-core contraction (precision SSHT_TF32X3)
-  DftPlan* dft = nullptr;  // odd-length torus DFTs of FP32 plans (FP64 plans use cuFFT Z2Z)
+  TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -177,11 +177,14 @@ int exec_fft(const ssht_plan_t p, cufftHandle h, void* in, void* out, int dir, c
   return 0;
 }
 
-// A batch of length-N torus DFTs: the library's Bluestein kernel for FP32 plans, cuFFT for FP64.
-int run_dft(ssht_plan_t p, cufftHandle h, int sign, long long nrows, void* in, void* out, cudaStream_t st) {
-  if (p->f64) return exec_fft(p, h, in, out, sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, st);
+int run_dft(ssht_plan_t p, cufftHandle h, int sign, void* in, void* out, cudaStream_t st) {
+  return exec_fft(p, h, in, out, sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, st);
+}
+
+// One fused torus pass of an FP32 plan (DFT along theta or phi with its glue), timed as FFT work.
+int run_torus(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_FFT, st);
-  SSHT_CUDA(dft_rows(p->dft, sign, nrows, in, out, st), "torus DFT");
+  SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, in, out, st), "torus pass");
   p->launches += 1;
   return 0;
 }
@@ -324,18 +327,22 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
     if ((rc = tc_contract(p, 0, flm, p->W1, st))) return rc;
   } else {
     StageScope sc(p, SSHT_STAGE_INVERSE, st);
-    SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, st),
+    SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, p->torus ? 1 : 0, st),
               "inverse contraction");
     p->launches += 1;
   }
-  rc = run_dft(p, p->fft_theta, +1, (long long)p->B * d.N, p->W1, p->W2, st);
+  if (p->torus) {
+    if ((rc = run_torus(p, 0, p->W1, p->W2, st))) return rc;
+    return run_torus(p, 1, p->W2, f, st);
+  }
+  rc = run_dft(p, p->fft_theta, +1, p->W1, p->W2, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
     SSHT_CUDA(inv_theta_to_phi<T>(d, p->B, p->W2, p->W1, p->ph, st), "theta-to-phi transpose");
     p->launches += 1;
   }
-  return run_dft(p, p->fft_phi, +1, (long long)p->B * d.L, p->W1, f, st);
+  return run_dft(p, p->fft_phi, +1, p->W1, f, st);
 }
 
 // Shared front of the forward transform (mode 0) and the adjoint (mode 1): phi DFT,
@@ -343,20 +350,30 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
 template <typename T>
 int analysis_front(ssht_plan_t p, const void* f, int mode, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = run_dft(p, p->fft_phi, -1, (long long)p->B * d.L, const_cast<void*>(f), p->W2, st);
+  int rc = run_dft(p, p->fft_phi, -1, const_cast<void*>(f), p->W2, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
     SSHT_CUDA(fwd_phi_to_theta<T>(d, p->s, p->B, mode, p->W2, p->W1, p->ph, st), "phi-to-theta extension");
     p->launches += 1;
   }
-  return run_dft(p, p->fft_theta, -1, (long long)p->B * d.N, p->W1, p->W1, st);
+  return run_dft(p, p->fft_theta, -1, p->W1, p->W1, st);
 }
 
 template <typename T>
 int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = analysis_front<T>(p, f, 0, st);
+  int rc;
+  if (p->torus) {
+    if ((rc = run_torus(p, 2, f, p->W2, st)) || (rc = run_torus(p, 4, p->W2, p->W1, st))) return rc;
+    if ((rc = ensure_operands(p, 1, st))) return rc;
+    if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "forward contraction");
+    p->launches += 1;
+    return 0;
+  }
+  rc = analysis_front<T>(p, f, 0, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
@@ -388,7 +405,17 @@ int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
 template <typename T>
 int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = analysis_front<T>(p, g, 1, st);
+  int rc;
+  if (p->torus) {
+    if ((rc = run_torus(p, 3, g, p->W2, st)) || (rc = run_torus(p, 5, p->W2, p->W1, st))) return rc;
+    if ((rc = ensure_operands(p, 1, st))) return rc;
+    if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "adjoint contraction");
+    p->launches += 1;
+    return 0;
+  }
+  rc = analysis_front<T>(p, g, 1, st);
   if (rc) return rc;
   {
     StageScope sc(p, SSHT_STAGE_TORUS, st);
@@ -413,7 +440,7 @@ void release(ssht_plan_t p) {
     cudaEventDestroy(e.b);
   }
   if (p->tc) tc_destroy(p->tc);
-  if (p->dft) dft_destroy(p->dft);
+  if (p->torus) torus_destroy(p->torus);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
@@ -474,11 +501,15 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   }
   p->bytes += delta_offset(L) * 8 + 2 * tri(L + 1) * 8;
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
-  const size_t torus = (size_t)B * d.N * d.N * p->elem;
+  // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
+  // rows of N x L only.
+  const size_t torus = (size_t)B * d.N * (p->f64 ? d.N : d.L) * p->elem;
   if ((rc = dalloc(p, &p->W1, torus, "torus workspace 1"))) return bail(rc);
   if ((rc = dalloc(p, &p->W2, torus, "torus workspace 2"))) return bail(rc);
-  if ((rc = dalloc(p, &p->W3, (size_t)B * d.N * d.M * p->elem, "convolution workspace"))) return bail(rc);
-  if ((rc = dalloc(p, &p->khat, (size_t)d.M * p->elem, "weight spectrum"))) return bail(rc);
+  if (p->f64) {
+    if ((rc = dalloc(p, &p->W3, (size_t)B * d.N * d.M * p->elem, "convolution workspace"))) return bail(rc);
+    if ((rc = dalloc(p, &p->khat, (size_t)d.M * p->elem, "weight spectrum"))) return bail(rc);
+  }
   if ((rc = dalloc(p, &p->ph, (size_t)(2 * d.N - 1) * p->elem, "phase table"))) return bail(rc);
   if ((rc = dalloc(p, (void**)&p->ph64, (size_t)(2 * d.N - 1) * sizeof(double2), "phase table"))) return bail(rc);
 
@@ -505,37 +536,32 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   if (p->f64) {
     if ((rc = make_fft(p, &p->fft_phi, &p->have_phi, d.N, (size_t)B * d.L, "cuFFT phi plan"))) return bail(rc);
     if ((rc = make_fft(p, &p->fft_theta, &p->have_theta, d.N, (size_t)B * d.N, "cuFFT theta plan"))) return bail(rc);
-  } else {
-    ce = dft_setup(&p->dft, d.N);
-    if (ce != cudaSuccess) {
-      release(p);
-      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
-                  std::string("torus DFT setup: ") + cudaGetErrorString(ce));
-    }
-    p->bytes += dft_bytes(p->dft);
-  }
-  if ((rc = make_fft(p, &p->fft_conv, &p->have_conv, d.M, (size_t)B * d.N, "cuFFT convolution plan"))) return bail(rc);
-
-  // Weight spectrum: FFT of the even part of w(p) = int_0^pi sin(t) e^{ipt} dt.
-  {
+    if ((rc = make_fft(p, &p->fft_conv, &p->have_conv, d.M, (size_t)B * d.N, "cuFFT convolution plan")))
+      return bail(rc);
+    // Weight spectrum: FFT of the even part of w(p) = int_0^pi sin(t) e^{ipt} dt.
     cufftHandle k1;
     int nn = d.M;
-    cufftResult r = cufftPlan1d(&k1, nn, p->f64 ? CUFFT_Z2Z : CUFFT_C2C, 1);
+    cufftResult r = cufftPlan1d(&k1, nn, CUFFT_Z2Z, 1);
     if (r != CUFFT_SUCCESS) {
       release(p);
       return fail(SSHT_ECUDA, std::string("cuFFT weight plan: ") + cufft_name(r));
     }
-    ce = p->f64 ? make_weight_kernel<double>(d, p->khat, 0) : make_weight_kernel<float>(d, p->khat, 0);
-    if (ce == cudaSuccess) {
-      r = p->f64 ? cufftExecZ2Z(k1, (cufftDoubleComplex*)p->khat, (cufftDoubleComplex*)p->khat, CUFFT_FORWARD)
-                 : cufftExecC2C(k1, (cufftComplex*)p->khat, (cufftComplex*)p->khat, CUFFT_FORWARD);
-    }
+    ce = make_weight_kernel<double>(d, p->khat, 0);
+    if (ce == cudaSuccess) r = cufftExecZ2Z(k1, (cufftDoubleComplex*)p->khat, (cufftDoubleComplex*)p->khat, CUFFT_FORWARD);
     cudaError_t se = cudaDeviceSynchronize();
     cufftDestroy(k1);
     if (ce != cudaSuccess || r != CUFFT_SUCCESS || se != cudaSuccess) {
       release(p);
       return fail(SSHT_ECUDA, "weight spectrum setup failed");
     }
+  } else {
+    ce = torus_setup(&p->torus, L, p->ph, p->device);
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                  std::string("torus pass setup: ") + cudaGetErrorString(ce));
+    }
+    p->bytes += torus_bytes(p->torus);
   }
   if (desc->precision == SSHT_TF32X3) {
     ce = tc_setup(&p->tc, L, s, B, p->device);

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) inverse_kernel(int L, int s, int B, const
                                                       const double* __restrict__ U,
                                                       const typename Cplx<T>::type* __restrict__ flm,
                                                       typename Cplx<T>::type* __restrict__ E,
-                                                      const double2* __restrict__ ph) {
+                                                      const double2* __restrict__ ph, int half) {
   using C = typename Cplx<T>::type;
   const int Lp = L - 1, N = 2 * L - 1;
   const int m = blockIdx.x * 32 + threadIdx.x;  // |m|
@@ -91,8 +91,14 @@ __global__ void __launch_bounds__(256) inverse_kernel(int L, int s, int B, const
       if (sgn == 0) { ar = pr[j]; ai = pi[j]; }
       else { ar = msign * ((double)ner[j] - (double)nor[j]); ai = msign * ((double)nei[j] - (double)noi[j]); }
       const double Fr = fr * ar - fi * ai, Fi = fr * ai + fi * ar;
-      C* row = E + ((size_t)(b0 + j) * N + (mm + Lp)) * N;
       C v;
+      if (half) {
+        v.x = (T)Fr;
+        v.y = (T)Fi;
+        E[((size_t)(b0 + j) * N + (mm + Lp)) * L + mp] = v;
+        continue;
+      }
+      C* row = E + ((size_t)(b0 + j) * N + (mm + Lp)) * N;
       v.x = (T)(Fr * eth.x - Fi * eth.y);
       v.y = (T)(Fr * eth.y + Fi * eth.x);
       row[mp] = v;
@@ -179,12 +185,12 @@ __global__ void __launch_bounds__(256) project_kernel(int L, int s, int B, const
 
 template <typename T>
 cudaError_t contract_inverse_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* flm, void* E, const double2* ph, cudaStream_t st) {
+                                  const void* flm, void* E, const double2* ph, int half, cudaStream_t st) {
   using C = typename Cplx<T>::type;
   constexpr int BB = 2;
   dim3 block(32, 8);
   dim3 grid((d.L + 31) / 32, (d.L + 7) / 8, (B + BB - 1) / BB);
-  inverse_kernel<T, BB><<<grid, block, 0, st>>>(d.L, s, B, table, U, (const C*)flm, (C*)E, ph);
+  inverse_kernel<T, BB><<<grid, block, 0, st>>>(d.L, s, B, table, U, (const C*)flm, (C*)E, ph, half);
   return cudaGetLastError();
 }
 
@@ -200,8 +206,8 @@ cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* tab
   return cudaGetLastError();
 }
 
-template cudaError_t contract_inverse_simt<double>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, cudaStream_t);
-template cudaError_t contract_inverse_simt<float>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, cudaStream_t);
+template cudaError_t contract_inverse_simt<double>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, int, cudaStream_t);
+template cudaError_t contract_inverse_simt<float>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, int, cudaStream_t);
 template cudaError_t contract_project_simt<double>(const Dims&, int, int, const double*, const double*, const void*, void*, cudaStream_t);
 template cudaError_t contract_project_simt<float>(const Dims&, int, int, const double*, const double*, const void*, void*, cudaStream_t);
 

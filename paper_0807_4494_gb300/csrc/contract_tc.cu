@@ -24,10 +24,11 @@
 //
 // Operands are packed once per call (A also once per plan with the Delta cache) into 32 KB / 64 KB
 // tiles already in the K-major SWIZZLE_128B layout, so the main kernel moves them with 1-D bulk
-// copies.  Main kernel: persistent, one CTA per SM, 6 warps: warp 0 lane 0 issues the bulk copies
-// (2-stage ring of 96 KB), warp 1 lane 0 issues tcgen05.mma into one of two 128 x 256 FP32
-// accumulators in tensor memory, warps 2-5 (one per 32-lane quarter of tensor memory) read the
-// accumulator with tcgen05.ld, apply the phases and write the outputs.  Work items (m, row block)
+// copies.  Main kernel: persistent, one CTA per SM, 10 warps: warp 0 lane 0 issues the bulk copies
+// (2-stage ring), warp 1 lane 0 issues tcgen05.mma into one of two 128 x 256 FP32 accumulator
+// segments in tensor memory, warps 2-9 (two per 32-lane quarter of tensor memory, one for each
+// sign of m) read the accumulator with tcgen05.ld, apply the phases and write the outputs (the
+// inverse writes half rows m' >= 0 of F; the torus passes apply the extension).  Work items (m, row block)
 // are sorted by decreasing length and dealt round-robin to the CTAs.  Every wait is bounded; a
 // timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
 #include "ssht_internal.h"
@@ -361,14 +362,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
         if (FWD) {
           a.out[(size_t)b * L * L + (size_t)rowv * rowv + rowv + mm] = F;
         } else {
-          float2* row = a.out + ((size_t)b * NT + (mm + Lp)) * NT;
-          const float2 e = a.ph[rowv + NT - 1];  // e^{i pi m'/N}
-          row[rowv] = make_float2(F.x * e.x - F.y * e.y, F.x * e.y + F.y * e.x);
-          if (rowv > 0) {
-            const float sg = ((mm + s) & 1) ? -1.f : 1.f;
-            const float2 ec = a.ph[-rowv + NT - 1];
-            row[NT - rowv] = make_float2(sg * (F.x * ec.x - F.y * ec.y), sg * (F.x * ec.y + F.y * ec.x));
-          }
+          a.out[((size_t)b * NT + (mm + Lp)) * L + rowv] = F;  // half row m' >= 0
         }
       }
     }

@@ -52,11 +52,12 @@ cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cuda
 // ---------------------------------------------------------------------------
 // SIMT contractions (contract_simt.cu); T is double or float
 // ---------------------------------------------------------------------------
-// Inverse: writes the theta-DFT input E[b][m + Lp][k], k = m' mod N, of the extended,
-// phase-shifted F (eqn fourier_coeff, eqn Ffourier_sym, eqn idft_spatial phase).
+// Inverse: half = 0 writes the theta-DFT input E[b][m + Lp][k], k = m' mod N, of the extended,
+// phase-shifted F (eqn fourier_coeff, eqn Ffourier_sym, eqn idft_spatial phase); half = 1 writes
+// the half rows F[b][m + Lp][m'], 0 <= m' < L, without phases (the torus passes' input).
 template <typename T>
 cudaError_t contract_inverse_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* flm, void* E, const double2* ph, cudaStream_t st);
+                                  const void* flm, void* E, const double2* ph, int half, cudaStream_t st);
 // Projection: flm[b][l*l+l+m] = (-1)^s i^{m+s} c_l sum_{m'>=0} Delta_{m'm} Delta_{m',-s} H[b][m+Lp][m']
 template <typename T>
 cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* table, const double* U,
@@ -74,19 +75,22 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double*
 // Pack the data operand: forward = 0: V from flm (float2 [B][L*L]); forward = 1: Y from the
 // folded torus sums H (float2 [B][N][L]).
 cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches);
-// The contraction: forward = 0 writes the theta-DFT input E (float2 [B][N][N]) of the inverse;
+// The contraction: forward = 0 writes the half rows F (float2 [B][N][L], m' >= 0) of the inverse;
 // forward = 1 writes flm (float2 [B][L*L]).  Timeouts set bit 2 of *status.
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);
 
 // ---------------------------------------------------------------------------
-// Odd-length DFTs of the torus rows (dft.cu), FP32, Bluestein in shared memory
+// Fused torus passes of FP32 plans (torus_pass.cu)
 // ---------------------------------------------------------------------------
-struct DftPlan;
-cudaError_t dft_setup(DftPlan** out, int N);
-void dft_destroy(DftPlan* p);
-size_t dft_bytes(const DftPlan* p);
-// out[row][k] = sum_n in[row][n] e^{sign 2 pi i n k / N} (float2 rows of length N; in == out allowed).
-cudaError_t dft_rows(const DftPlan* p, int sign, long long nrows, const void* in, void* out, cudaStream_t st);
+// Odd-length DFTs along theta and phi (Bluestein in shared memory) with the extension, phases, sin(theta) weight convolution and transpositions folded in.  Layouts (float2):
+// F half rows [B][N][L] (m + Lp, m' >= 0), h [B][L][N], f [B][L][N], X [B][N][L], H [B][N][L].
+struct TorusPlan;
+cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device);
+void torus_destroy(TorusPlan* p);
+size_t torus_bytes(const TorusPlan* p);
+// which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
+// 3 adjoint phi (f -> X), 4 forward theta with the weight convolution (X -> H), 5 adjoint theta (X -> H).
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Torus kernels (torus.cu)

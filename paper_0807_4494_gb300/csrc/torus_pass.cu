@@ -1,0 +1,620 @@
+// Fused torus passes of the FP32 / tensor-core plans: the odd-length DFTs along theta and phi
+// (eqns dft_spatial / idft_spatial, Sec. 3.4.1) with the extension, phase, weight convolution and
+// transposition steps folded into their loads and stores.
+//
+// DFT core.  A row of length N = 2L-1 is transformed by Bluestein's algorithm (see dft.cu): the
+// chirped row goes through a forward FFT of size M = 2^p >= 2N-1, a product with the chirp
+// kernel's spectrum and an inverse FFT.  The FFTs are Stockham autosort passes (radix 16, last
+// pass radix 2/4/8) executed by T = M/16 threads per row; the first pass reads its inputs through a
+// source functor and the last pass hands its outputs to a sink functor, so the chirp and kernel
+// products and the kernels' own input/output transforms cost no extra shared-memory round trip.
+// Twiddles are staged in shared memory once per CTA, one table per pass laid out so that a warp
+// reads consecutive words.
+//
+// Pairing.  Along theta every phi-frequency column m is even or odd about theta = 0 (parity
+// (-1)^{m+s}, Sec. 3.2) and adjacent columns have opposite parities, so one complex DFT serves
+// two columns: z = x_m + x_{m+1} is transformed and the halves are separated afterwards,
+//   x_m(theta_t) = (z(theta_t) + s_m z(theta_{N-1-t}))/2,  x_{m+1}(theta_t) = (z(theta_t) - s_m z(theta_{N-1-t}))/2,
+// (theta_{N-1-t} = 2 pi - theta_t) and in the frequency domain likewise with k -> -k.
+//
+// Kernels (b = field, rows of the torus stored centred, m + Lp):
+//   inverse_theta:  F[b][m][m'] (m' in [0,L), eqn fourier_coeff) -> h[b][t][m mod N] (t < L),
+//                   i.e. theta synthesis with the extension eqn Ffourier_sym and both phases of
+//                   eqn idft_spatial; one pair of columns per row group.
+//   rows (phi):     h[b][t][:] -> f[b][t][:] (inverse), f[b][t][:] -> X[b][m][t] (forward/adjoint).
+//   forward_theta:  X[b][m][t] -> H[b][m][m'] (m' in [0,L)): per-m parity extension, theta DFT,
+//                   then the sin(theta) weight convolution as a zero-padded circular convolution
+//                   of length M in the same shared-memory buffer, and the fold of m' < 0.
+//   adjoint_theta:  X[b][m][t] -> H[b][m][m']: theta DFT of the unextended rings, fold of m' < 0.
+#include "ssht_internal.h"
+
+#include <cmath>
+#include <complex>
+#include <vector>
+
+namespace ssht {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+template <int SIGN>
+__device__ __forceinline__ float2 mul_mi(float2 a) {  // * e^{SIGN i pi/2}
+  return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<SIGN>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// e^{SIGN 2 pi i k/16}, k a compile-time constant after unrolling
+template <int SIGN>
+__device__ __forceinline__ float2 w16(int k) {
+  const float c0 = 1.f, c1 = 0.92387953251128674f, c2 = 0.70710678118654752f, c3 = 0.38268343236508977f;
+  const int kk = k & 15;
+  const float cs[16] = {c0, c1, c2, c3, 0.f, -c3, -c2, -c1, -c0, -c1, -c2, -c3, 0.f, c3, c2, c1};
+  const float s = cs[(kk + 12) & 15];
+  return make_float2(cs[kk], SIGN < 0 ? -s : s);
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R == 2) {
+    const float2 t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  } else if constexpr (R == 4) {
+    dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    float2 a0 = v[0], a1 = v[2], a2 = v[4], a3 = v[6], b0 = v[1], b1 = v[3], b2 = v[5], b3 = v[7];
+    dft4<SIGN>(a0, a1, a2, a3);
+    dft4<SIGN>(b0, b1, b2, b3);
+    b1 = cmul(b1, w16<SIGN>(2));
+    b2 = cmul(b2, w16<SIGN>(4));
+    b3 = cmul(b3, w16<SIGN>(6));
+    v[0] = cadd(a0, b0); v[4] = csub(a0, b0);
+    v[1] = cadd(a1, b1); v[5] = csub(a1, b1);
+    v[2] = cadd(a2, b2); v[6] = csub(a2, b2);
+    v[3] = cadd(a3, b3); v[7] = csub(a3, b3);
+  } else {
+    // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // now v[4 k1 + n2] holds Y[n2][k1]
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<SIGN>(n2 * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4x4 block into natural order
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+  }
+}
+
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// Pass structure of an FFT of size M: P16 radix-16 passes, then one pass of radix REST (1 = none).
+// Pass i has stride NS = 16^i.  Twiddles of pass i >= 1 sit in a table of (R - 1) * NS entries,
+// entry (r - 1) * NS + j' = e^{-2 pi i j' r / (NS R)}, so that consecutive threads read
+// consecutive words; the tables of all passes are stored back to back (about M entries).
+__host__ __device__ constexpr int pow16(int i) { return i == 0 ? 1 : 16 * pow16(i - 1); }
+template <int M> struct Plan16 {
+  static constexpr int P16 = (M >= 4096) ? 3 : (M >= 256) ? 2 : 1;
+  static constexpr int REST = M >> (4 * P16);
+  static constexpr int NP = P16 + (REST > 1 ? 1 : 0);
+  __host__ __device__ static constexpr int radix(int i) { return i < P16 ? 16 : REST; }
+  __host__ __device__ static constexpr int off(int i) { return i <= 1 ? 0 : off(i - 1) + (radix(i - 1) - 1) * pow16(i - 1); }
+  static constexpr int TW = off(NP);  // table entries
+};
+
+// One Stockham pass of radix R and stride NS: inputs through src(i) (first pass) or shared memory,
+// outputs through sink(k, v) (last pass) or shared memory.  twp: this pass's twiddle table.
+template <int M, int R, int NS, int SIGN, bool FROM_SRC, bool TO_SINK, class Src, class Sink>
+__device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Src& src, Sink& sink) {
+  constexpr int T = M / 16;
+  constexpr int J = M / R;
+  constexpr int PER = J / T;
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid + q * T;
+    const int jm = j & (NS - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 x;
+      if constexpr (FROM_SRC) x = src(j + r * J);
+      else x = buf[pidx(j + r * J)];
+      if constexpr (NS > 1) {
+        if (r > 0) {
+          float2 w = twp[(r - 1) * NS + jm];
+          if (SIGN > 0) w = conjf2(w);
+          x = cmul(x, w);
+        }
+      }
+      v[q][r] = x;
+    }
+    dft_reg<R, SIGN>(v[q]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid + q * T;
+    const int d = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (TO_SINK) sink(d + r * NS, v[q][r]);
+      else buf[pidx(d + r * NS)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int M, int SIGN, int I, class Src, class Sink>
+__device__ __forceinline__ void run_passes(float2* buf, int tid, const float2* tw, Src& src, Sink& sink) {
+  using P = Plan16<M>;
+  pass<M, P::radix(I), pow16(I), SIGN, I == 0, I == P::NP - 1>(buf, tid, tw + P::off(I), src, sink);
+  if constexpr (I + 1 < P::NP) run_passes<M, SIGN, I + 1>(buf, tid, tw, src, sink);
+}
+
+// FFT of size M (sign SIGN, unnormalised): inputs through src(i), outputs through sink(k, v),
+// both in natural order.  Ends with a barrier; buf is free afterwards.
+template <int M, int SIGN, class Src, class Sink>
+__device__ __forceinline__ void fft(float2* buf, int tid, const float2* tw, Src src, Sink sink) {
+  run_passes<M, SIGN, 0>(buf, tid, tw, src, sink);
+}
+
+struct TorusTables {
+  const float2* chirp;  // e^{-i pi n^2/N}, n < N
+  const float2* khat_f; // spectrum of the forward-DFT chirp kernel, / M
+  const float2* khat_i; // the same for the inverse DFT
+  const float2* tw;     // per-pass twiddle tables (Plan16<M>::TW entries)
+  const float2* what;   // spectrum of the even sin(theta) weight w_e (zero-padded, length M), / M
+  const float2* ph;     // e^{i pi k/N}, |k| < N, at k + N - 1
+};
+
+// Bluestein DFT of one row: out_k = sum_n in_n e^{SIGN 2 pi i n k/N}.  in through src(n) (n < N),
+// out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.
+template <int M, int SIGN, class Src, class Sink>
+__device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw, const TorusTables& tb, int N, Src src,
+                                          Sink sink) {
+  const float2* khat = SIGN < 0 ? tb.khat_f : tb.khat_i;
+  auto in = [&](int n) {
+    if (n >= N) return make_float2(0.f, 0.f);
+    float2 c = __ldg(&tb.chirp[n]);
+    if (SIGN > 0) c = conjf2(c);
+    return cmul(src(n), c);
+  };
+  auto mid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&khat[k])); };
+  fft<M, -1>(buf, tid, tw, in, mid);
+  auto back = [&](int n) { return buf[pidx(n)]; };
+  auto out = [&](int k, float2 v) {
+    if (k < N) {
+      float2 c = __ldg(&tb.chirp[k]);
+      if (SIGN > 0) c = conjf2(c);
+      sink(k, cmul(v, c));
+    }
+  };
+  fft<M, 1>(buf, tid, tw, back, out);
+}
+
+template <int M> struct Geo {
+  static constexpr int T = M / 16;
+  static constexpr int G = (T >= 256) ? 1 : 256 / T;  // row groups per CTA
+  static constexpr int THREADS = T * G;
+  static constexpr int BUF = M + M / 16;
+  static constexpr int MINB = THREADS >= 512 ? 1 : 3;  // CTAs per SM the register budget is sized for
+  static constexpr int SMEM = (Plan16<M>::TW + G * BUF) * 8;
+};
+
+// Stage the twiddle table in shared memory; returns the row group's buffer.
+template <int M>
+__device__ __forceinline__ float2* setup_smem(const TorusTables& tb, float2** tw_out) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  for (int k = threadIdx.x; k < Plan16<M>::TW; k += blockDim.x) tw[k] = __ldg(&tb.tw[k]);
+  __syncthreads();
+  *tw_out = tw;
+  return sm + Plan16<M>::TW + (threadIdx.x / Geo<M>::T) * Geo<M>::BUF;
+}
+
+// ---------------------------------------------------------------------------------------------
+// inverse theta synthesis: F half rows -> h (phi-DFT input), one pair of columns per row group
+// ---------------------------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_kernel(int L, int s, int B, const float2* __restrict__ F,
+                                                                       float2* __restrict__ h, TorusTables tb) {
+  float2* tw;
+  float2* buf = setup_smem<M>(tb, &tw);
+  const int Lp = L - 1, N = 2 * L - 1;
+  const int tid = threadIdx.x % Geo<M>::T;
+  const long long npairs = (long long)B * L;  // pair p: m = -Lp + 2p (and m + 1 when p < Lp)
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
+    const bool active = u < npairs;
+    const int b = active ? (int)(u / L) : 0, p = active ? (int)(u % L) : 0;
+    const int m = -Lp + 2 * p;
+    const bool two = p < Lp;
+    const float sig = ((m + s) & 1) ? -1.f : 1.f;  // parity of column m; column m+1 has -sig
+    const float2* F0 = F + ((size_t)b * N + (m + Lp)) * L;
+    const float2* F1 = F0 + L;
+    auto src = [&](int n) {
+      if (!active) return make_float2(0.f, 0.f);
+      const int mp = n < L ? n : N - n;  // theta frequency m' (>= 0) of DFT bin n
+      float2 a = F0[mp];
+      const float2 c = two ? F1[mp] : make_float2(0.f, 0.f);
+      float2 z = (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);  // F_{m,-m'} = sig F_{m m'}, column m+1: -sig
+      return cmul(z, tb.ph[(n < L ? mp : -mp) + N - 1]);           // e^{i pi (+-m')/N}
+    };
+    auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };
+    bluestein<M, 1>(buf, tid, tw, tb, N, src, sink);
+    __syncthreads();
+    if (active) {
+      // separate the two columns and write h[b][t][m mod N] with the phi phase e^{i pi m/N}
+      const float2 e0 = tb.ph[m + N - 1], e1 = two ? tb.ph[m + 1 + N - 1] : e0;
+      const int k0 = m >= 0 ? m : m + N, k1 = (m + 1) >= 0 ? m + 1 : m + 1 + N;
+      float2* hb = h + (size_t)b * L * N;
+      for (int t = tid; t < L; t += Geo<M>::T) {
+        const float2 z = buf[pidx(t)], zr = buf[pidx(N - 1 - t)];
+        if (two) {
+          const float2 x0 = cscale(cadd(z, cscale(zr, sig)), 0.5f), x1 = cscale(csub(z, cscale(zr, sig)), 0.5f);
+          hb[(size_t)t * N + k0] = cmul(x0, e0);
+          hb[(size_t)t * N + k1] = cmul(x1, e1);
+        } else {
+          hb[(size_t)t * N + k0] = cmul(z, e0);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// rows along phi: inverse h -> f; forward f -> X[b][m][t] (scale 1/N for the forward transform)
+// ---------------------------------------------------------------------------------------------
+template <int M, int SIGN>
+__global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int L, int B, float scale, const float2* __restrict__ in,
+                                                             float2* __restrict__ out, TorusTables tb) {
+  float2* tw;
+  float2* buf = setup_smem<M>(tb, &tw);
+  const int Lp = L - 1, N = 2 * L - 1;
+  const int tid = threadIdx.x % Geo<M>::T;
+  const long long nrows = (long long)B * L;
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
+    const bool active = u < nrows;
+    const float2* x = in + (size_t)(active ? u : 0) * N;
+    auto src = [&](int n) { return active ? x[n] : make_float2(0.f, 0.f); };
+    if constexpr (SIGN > 0) {
+      float2* y = out + (size_t)(active ? u : 0) * N;
+      auto sink = [&](int k, float2 v) {
+        if (active) y[k] = v;
+      };
+      bluestein<M, SIGN>(buf, tid, tw, tb, N, src, sink);
+    } else {
+      const int b = active ? (int)(u / L) : 0, t = active ? (int)(u % L) : 0;
+      float2* Xb = out + (size_t)b * N * L;
+      auto sink = [&](int k, float2 v) {
+        if (!active) return;
+        const int m = k <= Lp ? k : k - N;
+        Xb[(size_t)(m + Lp) * L + t] = cscale(cmul(v, tb.ph[-m + N - 1]), scale);  // e^{-i pi m/N}
+      };
+      bluestein<M, SIGN>(buf, tid, tw, tb, N, src, sink);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// forward theta analysis with the sin(theta) weight: X[b][m][t] -> H[b][m][m'], pairs of columns
+// ---------------------------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
+                                                                       float2* __restrict__ H, TorusTables tb) {
+  float2* tw;
+  float2* buf = setup_smem<M>(tb, &tw);
+  const int Lp = L - 1, N = 2 * L - 1;
+  const int tid = threadIdx.x % Geo<M>::T;
+  const float invN = 1.f / (float)N;
+  const long long npairs = (long long)B * L;
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
+    const bool active = u < npairs;
+    const int b = active ? (int)(u / L) : 0, p = active ? (int)(u % L) : 0;
+    const int m = -Lp + 2 * p;
+    const bool two = p < Lp;
+    const bool odd0 = ((m + s) & 1) != 0;
+    const float sig = odd0 ? -1.f : 1.f;
+    const float2* X0 = X + ((size_t)b * N + (m + Lp)) * L;
+    const float2* X1 = X0 + L;
+    // extended samples of both columns on theta in [0, 2 pi): the odd one vanishes at theta = pi
+    auto src = [&](int n) {
+      if (!active) return make_float2(0.f, 0.f);
+      const int t = n < L ? n : N - 1 - n;
+      float2 a = X0[t];
+      float2 c = two ? X1[t] : make_float2(0.f, 0.f);
+      if (t == Lp) {
+        if (odd0) a = make_float2(0.f, 0.f);
+        else c = make_float2(0.f, 0.f);
+      }
+      return (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);
+    };
+    // theta DFT -> F (both columns summed) placed at m'' mod M with e^{-i pi m''/N}/N; the M - N
+    // remaining positions receive zeros (k >= N maps onto the gap [L, M - Lp)).
+    auto to_conv = [&](int k, float2 v) {
+      int pos;
+      float2 val;
+      if (k < N) {
+        const int mpp = k <= Lp ? k : k - N;
+        pos = mpp >= 0 ? mpp : mpp + M;
+        val = cscale(cmul(v, tb.ph[-mpp + N - 1]), invN);
+      } else {
+        pos = k - N + L;
+        val = make_float2(0.f, 0.f);
+      }
+      buf[pidx(pos)] = val;
+    };
+    // Bluestein with an all-index sink: run the two FFTs directly so that k >= N reaches to_conv.
+    {
+      auto in = [&](int n) {
+        if (n >= N) return make_float2(0.f, 0.f);
+        return cmul(src(n), __ldg(&tb.chirp[n]));
+      };
+      auto mid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&tb.khat_f[k])); };
+      fft<M, -1>(buf, tid, tw, in, mid);
+      auto back = [&](int n) { return buf[pidx(n)]; };
+      auto out = [&](int k, float2 v) { to_conv(k, k < N ? cmul(v, __ldg(&tb.chirp[k])) : v); };
+      fft<M, 1>(buf, tid, tw, back, out);
+    }
+    // circular convolution with the even weight: y = IFFT(FFT(x) * what), what = FFT(w_e)/M
+    auto cin = [&](int n) { return buf[pidx(n)]; };
+    auto cmid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&tb.what[k])); };
+    fft<M, -1>(buf, tid, tw, cin, cmid);
+    auto cout = [&](int k, float2 v) { buf[pidx(k)] = v; };
+    fft<M, 1>(buf, tid, tw, cin, cout);
+    if (active) {
+      // y[m'] = H'_m[m'] + H'_{m+1}[m'], y[-m'] = sig (H'_m[m'] - H'_{m+1}[m']); fold m' < 0:
+      // H = (2 - delta_{m'0}) 2 pi H'
+      float2* H0 = H + ((size_t)b * N + (m + Lp)) * L;
+      float2* H1 = H0 + L;
+      const float c2 = 6.28318530717958648f, c4 = 12.5663706143591730f;
+      for (int mp = tid; mp < L; mp += Geo<M>::T) {
+        const float2 yp = buf[pidx(mp)], ym = buf[pidx((M - mp) & (M - 1))];
+        const float c = mp == 0 ? c2 : c4;
+        if (two) {
+          H0[mp] = cscale(cadd(yp, cscale(ym, sig)), 0.5f * c);
+          H1[mp] = cscale(csub(yp, cscale(ym, sig)), 0.5f * c);
+        } else {
+          H0[mp] = cscale(yp, c);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// adjoint theta sums: X[b][m][t] (t < L, no extension) -> H[b][m][m'] = H'_{m'} + s_m H'_{-m'}
+// ---------------------------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
+                                                                       float2* __restrict__ H, TorusTables tb) {
+  float2* tw;
+  float2* buf = setup_smem<M>(tb, &tw);
+  const int Lp = L - 1, N = 2 * L - 1;
+  const int tid = threadIdx.x % Geo<M>::T;
+  const long long nrows = (long long)B * N;
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
+    const bool active = u < nrows;
+    const float2* x = X + (size_t)(active ? u : 0) * L;
+    const int m = active ? (int)(u % N) - Lp : 0;
+    auto src = [&](int n) { return (active && n < L) ? x[n] : make_float2(0.f, 0.f); };
+    auto sink = [&](int k, float2 v) {
+      const int mpp = k <= Lp ? k : k - N;
+      buf[pidx(k)] = cmul(v, tb.ph[-mpp + N - 1]);  // H'_{m''} at bin k
+    };
+    bluestein<M, -1>(buf, tid, tw, tb, N, src, sink);
+    __syncthreads();
+    if (active) {
+      const float sig = ((m + s) & 1) ? -1.f : 1.f;
+      float2* Hr = H + (size_t)u * L;
+      for (int mp = tid; mp < L; mp += Geo<M>::T) {
+        const float2 a = buf[pidx(mp)];
+        Hr[mp] = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void host_fft(std::vector<std::complex<double>>& a, int sign) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  const double pi = 3.14159265358979323846;
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const double ang = sign * 2 * pi / (double)len;
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
+
+struct TorusPlan {
+  int L = 0, N = 0, M = 0;
+  float2* buf = nullptr;  // chirp | khat_f | khat_i | what | twiddles (one allocation)
+  TorusTables tb{};
+  size_t bytes = 0;
+  int smem = 0;
+  int grid = 0;
+};
+
+cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
+  *out = nullptr;
+  const int N = 2 * L - 1;
+  int M = 128;
+  while (M < 2 * N - 1) M <<= 1;
+  if (M > 8192) return cudaErrorInvalidValue;
+  TorusPlan* p = new TorusPlan();
+  p->L = L;
+  p->N = N;
+  p->M = M;
+  const double pi = 3.14159265358979323846;
+  // pass structure of the size-M FFT (mirrors Plan16)
+  const int P16 = M >= 4096 ? 3 : M >= 256 ? 2 : 1, REST = M >> (4 * P16);
+  const int NP = P16 + (REST > 1 ? 1 : 0);
+  int TW = 0;
+  for (int i = 1, ns = 16; i < NP; ++i, ns *= 16) TW += ((i < P16 ? 16 : REST) - 1) * ns;
+  std::vector<float2> host((size_t)N + 3 * (size_t)M + (size_t)TW);
+  float2* chirp = host.data();
+  float2* kf = chirp + N;
+  float2* ki = kf + M;
+  float2* wh = ki + M;
+  float2* tw = wh + M;
+  for (int n = 0; n < N; ++n) {
+    const long long r = ((long long)n * n) % (2LL * N);
+    chirp[n] = make_float2((float)std::cos(-pi * r / N), (float)std::sin(-pi * r / N));
+  }
+  {
+    float2* t = tw;
+    for (int i = 1, ns = 16; i < NP; ++i, ns *= 16) {
+      const int R = i < P16 ? 16 : REST;
+      for (int r = 1; r < R; ++r)
+        for (int j = 0; j < ns; ++j) {
+          const double a = -2 * pi * (double)j * r / ((double)ns * R);
+          *t++ = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+  }
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<std::complex<double>> b(M, 0.0);
+    for (int j = -(N - 1); j <= N - 1; ++j) {
+      const long long jj = (long long)j * j % (2LL * N);
+      const double a = (dir == 0 ? 1.0 : -1.0) * pi * (double)jj / (double)N;
+      b[(j + M) % M] = std::complex<double>(std::cos(a), std::sin(a));
+    }
+    host_fft(b, -1);
+    float2* dst = dir == 0 ? kf : ki;
+    for (int k = 0; k < M; ++k) dst[k] = make_float2((float)(b[k].real() / M), (float)(b[k].imag() / M));
+  }
+  {
+    // w_e(p) = 2/(1-p^2) for even |p| <= 2(L-1), placed at p mod M (M >= 4L-3 > 4(L-1): no overlap)
+    std::vector<std::complex<double>> w(M, 0.0);
+    for (int q = -2 * (L - 1); q <= 2 * (L - 1); q += 2) w[(q + M) % M] = 2.0 / (1.0 - (double)q * q);
+    host_fft(w, -1);
+    for (int k = 0; k < M; ++k) wh[k] = make_float2((float)(w[k].real() / M), (float)(w[k].imag() / M));
+  }
+  cudaError_t e = cudaMalloc(&p->buf, host.size() * sizeof(float2));
+  if (e != cudaSuccess) {
+    delete p;
+    return e;
+  }
+  p->bytes = host.size() * sizeof(float2);
+  e = cudaMemcpy(p->buf, host.data(), p->bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    torus_destroy(p);
+    return e;
+  }
+  p->tb.chirp = p->buf;
+  p->tb.khat_f = p->buf + N;
+  p->tb.khat_i = p->buf + N + M;
+  p->tb.what = p->buf + N + 2 * M;
+  p->tb.tw = p->buf + N + 3 * M;
+  p->tb.ph = (const float2*)ph;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  p->grid = sms * 8;
+#define SSHT_TP_ATTR(MM)                                                                               \
+  if (M == MM) {                                                                                       \
+    if (Plan16<MM>::TW != TW) {                                                                        \
+      torus_destroy(p);                                                                                \
+      return cudaErrorInvalidValue;                                                                    \
+    }                                                                                                  \
+    p->smem = Geo<MM>::SMEM;                                                                           \
+    if ((e = set_smem(inverse_theta_kernel<MM>, p->smem)) != cudaSuccess ||                            \
+        (e = set_smem(phi_kernel<MM, 1>, p->smem)) != cudaSuccess ||                                   \
+        (e = set_smem(phi_kernel<MM, -1>, p->smem)) != cudaSuccess ||                                  \
+        (e = set_smem(forward_theta_kernel<MM>, p->smem)) != cudaSuccess ||                            \
+        (e = set_smem(adjoint_theta_kernel<MM>, p->smem)) != cudaSuccess) {                            \
+      torus_destroy(p);                                                                                \
+      return e;                                                                                        \
+    }                                                                                                  \
+  }
+  SSHT_TP_ATTR(128) SSHT_TP_ATTR(256) SSHT_TP_ATTR(512) SSHT_TP_ATTR(1024) SSHT_TP_ATTR(2048)
+  SSHT_TP_ATTR(4096) SSHT_TP_ATTR(8192)
+#undef SSHT_TP_ATTR
+  *out = p;
+  return cudaSuccess;
+}
+
+void torus_destroy(TorusPlan* p) {
+  if (!p) return;
+  if (p->buf) cudaFree(p->buf);
+  delete p;
+}
+
+size_t torus_bytes(const TorusPlan* p) { return p ? p->bytes : 0; }
+
+// which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
+// 3 adjoint phi (f -> X, no scale), 4 forward theta (X -> H), 5 adjoint theta (X -> H).
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st) {
+  const int L = p->L, M = p->M;
+  const long long rows = (which == 1 || which == 2 || which == 3) ? (long long)B * L
+                         : (which == 5)                            ? (long long)B * p->N
+                                                                   : (long long)B * L;  // pairs
+#define SSHT_TP_LAUNCH(MM)                                                                                   \
+  if (M == MM) {                                                                                             \
+    const long long need = (rows + Geo<MM>::G - 1) / Geo<MM>::G;                                            \
+    const unsigned blocks = (unsigned)std::min<long long>(need, (long long)p->grid);                        \
+    const dim3 thr(Geo<MM>::THREADS);                                                                        \
+    const float2* I = (const float2*)in;                                                                     \
+    float2* O = (float2*)out;                                                                                \
+    switch (which) {                                                                                         \
+      case 0: inverse_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
+      case 1: phi_kernel<MM, 1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;               \
+      case 2: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f / (float)p->N, I, O, p->tb); break; \
+      case 3: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;              \
+      case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
+      case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
+      default: return cudaErrorInvalidValue;                                                                 \
+    }                                                                                                        \
+    return cudaGetLastError();                                                                               \
+  }
+  SSHT_TP_LAUNCH(128) SSHT_TP_LAUNCH(256) SSHT_TP_LAUNCH(512) SSHT_TP_LAUNCH(1024) SSHT_TP_LAUNCH(2048)
+  SSHT_TP_LAUNCH(4096) SSHT_TP_LAUNCH(8192)
+#undef SSHT_TP_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ssht
