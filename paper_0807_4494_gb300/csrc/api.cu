@@ -499,7 +499,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
     return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
                 std::string("Delta recursion setup: ") + cudaGetErrorString(ce));
   }
-  p->bytes += delta_offset(L) * 8 + 2 * tri(L + 1) * 8;
+  p->bytes += p->delta.bytes;
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
   // rows of N x L only.

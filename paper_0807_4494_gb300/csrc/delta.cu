@@ -10,20 +10,23 @@
 //   d_{mn} = (-1)^{m-n} d_{-m,-n}         (eqn wignerd_sym1),
 //   Delta^l_{m,-n} = (-1)^{l+m} Delta^l_{mn}  (eqn wignerd_sym1 with eqn wignerd_sym2, integer l).
 //
-// Storage.  Integer degree l: octant slab Y[m(m+1)/2 + n], 0 <= n <= m <= l.
-// Half-integer degree l+1/2: rows a = A + 1/2 (A = 0..l), columns b = B - 1/2 (B = 0..A+1),
-// i.e. the octant plus the column b = -1/2, at A(A+3)/2 + B.
+// Storage.  The octant slab of integer degree l keeps row m (0 <= m <= l) with the columns
+// n = -1 .. m+1, the two extra ones holding Delta_{m,-1} and Delta_{m,m+1} (given by the symmetry
+// relations), so that every stencil read is a plain indexed load; the half-integer rows are laid
+// out the same way in shared memory.
 //
-// Parallel layout.  One cooperative persistent grid walks l.  For the step l -> l+1 the
-// rows of the new integer slab are split over the CTAs by equal entry counts.  A CTA that
-// owns integer rows [r0, r1) works through them in chunks [c0, c1) sized to its shared
-// memory: it copies the contiguous packed integer rows [c0-1, c1] of degree l from global
-// memory into shared memory (coalesced), computes from them the half-integer rows
-// [c0-1, c1-1] (one row is also computed by the neighbouring chunk), then the integer rows
-// [c0, c1), which it writes to the next octant buffer and, in both orientations, to the
-// quadrant table.  So each degree costs one grid barrier, and the four operands of every
-// update come from shared memory.  The barrier spins at most one second, then latches a
-// status bit and every CTA leaves the kernel.
+// Parallel layout.  One cooperative persistent grid walks l.  For the step l -> l+1 the rows
+// of the new integer slab are split over the CTAs in equal numbers of 32-column segments (a
+// warp computes one segment per instruction stream).  A CTA that owns integer rows [r0, r1)
+// works through them in chunks [c0, c1) sized to its shared memory: it copies the padded rows
+// [c0-1, c1] of degree l from global memory into shared memory, computes the half-integer rows
+// [c0-1, c1-1], then the integer rows [c0, c1), which go to the next slab (global) and to
+// shared memory.  It then publishes "degree l+1 done" in its flag word and writes the rows to the
+// quadrant table from shared memory, both orientations coalesced, while its neighbours already
+// proceed.  Before step l -> l+1 a CTA waits only for the CTAs that produced the rows of degree l
+// it reads (which are also all the readers of the slab rows it overwrites): no grid-wide barrier
+// per degree.  Every wait spins at most one second, then latches a status bit, raises the abort
+// flag and leaves the kernel; the other CTAs leave at their next wait.
 #include "ssht_internal.h"
 
 #include <algorithm>
@@ -37,11 +40,8 @@ namespace {
 #ifndef SSHT_RISBO_THREADS
 #define SSHT_RISBO_THREADS 512
 #endif
-#ifndef SSHT_RISBO_UNROLL
-#define SSHT_RISBO_UNROLL 1
-#endif
 #ifndef SSHT_RISBO_MARK
-#define SSHT_RISBO_MARK(k)  // phase boundary: 1 prologue, 2 staged, 3 half step, 4 integer step, 5 barrier
+#define SSHT_RISBO_MARK(k)  // phase boundary: 1 waited, 2 staged, 3 half step, 4 integer step, 5 table written
 #endif
 constexpr int kThreads = SSHT_RISBO_THREADS;
 
@@ -51,7 +51,7 @@ struct RisboParams {
   double* slab0;
   double* slab1;
   const double* sq;         // sqrt(k)
-  unsigned int* counter;    // [0] barrier counter, [1] abort flag (reset before launch)
+  unsigned int* counter;    // [0] barrier counter, [1] abort flag, [4 + c] degree done by CTA c (reset before launch)
   int* status;              // latched status bits
 };
 
@@ -100,45 +100,46 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* st
 }
 
 __host__ __device__ __forceinline__ long long tri_ll(long long m) { return m * (m + 1) / 2; }
-__host__ __device__ __forceinline__ long long hoff_ll(long long A) { return A * (A + 3) / 2; }
 
-// Largest m with tri(m) <= e.
-__device__ __forceinline__ int tri_row(long long e) {
-  int m = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  while (m > 0 && tri_ll(m) > e) --m;
-  while (tri_ll(m + 1) <= e) ++m;
-  return m;
+// Padded row layout shared by the octant slabs (global) and the staged rows (shared memory):
+// row m holds columns n = -1 .. m+1 at po(m) + n + 1, po(m) = m(m+5)/2 (row m has m+3 slots).
+// The two extra columns carry Delta_{m,-1} and Delta_{m,m+1}, which the symmetry relations give
+// from stored entries; with them every stencil read of a step is a plain indexed load.
+__host__ __device__ __forceinline__ long long po(long long m) { return m * (m + 5) / 2; }
+
+// Segments of 32 columns in rows 1 .. n of lengths 1 .. n: sum_{k=1}^{n} ceil(k/32).
+__host__ __device__ __forceinline__ long long segF(long long n) {
+  const long long q = n >> 5, r = n & 31;
+  return 16 * q * (q + 1) + r * (q + 1);
 }
 
-// Largest A with hoff(A) <= i.
-__device__ __forceinline__ int hoff_row(long long i) {
-  int A = (int)((sqrtf(8.0f * (float)i + 9.0f) - 3.0f) * 0.5f);
-  if (A < 0) A = 0;
-  while (A > 0 && hoff_ll(A) > i) --A;
-  while (hoff_ll(A + 1) <= i) ++A;
-  return A;
+// Work of integer rows [0, m) of a step, half rows included, in 32-column segments: row k has
+// k + 2 half-integer and k + 1 integer columns.
+__host__ __device__ __forceinline__ long long row_cost(long long m) { return segF(m + 1) - 1 + segF(m); }
+
+// Row m0 of the split of rows [0, rows) with cut o of nb: the smallest m with
+// row_cost(m) >= floor(row_cost(rows) * o / nb).
+__host__ __device__ __forceinline__ int cut_row(int rows, int o, int nb) {
+  const long long x = row_cost(rows) * o / nb;
+  int a = 0, b = rows;
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (row_cost(mid) >= x) b = mid; else a = mid + 1;
+  }
+  return a;
 }
 
-// Work of integer rows [0, m) of a step, half rows included: row m costs (m+1) integer and
-// (m+2) half-integer updates, so C(m) = sum_{k<m} (2k+3) = m^2 + 2m.
-__host__ __device__ __forceinline__ long long row_cost(long long m) { return m * m + 2 * m; }
-
-// Smallest m with C(m) >= x.  FP32 first guess, exact integer correction (FP64 arithmetic is
-// costly on this part and is kept for the recursion itself).
-__host__ __device__ __forceinline__ int share_row(long long x, int rows) {
-  int m = (int)(sqrtf(1.0f + (float)x) - 1.0f);
-  if (m < 0) m = 0;
-  if (m > rows) m = rows;
-  while (m > 0 && row_cost(m - 1) >= x) --m;
-  while (m < rows && row_cost(m) < x) ++m;
-  return m;
-}
-
-// Rows [r0, r1) of the new integer slab of degree lp owned by CTA cta of nb, balanced on C.
+// Rows [r0, r1) of the integer slab of degree lp (rows 0 .. lp) owned by CTA cta of nb.
 __host__ __device__ __forceinline__ void cta_rows(int lp, int cta, int nb, int* r0, int* r1) {
-  const long long S = row_cost(lp + 1);
-  *r0 = share_row(S * cta / nb, lp + 1);
-  *r1 = share_row(S * (cta + 1) / nb, lp + 1);
+  *r0 = cut_row(lp + 1, cta, nb);
+  *r1 = cut_row(lp + 1, cta + 1, nb);
+}
+
+// The CTA that owns row `row` of degree l: the largest o with cut_row(l + 1, o, nb) <= row.
+__host__ __device__ __forceinline__ int row_owner(int l, int row, int nb) {
+  const long long S = row_cost(l + 1);
+  const long long o = ((row_cost(row) + 1) * nb + S - 1) / S - 1;
+  return (int)(o < nb - 1 ? o : nb - 1);
 }
 
 // v with its sign flipped when neg is set, by integer ops on the sign bit (a multiplication by
@@ -147,55 +148,55 @@ __device__ __forceinline__ double flip(double v, bool neg) {
   return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
 }
 
-// Integer slab of degree l staged in shared memory from row ybase on (packed rows), any (m, n)
-// with 0 <= m <= l+1 and -1 <= n <= m+1.
-__device__ __forceinline__ double yget(const double* __restrict__ Y, int l, long long ybase, int m, int n) {
-  bool neg = false;
-  if (n == -1) {
-    if (m == 0) {  // Delta_{0,-1} = (-1)^l Delta_{0,1} = (-1)^{l+1} Delta_{1,0}
-      neg = (l & 1) == 0;
-      m = 1;
-      n = 0;
-    } else {       // Delta_{m,-1} = (-1)^{l+m} Delta_{m,1}
-      neg = ((l + m) & 1) != 0;
-      n = 1;
-    }
-  }
-  if (n > m) {     // transpose
-    if ((n - m) & 1) neg = !neg;
-    const int t = m; m = n; n = t;
-  }
-  if (m > l) return 0.0;
-  return flip(Y[tri_ll(m) + n - ybase], neg);
-}
+// Doubles of one padded octant slab for band-limit L (rows 0 .. L, with slack).
+__host__ __device__ constexpr size_t slab_doubles(long long L) { return (size_t)((L + 2) * (L + 7) / 2 + 2); }
 
-// Half-integer slab of degree l+1/2 held in shared memory from row Alo on,
-// any (A, B) with -1 <= A <= l+1 and 0 <= B <= A+2.
-__device__ __forceinline__ double xget(const double* __restrict__ X, int l, long long hbase, int A, int B) {
-  bool neg = false;
-  if (A == -1) {   // a = -1/2
-    if (B == 0) {  // (-1/2,-1/2) = (1/2,1/2)
-      A = 0; B = 1;
-    } else {       // (-1/2,1/2) = -(1/2,-1/2)
-      A = 0; B = 0; neg = true;
-    }
-  }
-  if (B > A + 1) { // b > a: transpose (a,b) -> (b,a), sign (-1)^{a-b}
-    if ((B - A - 1) & 1) neg = !neg;
-    const int nA = B - 1, nB = A + 1;
-    A = nA; B = nB;
-  }
-  if (A > l) return 0.0;
-  return flip(X[hoff_ll(A) + B - hbase], neg);
-}
-
-// Shared-memory doubles needed to produce integer rows [c0, c1) of degree l+1 from degree l:
-// the staged integer rows [Alo, min(Ahi+1, l)] and the half rows [Alo, Ahi].
+// Shared-memory doubles for integer rows [c0, c1) of degree l+1 made from degree l: integer rows
+// [Alo, Ahi + 1] and half rows [Alo - 1, c1 - 1] (row Alo - 1 has two slots), all padded, the new
+// rows [c0, c1) packed (for the table writes), and the row factors of both steps.
 __host__ __device__ __forceinline__ long long chunk_need(int l, int c0, int c1) {
   const int Alo = c0 > 0 ? c0 - 1 : 0;
   const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;
-  const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l;
-  return (tri_ll(Ytop + 1) - tri_ll(Alo)) + (hoff_ll(Ahi + 1) - hoff_ll(Alo));
+  return (po(Ahi + 2) - po(Alo)) + 2 + (po(c1) - po(Alo)) + (tri_ll(c1) - tri_ll(c0)) + 2 * (Ahi - Alo + 1) +
+         2 * (c1 - c0);
+}
+
+// 32-bit forms of the index maps for the kernel (all values stay below 2^31 for L <= 2048).
+__device__ __forceinline__ int po32(int m) { return m * (m + 5) / 2; }
+__device__ __forceinline__ int tri32(int m) { return m * (m + 1) / 2; }
+__device__ __forceinline__ int segF32(int n) {
+  const int q = n >> 5, r = n & 31;
+  return 16 * q * (q + 1) + r * (q + 1);
+}
+// Largest n >= 0 with segF(n) <= t (t >= 0): the 32-column block q from a square root, then the
+// column in it by one division.
+__device__ __forceinline__ int segF_inv(int t) {
+  int q = (int)((sqrtf(1.0f + 0.25f * (float)t) - 1.0f) * 0.5f);
+  if (q < 0) q = 0;
+  while (q > 0 && 16 * q * (q + 1) > t) --q;
+  while (16 * (q + 1) * (q + 2) <= t) ++q;
+  int r = (t - 16 * q * (q + 1)) / (q + 1);
+  return 32 * q + (r < 31 ? r : 31);
+}
+
+// A warp's share of the 32-column segments of rows [lo, hi] whose row x has x + add columns:
+// the first row x, the segment in it, and the number of segments; the shares of the warps of a
+// CTA are contiguous and equal to within one.
+struct SegRange {
+  int x, seg, count;
+};
+__device__ __forceinline__ SegRange warp_segments(int lo, int hi, int add, int warp, int nwarps) {
+  const int base = segF32(lo + add - 1);
+  const int S = segF32(hi + add) - base;
+  const int s0 = S * warp / nwarps, s1 = S * (warp + 1) / nwarps;
+  int x = segF_inv(base + s0) - add + 1;
+  if (x > hi) x = hi;
+  if (x < lo) x = lo;
+  SegRange r;
+  r.x = x;
+  r.seg = s0 - (segF32(x + add - 1) - base);
+  r.count = s1 - s0;
+  return r;
 }
 
 // 1/k to FP64 accuracy without an FP64 division: FP32 reciprocal, then two Newton steps.
@@ -206,145 +207,245 @@ __device__ __forceinline__ double recip(double k) {
   return r;
 }
 
-constexpr int kUnroll = SSHT_RISBO_UNROLL;  // independent updates in flight per thread
-constexpr int kRowCap = 512; // rows of pre-scaled row factors kept per chunk
+// Thread 0 waits until every flag of CTAs [o0, o1] has reached `degree` (acquire), one second at
+// most; all threads then learn whether to go on.
+__device__ bool wait_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
+                           int* status) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int good = 1;
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int spins = 0;
+    for (int o = o0; o <= o1 && good; ++o) {
+      while (ld_acquire_u32(done + o) < degree) {
+        if ((++spins & 63u) == 0u) {
+          if (*(volatile unsigned int*)abort_flag != 0u) { good = 0; break; }
+          if (globaltimer_ns() - t0 > 1000000000ull) {
+            atomicOr(status, kStatusBarrierTimeout);
+            atomicExch(abort_flag, 1u);
+            good = 0;
+            break;
+          }
+        }
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
 
 __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long long cap) {
   extern __shared__ double smem[];
-  __shared__ int s_rows[2];
-  __shared__ double s_scale[2];
-  // Rows and step scales p/(2j) of step l -> l + 1, computed while the previous barrier waits.
-  auto params = [&](int l) {
-    const int lp = l + 1;
-    cta_rows(lp, blockIdx.x, gridDim.x, &s_rows[0], &s_rows[1]);
-    s_scale[0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
-    s_scale[1] = 0.70710678118654752440 * recip((double)(2 * lp));
-  };
-  // row factors sqrt(j+a) p/(2j), sqrt(j-a) p/(2j) of the half step (s_ra, s_rb) and the integer step
-  __shared__ double s_ra[kRowCap + 2], s_rb[kRowCap + 2], s_ia[kRowCap + 2], s_ib[kRowCap + 2];
+  // Per step l -> l + 1 (slot l & 1): owned rows r0, r1 of degree l + 1, the CTAs o0..o1 that
+  // produced the degree-l rows read here, and the step scales p/(2j).
+  __shared__ int s_par[2][4];
+  __shared__ double s_sc[2][2];
   const int nb = gridDim.x;
   const int cta = blockIdx.x;
-  if (cta == 0 && threadIdx.x == 0) {
-    P.slab0[0] = 1.0;
-    P.table[0] = 1.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  auto params = [&](int l) {
+    int* q = s_par[l & 1];
+    const int lp = l + 1;
+    int r0, r1;
+    cta_rows(lp, cta, nb, &r0, &r1);
+    q[0] = r0;
+    q[1] = r1;
+    // Degree-l rows [r0 - 2, r1 + 1]: the rows staged here, and the rows whose producers also
+    // read (one step earlier) the slab rows this CTA overwrites, pad slots included.
+    const int a = r0 - 2 > 0 ? r0 - 2 : 0, b = r1 + 1 < l ? r1 + 1 : l;
+    q[2] = row_owner(l, a, nb);
+    q[3] = row_owner(l, b, nb);
+    s_sc[l & 1][0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
+    s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
+  };
+  const double* __restrict__ sq = P.sq;
+  unsigned int* done = P.counter + 4;
+  if (cta == 0 && threadIdx.x < 3) {  // degree 0: row 0 = (Delta_{0,-1}, Delta_00, Delta_01) = (0, 1, 0)
+    P.slab0[threadIdx.x] = threadIdx.x == 1 ? 1.0 : 0.0;
+    if (threadIdx.x == 0) P.table[0] = 1.0;
   }
-  unsigned int phase = 1;
-  if (!grid_barrier(P.counter, phase * nb, P.status, [&] { params(0); })) return;
+  if (!grid_barrier(P.counter, nb, P.status, [&] { params(0); })) return;
   for (int l = 0; l + 1 < P.L; ++l) {
+    __syncthreads();  // params(l) visible; every thread is done with step l - 1
+    const int lp = l + 1;
+    const int r0 = s_par[l & 1][0], r1 = s_par[l & 1][1];
+    const int o0 = s_par[l & 1][2], o1 = s_par[l & 1][3];
+    const double sc = s_sc[l & 1][0], sc2 = s_sc[l & 1][1];
+    if (threadIdx.x == 32 && l + 2 < P.L) params(l + 1);
+    if (r0 >= r1) {  // nothing owned at this degree: nothing to wait for or to publish but progress
+      if (threadIdx.x == 0) atomicExch(done + cta, (unsigned)lp);
+      continue;
+    }
+    if (!wait_flags(done, o0, o1, (unsigned)l, P.counter + 1, P.status)) return;
+    SSHT_RISBO_MARK(1);
     const double* __restrict__ Yg = (l & 1) ? P.slab1 : P.slab0;
     double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
-    const int lp = l + 1;
-    const int r0 = s_rows[0], r1 = s_rows[1];
-    const double sc = s_scale[0], sc2 = s_scale[1];
-    SSHT_RISBO_MARK(1);
     double* __restrict__ T = P.table + (size_t)((long long)lp * (lp + 1) * (2 * lp + 1) / 6);
     for (int c0 = r0; c0 < r1;) {
-      // Largest c1 <= min(r1, c0 + kRowCap) whose chunk fits (chunk_need grows with c1).
-      int lo = c0 + 1, hi = (r1 < c0 + kRowCap) ? r1 : c0 + kRowCap;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (chunk_need(l, c0, mid) <= cap) lo = mid; else hi = mid - 1;
+      // The whole share in one chunk when it fits (the usual case), else the largest c1 that fits.
+      int c1 = r1;
+      if (chunk_need(l, c0, r1) > cap) {
+        int lo = c0 + 1, hi = r1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (chunk_need(l, c0, mid) <= cap) lo = mid; else hi = mid - 1;
+        }
+        c1 = lo;
       }
-      const int c1 = lo;
       const int Alo = c0 > 0 ? c0 - 1 : 0;
-      const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;
-      const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l;
-      const long long ybase = tri_ll(Alo);
-      const int ycount = (int)(tri_ll(Ytop + 1) - ybase);
-      const long long hbase = hoff_ll(Alo);
-      const int hcount = (int)(hoff_ll(Ahi + 1) - hbase);
-      double* __restrict__ Ys = smem;
-      double* __restrict__ Xs = smem + ycount;
-      __syncthreads();  // the previous chunk is done with shared memory
-      // Stage the contiguous packed rows [Alo, Ytop] of the integer slab (asynchronous copies,
-      // all in flight together); pre-scale the row factors meanwhile.
+      const int Ahi = (c1 - 1 < l) ? c1 - 1 : l;   // half rows computed here
+      const int Ytop = (Ahi + 1 < l) ? Ahi + 1 : l; // integer rows staged from degree l
+      const int ybase = po32(Alo);
+      const int ycount = po32(Ytop + 1) - ybase;
+      const int z0 = tri32(c0);
+      double* __restrict__ Ys = smem;                              // integer rows [Alo, Ahi + 1]
+      double* __restrict__ Xs = smem + (po32(Ahi + 2) - ybase);    // half rows [Alo - 1, c1 - 1]
+      double* __restrict__ Zs = Xs + 2 + (po32(c1) - ybase);       // new rows [c0, c1), packed
+      double* __restrict__ Rh = Zs + (tri32(c1) - z0);             // half-step row factors, 2 per row
+      double* __restrict__ Ri = Rh + 2 * (Ahi - Alo + 1);          // integer-step row factors
+      if (c0 > r0) __syncthreads();  // the previous chunk is done with shared memory
+      // Stage the contiguous padded rows [Alo, Ytop] of degree l (asynchronous copies, all in
+      // flight together).  Rows beyond l are zero: the integer row l + 1 (when Ahi = l) and the
+      // half row l + 1 (when c1 - 1 = l + 1), whose padded neighbour slot in row l is zero too.
       for (int i = threadIdx.x; i < ycount; i += blockDim.x) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(Ys + i);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(Yg + ybase + i) : "memory");
       }
+      if (Ytop < Ahi + 1)
+        for (int i = threadIdx.x; i < l + 4; i += blockDim.x) Ys[po32(l + 1) - ybase + i] = 0.0;
+      if (c1 - 1 > l)
+        for (int i = threadIdx.x; i < l + 4; i += blockDim.x) Xs[2 + po32(l + 1) - ybase + i] = 0.0;
+      // Row factors: sqrt(j+a) p/(2j), sqrt(j-a) p/(2j) of both steps.
       for (int A = Alo + (int)threadIdx.x; A <= Ahi; A += blockDim.x) {
-        s_ra[A - Alo] = P.sq[l + A + 1] * sc;  // j + a = l + A + 1
-        s_rb[A - Alo] = P.sq[l - A] * sc;      // j - a = l - A
+        Rh[2 * (A - Alo)] = sq[l + A + 1] * sc;  // j + a = l + A + 1
+        Rh[2 * (A - Alo) + 1] = sq[l - A] * sc;  // j - a = l - A
       }
       for (int m = c0 + (int)threadIdx.x; m < c1; m += blockDim.x) {
-        s_ia[m - c0] = P.sq[lp + m] * sc2;
-        s_ib[m - c0] = P.sq[lp - m] * sc2;
+        Ri[2 * (m - c0)] = sq[lp + m] * sc2;
+        Ri[2 * (m - c0) + 1] = sq[lp - m] * sc2;
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
       SSHT_RISBO_MARK(2);
-      // Half step l -> l + 1/2 (2j = 2l + 1): j+b = l+B, j-b = l+1-B.
-      for (int base = threadIdx.x; base < hcount; base += kUnroll * blockDim.x) {
-        double x1[kUnroll], x2[kUnroll], x3[kUnroll], x4[kUnroll], sb[kUnroll], smb[kUnroll], ra[kUnroll], rb[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int i = base + u * blockDim.x;
-          const int ii = i < hcount ? i : hcount - 1;
-          const int A = hoff_row(hbase + ii);
-          const int B = (int)(hbase + ii - hoff_ll(A));
-          x1[u] = yget(Ys, l, ybase, A, B - 1);
-          x2[u] = yget(Ys, l, ybase, A, B);
-          x3[u] = yget(Ys, l, ybase, A + 1, B - 1);
-          x4[u] = yget(Ys, l, ybase, A + 1, B);
-          sb[u] = P.sq[l + B];
-          smb[u] = P.sq[l + 1 - B];
-          ra[u] = s_ra[A - Alo];
-          rb[u] = s_rb[A - Alo];
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int i = base + u * blockDim.x;
-          const double t1 = fma(-smb[u], x2[u], sb[u] * x1[u]);
-          const double t2 = fma(smb[u], x4[u], sb[u] * x3[u]);
-          const double v = fma(ra[u], t1, rb[u] * t2);
-          if (i < hcount) Xs[i] = v;
-        }
-      }
-      __syncthreads();
-      SSHT_RISBO_MARK(3);
-      // Integer step l + 1/2 -> lp (2j = 2 lp).
-      const long long e0 = tri_ll(c0);
-      const int ecount = (int)(tri_ll(c1) - e0);
-      for (int base = threadIdx.x; base < ecount; base += kUnroll * blockDim.x) {
-        double x1[kUnroll], x2[kUnroll], x3[kUnroll], x4[kUnroll], sb[kUnroll], smb[kUnroll], ra[kUnroll], rb[kUnroll];
-        int mm[kUnroll], nn[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int i = base + u * blockDim.x;
-          const long long e = e0 + (i < ecount ? i : ecount - 1);
-          const int m = tri_row(e);
-          const int n = (int)(e - tri_ll(m));
-          mm[u] = m;
-          nn[u] = n;
-          x1[u] = xget(Xs, l, hbase, m - 1, n);
-          x2[u] = xget(Xs, l, hbase, m - 1, n + 1);
-          x3[u] = xget(Xs, l, hbase, m, n);
-          x4[u] = xget(Xs, l, hbase, m, n + 1);
-          sb[u] = P.sq[lp + n];
-          smb[u] = P.sq[lp - n];
-          ra[u] = s_ia[m - c0];
-          rb[u] = s_ib[m - c0];
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int i = base + u * blockDim.x;
-          const double t1 = fma(-smb[u], x2[u], sb[u] * x1[u]);
-          const double t2 = fma(smb[u], x4[u], sb[u] * x3[u]);
-          const double v = fma(ra[u], t1, rb[u] * t2);
-          if (i < ecount) {
-            const int m = mm[u], n = nn[u];
-            Yn[e0 + i] = v;
-            T[(size_t)m * (lp + 1) + n] = v;
-            if (n != m) T[(size_t)n * (lp + 1) + m] = flip(v, ((m - n) & 1) != 0);
+      // Half step l -> l + 1/2 (2j = 2l + 1), half rows A in [Alo, Ahi], columns B in [0, A+1]
+      // (a = A + 1/2, b = B - 1/2): j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.
+      {
+        const SegRange w = warp_segments(Alo, Ahi, 2, warp, nwarps);
+        int A = w.x, seg = w.seg;
+        int yo = po32(A) - ybase;  // row A of Ys; half row A of Xs is at 2 + yo
+        double ra = Rh[2 * (A - Alo)], rb = Rh[2 * (A - Alo) + 1];
+        for (int k = 0; k < w.count; ++k) {
+          const int B = seg * 32 + lane;
+          if (B <= A + 1) {
+            const double* y0 = Ys + yo + B;          // Y(A, B-1), Y(A, B)
+            const double* y1 = y0 + (A + 3);         // Y(A+1, B-1), Y(A+1, B)
+            const double sb = sq[l + B], smb = sq[l + 1 - B];
+            const double t1 = fma(-smb, y0[1], sb * y0[0]);
+            const double t2 = fma(smb, y1[1], sb * y1[0]);
+            const double v = fma(ra, t1, rb * t2);
+            double* xr = Xs + 2 + yo;
+            xr[B] = v;
+            if (B == A) {
+              if (A > Alo) xr[-1] = flip(v, true);       // pad of row A-1: X(A-1, A+1) = -X(A, A)
+              else if (A == 0) Xs[1] = flip(v, true);    // X(-1/2, 1/2) = -X(1/2, -1/2)
+            }
+            if (A == 0 && B == 1) Xs[0] = v;             // X(-1/2, -1/2) = X(1/2, 1/2)
+          }
+          if (++seg * 32 > A + 1) {
+            yo += A + 3;
+            ++A;
+            seg = 0;
+            if (A <= Ahi) {
+              ra = Rh[2 * (A - Alo)];
+              rb = Rh[2 * (A - Alo) + 1];
+            }
           }
         }
       }
+      if (c1 - 1 > l && threadIdx.x == 0) Xs[2 + (po32(l) - ybase) + l + 2] = 0.0;  // X(l, l+2) = -X(l+1, l+1) = 0
+      __syncthreads();
+      SSHT_RISBO_MARK(3);
+      // Integer step l + 1/2 -> lp (2j = 2 lp), rows m in [c0, c1), columns n in [0, m]:
+      // j+m = lp+m, j-m = lp-m, j+n = lp+n, j-n = lp-n; X(m - 1/2, .) is half row m - 1.
+      {
+        const SegRange w = warp_segments(c0, c1 - 1, 1, warp, nwarps);
+        int m = w.x, seg = w.seg;
+        int xo = 2 + po32(m) - ybase;  // half row m in Xs (row m - 1 starts m + 2 earlier; row -1 at 0)
+        int zo = tri32(m) - z0;
+        double* yr = Yn + po32(m);
+        double ia = Ri[2 * (m - c0)], ib = Ri[2 * (m - c0) + 1];
+        for (int k = 0; k < w.count; ++k) {
+          const int n = seg * 32 + lane;
+          if (n <= m) {
+            const double* x0 = Xs + (m > 0 ? xo - (m + 2) : 0) + n;  // X(m-1, n), X(m-1, n+1)
+            const double* x1 = Xs + xo + n;                          // X(m, n), X(m, n+1)
+            const double sb = sq[lp + n], smb = sq[lp - n];
+            const double t1 = fma(-smb, x0[1], sb * x0[0]);
+            const double t2 = fma(smb, x1[1], sb * x1[0]);
+            const double v = fma(ia, t1, ib * t2);
+            yr[n + 1] = v;
+            if (n == 1) yr[0] = flip(v, ((lp + m) & 1) != 0);            // Delta_{m,-1} = (-1)^{l+m} Delta_{m,1}
+            if (n + 1 == m) {
+              yr[-1] = flip(v, true);                                     // Delta_{m-1,m} = -Delta_{m,m-1}
+              if (m == 1) yr[-3] = flip(v, (lp & 1) == 0);                // Delta_{0,-1} = (-1)^{l+1} Delta_{1,0}
+            }
+            if (n == m && m == lp) yr[m + 2] = 0.0;                       // Delta_{l,l+1} = 0
+            Zs[zo + n] = v;
+          }
+          if (++seg * 32 > m) {
+            xo += m + 3;
+            zo += m + 1;
+            yr += m + 3;
+            ++m;
+            seg = 0;
+            if (m < c1) {
+              ia = Ri[2 * (m - c0)];
+              ib = Ri[2 * (m - c0) + 1];
+            }
+          }
+        }
+      }
+      __syncthreads();
       SSHT_RISBO_MARK(4);
+      if (c1 == r1 && threadIdx.x == 0) {  // the slab rows of this CTA are complete: publish them
+        __threadfence();
+        atomicExch(done + cta, (unsigned)lp);
+      }
+      // Quadrant table from shared memory: rows T[m][n] = Delta_{mn} (n <= m) ...
+      {
+        const SegRange w = warp_segments(c0, c1 - 1, 1, warp, nwarps);
+        int m = w.x, seg = w.seg;
+        int zo = tri32(m) - z0;
+        double* trow = T + (size_t)m * (lp + 1);
+        for (int k = 0; k < w.count; ++k) {
+          const int n = seg * 32 + lane;
+          if (n <= m) trow[n] = Zs[zo + n];
+          if (++seg * 32 > m) {
+            zo += m + 1;
+            trow += lp + 1;
+            ++m;
+            seg = 0;
+          }
+        }
+      }
+      // ... and T[n][m] = (-1)^{m-n} Delta_{mn} (n < m): for each table row n, the columns
+      // m in [max(c0, n+1), c1) are contiguous.
+      {
+        const int width = c1 - c0;
+        const int items = (c1 - 1) * width;  // n in [0, c1 - 1)
+        const float inv_w = 1.0f / (float)width;
+        for (int i = threadIdx.x; i < items; i += blockDim.x) {
+          int n = (int)(((float)i + 0.5f) * inv_w);
+          int j = i - n * width;
+          if (j < 0) { --n; j += width; } else if (j >= width) { ++n; j -= width; }
+          const int m = c0 + j;
+          if (m > n) T[(size_t)n * (lp + 1) + m] = flip(Zs[tri32(m) - z0 + n], ((m - n) & 1) != 0);
+        }
+      }
+      SSHT_RISBO_MARK(5);
       c0 = c1;
     }
-    ++phase;
-    if (!grid_barrier(P.counter, phase * nb, P.status, [&] { params(l + 1); })) return;
-    SSHT_RISBO_MARK(5);
   }
 }
 
@@ -387,12 +488,14 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.slab[0], tri(L + 1) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.slab[1], tri(L + 1) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.slab[0], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.slab[1], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.sqrt_tab, (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.barrier, 4 * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.barrier, (4 + (size_t)w.blocks) * sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
+  w.bytes = (delta_offset(L) + 2 * slab_doubles(L) + 2 * (size_t)L + 4) * sizeof(double) +
+            (4 + (size_t)w.blocks) * sizeof(unsigned int) + sizeof(int);
   std::vector<double> sq(2 * (size_t)L + 4);
   for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
   return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -400,7 +503,7 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
 
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.barrier, 0, (4 + (size_t)w.blocks) * sizeof(unsigned int), st)) != cudaSuccess) return e;
   RisboParams P;
   P.L = L;
   P.table = w.table;
@@ -438,11 +541,14 @@ namespace ssht {
 namespace {
 
 constexpr int kNoAllocMaxL = 512;
-// doubles: two octant slabs of tri(kNoAllocMaxL + 1) entries and the sqrt table (2L + 4 entries),
-// then 4 words for the barrier counter / abort flag and the status word.
-constexpr size_t kNoAllocSlab = (size_t)(kNoAllocMaxL + 1) * (kNoAllocMaxL + 2) / 2;
+// doubles: two padded octant slabs and the sqrt table (2L + 4 entries), then the
+// synchronisation words: barrier counter, abort flag, status, one spare, and one degree flag
+// per CTA (at most kNoAllocMaxCtas CTAs, one per SM).
+constexpr size_t kNoAllocSlab = slab_doubles(kNoAllocMaxL);
 constexpr size_t kNoAllocSqrt = 2 * (size_t)kNoAllocMaxL + 4;
-constexpr size_t kNoAllocDoubles = 2 * kNoAllocSlab + kNoAllocSqrt + 4;
+constexpr int kNoAllocMaxCtas = 1024;
+constexpr size_t kNoAllocWordDoubles = (4 + kNoAllocMaxCtas) / 2;
+constexpr size_t kNoAllocDoubles = 2 * kNoAllocSlab + kNoAllocSqrt + kNoAllocWordDoubles;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
@@ -505,9 +611,11 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return SSHT_ECUDA;
   const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
-  unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + kNoAllocSqrt);  // counter, abort, status
-  // The array keeps the previous call's contents: the barrier words and the status start at zero.
-  if (cudaMemsetAsync(words, 0, 4 * sizeof(double), st) != cudaSuccess) return SSHT_ECUDA;
+  if (sms > kNoAllocMaxCtas)
+    return set_last_error(SSHT_EUNSUPPORTED, "ssht_wigner_delta_noalloc: more SMs than its fixed scratch has flags for");
+  unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + kNoAllocSqrt);  // counter, abort, status, -, flags
+  // The array keeps the previous call's contents: the synchronisation words start at zero.
+  if (cudaMemsetAsync(words, 0, (4 + (size_t)sms) * sizeof(unsigned int), st) != cudaSuccess) return SSHT_ECUDA;
   RisboParams P;
   P.L = L;
   P.table = out;

@@ -34,13 +34,14 @@ inline size_t tri(long long l) { return (size_t)(l * (l + 1) / 2); }
 // ---------------------------------------------------------------------------
 struct DeltaWork {
   double* table = nullptr;        // quadrant table, delta_offset(L) doubles
-  double* slab[2] = {nullptr, nullptr};  // octant buffers, tri(L) doubles each
+  double* slab[2] = {nullptr, nullptr};  // padded octant slabs (rows 0..L, columns -1..m+1)
   double* sqrt_tab = nullptr;     // sqrt(k), k = 0 .. 2L + 2
   unsigned int* barrier = nullptr;  // grid barrier counter
   int* status = nullptr;          // latched status word
   int blocks = 0;                 // cooperative grid size
   int threads = 0;
   size_t smem = 0;
+  size_t bytes = 0;   // device memory held (table, slabs, tables, words)
   long long cap = 0;  // shared-memory doubles per CTA
 };
 
