@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cache-line", action="store_true")
+    ap.add_argument("--no-alt", action="store_true", help="skip the other split precision's line")
     return ap.parse_args()
 
 
@@ -247,19 +248,61 @@ def run_ssht(args):
     # roundtrip error over the whole batch, and the oracle check on sampled fields
     rt = float((back - flm).abs().max() / flm.abs().max())
     check = None
-    if rank == 0 and not args.no_check:
+    fields = sorted({0, B - 1})
+    inv_oracle = {}
+
+    def oracle_errors(g_dev, b_dev):
         from oracle import transforms as T
-        fields = sorted({0, B - 1})
-        g = grid.cpu().numpy()
-        b_out = back.cpu().numpy()
+        g = g_dev.cpu().numpy()
+        b_out = b_dev.cpu().numpy()
         e_inv, e_fwd = 0.0, 0.0
         for b in fields:
-            f_or = T.inverse(flm_np[b], L, s)
+            if b not in inv_oracle:
+                inv_oracle[b] = T.inverse(flm_np[b], L, s)
+            f_or = inv_oracle[b]
             e_inv = max(e_inv, float(np.abs(g[b] - f_or).max() / np.abs(f_or).max()))
             fw_or = T.forward(g[b].astype(np.complex128), L, s)
             e_fwd = max(e_fwd, float(np.abs(b_out[b] - fw_or).max() / np.abs(fw_or).max()))
+        return e_inv, e_fwd
+
+    if rank == 0 and not args.no_check:
+        e_inv, e_fwd = oracle_errors(grid, back)
         check = {"inverse": e_inv, "forward": e_fwd, "roundtrip": rt, "fields_checked": fields,
                  "measure": "max|x - oracle| / max|oracle|"}
+
+    # the other split form of the tensor-core contraction on the same workload (3xTF32 <-> split-BF16)
+    alt = None
+    if not args.no_alt and prec in ("tf32x3", "bf16x6"):
+        other = "bf16x6" if prec == "tf32x3" else "tf32x3"
+        aplan = ssht.Plan(L, s, B, precision=other, delta_mode=args.delta_mode)
+        grid2 = torch.empty_like(grid)
+        back2 = torch.empty_like(back)
+
+        def astep():
+            aplan.inverse(flm, out=grid2)
+            aplan.forward(grid2, out=back2)
+        for _ in range(args.warmup):
+            astep()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        nalt = min(args.steps, 10)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(nalt):
+            astep()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        aplan.check()
+        ams = max_over_ranks(a0.elapsed_time(a1), world, device)
+        alt = {"precision": other, "value": world * B * nalt / (ams / 1e3), "unit": "transforms/s",
+               "ms_per_step": ams / nalt, "steps": nalt,
+               "roundtrip": float((back2 - flm).abs().max() / flm.abs().max())}
+        if rank == 0 and not args.no_check:
+            e_inv, e_fwd = oracle_errors(grid2, back2)
+            alt.update({"inverse": e_inv, "forward": e_fwd, "fields_checked": fields})
+        aplan.close()
+        del grid2, back2
 
     # roofline of the dominant kernel of this library (cuFFT is excluded: library code)
     pk = peaks()
@@ -277,18 +320,19 @@ def run_ssht(args):
                     "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
                     "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
                     "work_per_launch": "%.3g flops = 10 x %.3g octant updates" % (flops, recursion_updates(L))}
-        elif dom in ("inverse", "project") and prec in ("tf32x3",):
-            # useful flops (4 per complex x real MAC) and the issued 3xTF32 tensor flops
+        elif dom in ("inverse", "project") and prec in ("tf32x3", "bf16x6"):
+            # useful flops (4 per complex x real MAC) and the issued split-product tensor flops
             flops = 4.0 * B * contraction_macs(L, s)
-            ach = 3.0 * flops / per_launch_s / 1e12
-            peak, src = pk["tf32_tflops"]
-            roof = {"bound": "tensor", "kernel": "tc_gemm_kernel<%s> (tcgen05 kind::tf32, 3 products)" % (
-                        "true" if dom == "project" else "false"),
+            nprod, kind, pkey = (3, "tf32", "tf32_tflops") if prec == "tf32x3" else (6, "f16 (bf16)", "bf16_tflops")
+            ach = nprod * flops / per_launch_s / 1e12
+            peak, src = pk[pkey]
+            roof = {"bound": "tensor", "kernel": "tc_gemm_kernel<%s> (tcgen05 kind::%s, %d products)" % (
+                        "forward" if dom == "project" else "inverse", kind, nprod),
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
                     "useful_tflops": flops / per_launch_s / 1e12,
                     "traffic": traffic_for("tc_gemm_kernel", ["paper_0807_4494_gb300/csrc/contract_tc.cu"]),
-                    "work_per_launch": "%.3g useful flops = 4 x B x %.3g MACs; x3 issued (hi*hi, hi*lo, lo*hi)" % (
-                        flops, contraction_macs(L, s))}
+                    "work_per_launch": "%.3g useful flops = 4 x B x %.3g MACs; x%d issued" % (
+                        flops, contraction_macs(L, s), nprod)}
         elif dom in ("inverse", "project"):
             flops = 4.0 * B * contraction_macs(L, s)
             ach = flops / per_launch_s / 1e12
@@ -369,6 +413,7 @@ def run_ssht(args):
                        "l2": "inputs larger than L2 (%.2f GB of coefficients, %.2f GB of samples per step)" % (
                            flm.numel() * flm.element_size() / 1e9, grid.numel() * grid.element_size() / 1e9)},
             "rel_err": check,
+            "alt_precision": alt,
             "roofline": roof,
             "stage_ms_per_step": stage_ms,
             "clocks": clocks,

@@ -89,7 +89,9 @@ typedef struct ssht_plan_s* ssht_plan_t;
 SSHT_API int ssht_plan(ssht_plan_t* out, int L, int s, int batch);
 
 /* Create a plan from a descriptor (precision and Delta mode).  With SSHT_DELTA_CACHE the
- * recursion runs here, synchronously, and its table stays resident in device memory. */
+ * recursion runs here, synchronously, and its table stays resident in device memory.
+ * The tensor-core precisions (SSHT_TF32X3, SSHT_BF16X6) take at most 64 fields per plan;
+ * a larger batch returns SSHT_EUNSUPPORTED. */
 SSHT_API int ssht_plan_ex(ssht_plan_t* out, const ssht_plan_desc* desc);
 
 /* Release every resource of a plan (NULL is accepted).  Synchronises the device. */

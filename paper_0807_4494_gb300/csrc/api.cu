@@ -101,7 +101,7 @@ struct ssht_plan_s {
   size_t stage_out_bytes = 0;
   bool delta_ready = false;
   size_t bytes = 0;
-  TcPlan* tc = nullptr;    // tensor-core contraction (precision SSHT_TF32X3)
+  TcPlan* tc = nullptr;    // tensor-core contraction (precisions SSHT_TF32X3, SSHT_BF16X6)
   TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
@@ -464,9 +464,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   if (desc->precision != SSHT_FP64 && desc->precision != SSHT_FP32 && desc->precision != SSHT_TF32X3 &&
       desc->precision != SSHT_BF16X6)
     return fail(SSHT_EINVAL, "unknown precision");
-  if (desc->precision == SSHT_BF16X6)
-    return fail(SSHT_EUNSUPPORTED, "the split-BF16 tensor-core precision is not built in this library version");
-  if (desc->precision == SSHT_TF32X3 && B > 64)
+  if ((desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6) && B > 64)
     return fail(SSHT_EUNSUPPORTED, "tensor-core plans take at most 64 fields per plan in this version");
 
   ssht_plan_t p = new (std::nothrow) ssht_plan_s();
@@ -563,8 +561,8 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
     }
     p->bytes += torus_bytes(p->torus);
   }
-  if (desc->precision == SSHT_TF32X3) {
-    ce = tc_setup(&p->tc, L, s, B, p->device);
+  if (desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6) {
+    ce = tc_setup(&p->tc, L, s, B, desc->precision == SSHT_BF16X6 ? 1 : 0, p->device);
     if (ce != cudaSuccess) {
       release(p);
       return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,

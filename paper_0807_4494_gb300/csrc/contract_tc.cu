@@ -86,7 +86,7 @@ __device__ __forceinline__ float2 ipow_signed(int s, int k) {
 
 // Inverse A tile (m, i, c): rows m' = 128 i + r, columns l = 32 c + k (K-major).
 // Forward A tile (m, i, c): rows l = 128 i + r, columns m' = 32 c + k.
-template <bool FWD>
+template <bool FWD, bool BF>
 __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* __restrict__ items,
                                                      const double* __restrict__ table, const double* __restrict__ U,
                                                      uint8_t* __restrict__ A) {
@@ -108,11 +108,7 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
       const double a = U[tri_ll(l) + mp] * d;
       x = (float)(((mp - m) & 1) ? -a : a);
     }
-    float hi, lo;
-    split_tf32(x, &hi, &lo);
-    const uint32_t o = sw128(r, k * 4);
-    *(float*)(tile + o) = hi;
-    *(float*)(tile + A_PART + o) = lo;
+    put_split<BF>(tile, A_PART, r, k, x);
   }
   __syncthreads();
   uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * A_TILE);
@@ -125,6 +121,7 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
 // ---------------------------------------------------------------------------------------------
 
 // Inverse data tile (m, c): V_m[l, j], l = 32 c + k.
+template <bool BF>
 __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC, const int* __restrict__ xc0,
                                                      const long long* __restrict__ xoff,
                                                      const float2* __restrict__ flm, uint8_t* __restrict__ X) {
@@ -147,11 +144,7 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC
         if (sign && (l & 1)) x = -x;
       }
     }
-    float hi, lo;
-    split_tf32(x, &hi, &lo);
-    const uint32_t o = sw128(j, k * 4);
-    *(float*)(tile + o) = hi;
-    *(float*)(tile + part_bytes + o) = lo;
+    put_split<BF>(tile, part_bytes, j, k, x);
   }
   __syncthreads();
   uint4* dst = (uint4*)(X + (size_t)(xoff[m] + blockIdx.x) * 2 * part_bytes);
@@ -160,6 +153,7 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC
 }
 
 // Forward data tile (m, c): Y_m[m', j], m' = 32 c + k, from H[b][m + Lp][m'] (m' < L).
+template <bool BF>
 __global__ void __launch_bounds__(256) pack_y_kernel(int L, int B, int NC, const float2* __restrict__ H,
                                                      uint8_t* __restrict__ X) {
   extern __shared__ __align__(16) uint8_t tile[];
@@ -179,11 +173,7 @@ __global__ void __launch_bounds__(256) pack_y_kernel(int L, int B, int NC, const
         if (sign && (mp & 1)) x = -x;
       }
     }
-    float hi, lo;
-    split_tf32(x, &hi, &lo);
-    const uint32_t o = sw128(j, k * 4);
-    *(float*)(tile + o) = hi;
-    *(float*)(tile + part_bytes + o) = lo;
+    put_split<BF>(tile, part_bytes, j, k, x);
   }
   __syncthreads();
   uint4* dst = (uint4*)(X + ((size_t)m * nC + c) * 2 * part_bytes);
@@ -211,7 +201,7 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
   for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-template <bool FWD>
+template <bool FWD, bool BF>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -271,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer: one tensor-memory segment per chunk, corrections first ----
-      const uint32_t idesc = idesc_tf32(TM, a.NC);
+      const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : idesc_tf32(TM, a.NC);
       int it = 0;
       for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
         const Item itm = a.items[w];
@@ -289,16 +279,29 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
           const uint32_t dt = tbase + (uint32_t)(seg * 256);
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
           const uint32_t sb = sa + A_TILE;
+          if constexpr (BF) {
+            // parts h, m at bytes 0 and 64 of part 0, l at byte 0 of part 1; K = 16 (32 bytes)
+            // per instruction.  Products from the smallest up: h*l, l*h, m*m, h*m, m*h, h*h.
+            const uint32_t oa[3] = {0u, 64u, (uint32_t)A_PART}, ob[3] = {0u, 64u, (uint32_t)b_part};
+            const int pa[6] = {0, 2, 1, 0, 1, 0}, pb[6] = {2, 0, 1, 1, 0, 0};
 #pragma unroll
-          for (int kk = 0; kk < TK / 8; ++kk) {
-            const uint32_t ko = kk * 32;
-            mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
-            mma_tf32(dt, desc_sw128(sa + A_PART + ko), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
-          }
+            for (int q = 0; q < 6; ++q)
 #pragma unroll
-          for (int kk = 0; kk < TK / 8; ++kk) {
-            const uint32_t ko = kk * 32;
-            mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
+              for (int kk = 0; kk < 2; ++kk)
+                mma_bf16(dt, desc_sw128(sa + oa[pa[q]] + kk * 32), desc_sw128(sb + ob[pb[q]] + kk * 32), idesc,
+                         (q == 0 && kk == 0) ? 0u : 1u);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < TK / 8; ++kk) {
+              const uint32_t ko = kk * 32;
+              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
+              mma_tf32(dt, desc_sw128(sa + A_PART + ko), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
+            }
+#pragma unroll
+            for (int kk = 0; kk < TK / 8; ++kk) {
+              const uint32_t ko = kk * 32;
+              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
+            }
           }
           mma_commit(&empty[s]);
           mma_commit(&seg_full[seg]);
@@ -382,6 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
 
 struct TcPlan {
   int L = 0, s = 0, B = 0, NC = 0, nC = 0, nI = 0;
+  bool bf16 = false;  // split-BF16 (3 parts, 6 products) instead of 3xTF32
   Item* items_inv = nullptr;
   Item* items_fwd = nullptr;
   int n_inv = 0, n_fwd = 0;
@@ -402,10 +406,11 @@ static cudaError_t tc_alloc(void** p, size_t bytes, size_t* total) {
   return e;
 }
 
-cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int device) {
+cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   *out = nullptr;
   if (B < 1 || B > 64) return cudaErrorInvalidValue;
   TcPlan* p = new TcPlan();
+  p->bf16 = bf16 != 0;
   p->L = L;
   p->s = s;
   p->B = B;
@@ -464,11 +469,18 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int device) {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) goto fail;
     p->grid = sms;
     p->smem = (size_t)STAGES * (A_TILE + 2 * p->NC * 128) + 1024;
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
     const int xsmem = 2 * p->NC * 128;
-    if ((e = cudaFuncSetAttribute(pack_v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
-    if ((e = cudaFuncSetAttribute(pack_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+    if (p->bf16) {
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_y_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+    } else {
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_y_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+    }
   }
   *out = p;
   return cudaSuccess;
@@ -489,21 +501,30 @@ size_t tc_bytes(const TcPlan* p) { return p ? p->bytes : 0; }
 
 cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double* U, cudaStream_t st, int* launches) {
   // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
-  if (forward)
-    pack_a_kernel<true><<<dim3(p->nC, p->n_fwd), 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
+  const dim3 gf(p->nC, p->n_fwd), gi(p->nC, p->n_inv);
+  if (forward && p->bf16)
+    pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
+  else if (forward)
+    pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
+  else if (p->bf16)
+    pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
   else
-    pack_a_kernel<false><<<dim3(p->nC, p->n_inv), 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+    pack_a_kernel<false, false><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
   *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches) {
   const int xsmem = 2 * p->NC * 128;
-  if (forward)
-    pack_y_kernel<<<dim3(p->nC, p->L), 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
+  const dim3 g(p->nC, p->L);
+  if (forward && p->bf16)
+    pack_y_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
+  else if (forward)
+    pack_y_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
+  else if (p->bf16)
+    pack_v_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);
   else
-    pack_v_kernel<<<dim3(p->nC, p->L), 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff,
-                                                          (const float2*)src, p->X);
+    pack_v_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -524,10 +545,14 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.out = (float2*)out;
   a.status = status;
   const int grid = std::min(p->grid, std::max(a.nitems, 1));
-  if (forward)
-    tc_gemm_kernel<true><<<grid, THREADS, p->smem, st>>>(a);
+  if (forward && p->bf16)
+    tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
+  else if (forward)
+    tc_gemm_kernel<true, false><<<grid, THREADS, p->smem, st>>>(a);
+  else if (p->bf16)
+    tc_gemm_kernel<false, true><<<grid, THREADS, p->smem, st>>>(a);
   else
-    tc_gemm_kernel<false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<false, false><<<grid, THREADS, p->smem, st>>>(a);
   *launches += 1;
   return cudaGetLastError();
 }

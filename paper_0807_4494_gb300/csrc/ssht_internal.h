@@ -65,10 +65,11 @@ cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* tab
                                   const void* H, void* flm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
-// Tensor-core contractions (contract_tc.cu), 3xTF32, batch of at most 64 fields per plan
+// Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16, at most 64 fields per plan
 // ---------------------------------------------------------------------------
 struct TcPlan;
-cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int device);
+// bf16 = 0: 3xTF32 split products; bf16 = 1: split-BF16 (three parts, six products).
+cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device);
 void tc_destroy(TcPlan* p);
 size_t tc_bytes(const TcPlan* p);
 // Pack the A operand (U_l[m'] Delta^l_{m'm}, split hi/lo) of one direction from the FP64 table.

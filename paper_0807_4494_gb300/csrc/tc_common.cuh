@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 namespace ssht {
 namespace tc {
 
@@ -31,6 +33,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
 __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// Instruction descriptor: D = F32, A = B = BF16 (kind::f16), both K-major, shape M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -88,6 +95,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
                ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 with BF16 operands (K = 16 per instruction).
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
 // Arrive on an mbarrier once every tcgen05.mma issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -114,6 +128,39 @@ __device__ __forceinline__ float tf32_round(float x) {
 __device__ __forceinline__ void split_tf32(float x, float* hi, float* lo) {
   *hi = tf32_round(x);
   *lo = tf32_round(x - *hi);
+}
+
+// x = h + m + l with each part rounded to BF16 (8 significant bits, round to nearest): the three
+// parts carry about 24 significant bits of x; each remainder is exact in FP32.
+__device__ __forceinline__ void split_bf16x3(float x, uint16_t* h, uint16_t* m, uint16_t* l) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b);
+  const __nv_bfloat16 c = __float2bfloat16_rn(r2);
+  *h = __bfloat16_as_ushort(a);
+  *m = __bfloat16_as_ushort(b);
+  *l = __bfloat16_as_ushort(c);
+}
+
+// Writes element (row, k), k < 32, of a K-chunk operand tile made of two parts of part_bytes each
+// (128-byte swizzled rows).  TF32 split: part 0 = hi (4-byte elements), part 1 = lo.  BF16 split:
+// part 0 = [h | m] (2-byte elements, k at byte 2k and 64 + 2k), part 1 = [l | 0].
+template <bool BF>
+__device__ __forceinline__ void put_split(uint8_t* tile, int part_bytes, int row, int k, float x) {
+  if constexpr (BF) {
+    uint16_t h, m, l;
+    split_bf16x3(x, &h, &m, &l);
+    *(uint16_t*)(tile + sw128(row, 2 * k)) = h;
+    *(uint16_t*)(tile + sw128(row, 64 + 2 * k)) = m;
+    *(uint16_t*)(tile + part_bytes + sw128(row, 2 * k)) = l;
+    *(uint16_t*)(tile + part_bytes + sw128(row, 64 + 2 * k)) = 0;
+  } else {
+    float hi, lo;
+    split_tf32(x, &hi, &lo);
+    *(float*)(tile + sw128(row, 4 * k)) = hi;
+    *(float*)(tile + part_bytes + sw128(row, 4 * k)) = lo;
+  }
 }
 
 }  // namespace tc
