@@ -103,6 +103,13 @@ struct ssht_plan_s {
   size_t bytes = 0;
   TcPlan* tc = nullptr;    // tensor-core contraction (precisions SSHT_TF32X3, SSHT_BF16X6)
   TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
+  // The Delta recursion (and the A packing) of a call runs on a second stream, forked from the
+  // caller's stream at the start of the call and joined before the contraction, so that the
+  // Delta-independent work of the call (the torus stage of forward/adjoint, data packing) runs
+  // beside it.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool join_pending = false;
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -230,26 +237,55 @@ int ensure_delta(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
-// Delta (and, for the tensor-core path, the packed A operand of one direction) ready for a call.
-int ensure_operands(ssht_plan_t p, int forward, cudaStream_t st) {
+// Start making Delta (and, for the tensor-core path, the packed A operand of one direction) on
+// the plan's second stream, after everything already queued on st; join_operands makes st wait.
+int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
-  int rc = run_delta(p, st);
+  SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
+  SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
+  int rc = run_delta(p, p->aux);
   if (rc) return rc;
-  if (p->tc && (rc = pack_a(p, forward, st))) return rc;
+  if (p->tc && (rc = pack_a(p, forward, p->aux))) return rc;
+  SSHT_CUDA(cudaEventRecord(p->ev_join, p->aux), "join event");
+  p->join_pending = true;
   return 0;
 }
 
-int tc_contract(ssht_plan_t p, int forward, const void* src, void* dst, cudaStream_t st) {
+int join_operands(ssht_plan_t p, cudaStream_t st) {
+  if (!p->join_pending) return 0;
+  p->join_pending = false;
+  SSHT_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0), "join wait");
+  return 0;
+}
+
+int tc_pack(ssht_plan_t p, int forward, const void* src, cudaStream_t st) {
   int n = 0;
-  {
-    StageScope sc(p, SSHT_STAGE_PACK, st);
-    SSHT_CUDA(tc_pack_data(p->tc, forward, src, st, &n), "tensor-core data packing");
-  }
-  {
-    StageScope sc(p, forward ? SSHT_STAGE_PROJECT : SSHT_STAGE_INVERSE, st);
-    SSHT_CUDA(tc_gemm(p->tc, forward, dst, p->ph, p->delta.status, st, &n), "tensor-core contraction");
-  }
+  StageScope sc(p, SSHT_STAGE_PACK, st);
+  SSHT_CUDA(tc_pack_data(p->tc, forward, src, st, &n), "tensor-core data packing");
   p->launches += n;
+  return 0;
+}
+
+int tc_multiply(ssht_plan_t p, int forward, void* dst, cudaStream_t st) {
+  int n = 0;
+  StageScope sc(p, forward ? SSHT_STAGE_PROJECT : SSHT_STAGE_INVERSE, st);
+  SSHT_CUDA(tc_gemm(p->tc, forward, dst, p->ph, p->delta.status, st, &n), "tensor-core contraction");
+  p->launches += n;
+  return 0;
+}
+
+// The projection of forward / adjoint from the folded torus sums H (in W), after the join.
+template <typename T>
+int project(ssht_plan_t p, const void* H, void* flm, cudaStream_t st) {
+  int rc;
+  if (p->tc) {
+    if ((rc = tc_pack(p, 1, H, st)) || (rc = join_operands(p, st))) return rc;
+    return tc_multiply(p, 1, flm, st);
+  }
+  if ((rc = join_operands(p, st))) return rc;
+  StageScope sc(p, SSHT_STAGE_PROJECT, st);
+  SSHT_CUDA(contract_project_simt<T>(p->d, p->s, p->B, p->delta.table, p->U, H, flm, st), "projection");
+  p->launches += 1;
   return 0;
 }
 
@@ -321,11 +357,13 @@ int io_end(ssht_plan_t p, const IO& io, cudaStream_t st) {
 template <typename T>
 int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc = ensure_operands(p, 0, st);
+  int rc = begin_operands(p, 0, st);
   if (rc) return rc;
   if (p->tc) {
-    if ((rc = tc_contract(p, 0, flm, p->W1, st))) return rc;
+    if ((rc = tc_pack(p, 0, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)))
+      return rc;
   } else {
+    if ((rc = join_operands(p, st))) return rc;
     StageScope sc(p, SSHT_STAGE_INVERSE, st);
     SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, p->torus ? 1 : 0, st),
               "inverse contraction");
@@ -363,15 +401,11 @@ int analysis_front(ssht_plan_t p, const void* f, int mode, cudaStream_t st) {
 template <typename T>
 int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc;
+  int rc = begin_operands(p, 1, st);
+  if (rc) return rc;
   if (p->torus) {
     if ((rc = run_torus(p, 2, f, p->W2, st)) || (rc = run_torus(p, 4, p->W2, p->W1, st))) return rc;
-    if ((rc = ensure_operands(p, 1, st))) return rc;
-    if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
-    StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "forward contraction");
-    p->launches += 1;
-    return 0;
+    return project<T>(p, p->W1, flm, st);
   }
   rc = analysis_front<T>(p, f, 0, st);
   if (rc) return rc;
@@ -392,28 +426,17 @@ int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
     SSHT_CUDA(conv_to_project<T>(d, p->B, p->W3, p->W1, st), "weight convolution output");
     p->launches += 1;
   }
-  if ((rc = ensure_operands(p, 1, st))) return rc;
-  if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
-  {
-    StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "forward contraction");
-    p->launches += 1;
-  }
-  return 0;
+  return project<T>(p, p->W1, flm, st);
 }
 
 template <typename T>
 int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
   const Dims& d = p->d;
-  int rc;
+  int rc = begin_operands(p, 1, st);
+  if (rc) return rc;
   if (p->torus) {
     if ((rc = run_torus(p, 3, g, p->W2, st)) || (rc = run_torus(p, 5, p->W2, p->W1, st))) return rc;
-    if ((rc = ensure_operands(p, 1, st))) return rc;
-    if (p->tc) return tc_contract(p, 1, p->W1, flm, st);
-    StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W1, flm, st), "adjoint contraction");
-    p->launches += 1;
-    return 0;
+    return project<T>(p, p->W1, flm, st);
   }
   rc = analysis_front<T>(p, g, 1, st);
   if (rc) return rc;
@@ -422,14 +445,7 @@ int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
     SSHT_CUDA(adj_theta_fold<T>(d, p->s, p->B, p->W1, p->W2, p->ph, st), "adjoint fold");
     p->launches += 1;
   }
-  if ((rc = ensure_operands(p, 1, st))) return rc;
-  if (p->tc) return tc_contract(p, 1, p->W2, flm, st);
-  {
-    StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(contract_project_simt<T>(d, p->s, p->B, p->delta.table, p->U, p->W2, flm, st), "adjoint contraction");
-    p->launches += 1;
-  }
-  return 0;
+  return project<T>(p, p->W2, flm, st);
 }
 
 void release(ssht_plan_t p) {
@@ -441,6 +457,9 @@ void release(ssht_plan_t p) {
   }
   if (p->tc) tc_destroy(p->tc);
   if (p->torus) torus_destroy(p->torus);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->aux) cudaStreamDestroy(p->aux);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
@@ -471,9 +490,12 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   if (!p) return fail(SSHT_ENOMEM, "host allocation of the plan");
   int rc = 0;
   cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     release(p);
-    return fail(SSHT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    return fail(SSHT_ECUDA, std::string("plan stream/event setup: ") + cudaGetErrorString(ce));
   }
   p->d.L = L;
   p->d.Lp = L - 1;

@@ -469,17 +469,19 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) goto fail;
     p->grid = sms;
     p->smem = (size_t)STAGES * (A_TILE + 2 * p->NC * 128) + 1024;
-    const int xsmem = 2 * p->NC * 128;
+    // Function attributes are process-wide upper bounds: set them for the largest column count
+    // (NC = 256) so that plans of other batch sizes can launch with their own amounts.
+    const int gemm_max = STAGES * (A_TILE + 2 * 256 * 128) + 1024, xsmem_max = 2 * 256 * 128;
     if (p->bf16) {
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_y_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_y_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
     } else {
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_y_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = cudaFuncSetAttribute(pack_y_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
     }
   }
   *out = p;

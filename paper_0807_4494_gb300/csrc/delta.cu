@@ -478,13 +478,29 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) return e;
   w.threads = kThreads;
   w.blocks = sms;  // one CTA per SM
-  // Shared memory: as much as one CTA per SM may take, leaving room for the static part.
-  w.smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
+  // Shared memory: what the largest single-chunk share of any degree needs (so no degree is
+  // split into chunks), at most 200 KB.  Staying small leaves room on each SM for the kernels
+  // that run beside the recursion on other streams.
+  {
+    long long need = 0;
+    for (int l = 0; l + 1 < L; ++l)
+      for (int c = 0; c < w.blocks; ++c) {
+        int r0, r1;
+        cta_rows(l + 1, c, w.blocks, &r0, &r1);
+        if (r0 < r1) need = std::max(need, chunk_need(l, r0, r1));
+      }
+    const size_t want = (((size_t)need + 16) * sizeof(double) + 1023) / 1024 * 1024;
+    w.smem = std::min(want, (size_t)std::min(smem_optin - 1024, 200 * 1024));
+  }
   w.cap = (long long)(w.smem / sizeof(double));
   // Every chunk holds at least one row: the widest single-row chunk (last degree) must fit.
   for (int m = 0; m < L; ++m)
     if (chunk_need(L - 2 > 0 ? L - 2 : 0, m, m + 1) > w.cap) return cudaErrorInvalidValue;
-  if ((e = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem)) != cudaSuccess) return e;
+  // The attribute is process-wide and an upper bound: always the cap, so that plans of other
+  // sizes (and the no-allocation entry point) can launch with their own amounts.
+  if ((e = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                std::min(smem_optin - 1024, 200 * 1024))) != cudaSuccess)
+    return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;

@@ -250,3 +250,45 @@ def test_full_size_single_field_L1024_fp64():
     back = plan.forward(dev(f_or)).cpu().numpy()
     plan.check()
     assert rel(back, T.forward(f_or, L, s)) < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3"])
+def test_calls_capture_into_a_cuda_graph(precision):
+    """inverse + forward (recursion forked onto the plan's second stream and joined) capture into
+    one CUDA graph whose replays reproduce the eager results bit for bit."""
+    L, s, B = 48, 2, 3
+    plan = S().Plan(L, s, B, precision=precision)
+    dt = plan.dtype
+    flm = torch.from_numpy(inputs.coeffs(L, s, B, seed=9)).to(dt).cuda()
+    f_eager = plan.inverse(flm)
+    b_eager = plan.forward(f_eager)
+    f_static = torch.empty_like(f_eager)
+    b_static = torch.empty_like(b_eager)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.inverse(flm, out=f_static)
+        plan.forward(f_static, out=b_static)
+    for _ in range(2):
+        f_static.zero_()
+        b_static.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(f_static, f_eager)
+        assert torch.equal(b_static, b_eager)
+    plan.check()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "bf16x6"])
+def test_plans_of_different_sizes_interleave(precision):
+    """Kernel launch limits are process-wide: a plan made after a larger one must not stop the
+    larger one from launching (shared-memory sizes differ with L and the batch)."""
+    big = S().Plan(200, 1, 40, precision=precision)
+    dt = big.dtype
+    flm_big = torch.from_numpy(inputs.coeffs(200, 1, 40, seed=3)).to(dt).cuda()
+    f1 = big.inverse(flm_big)
+    small = S().Plan(16, 0, 1, precision=precision)
+    small.inverse(torch.from_numpy(inputs.coeffs(16, 0, 1, seed=4)).to(dt).cuda())
+    f2 = big.inverse(flm_big)
+    assert torch.equal(f1, f2)
+    big.check()
+    small.check()
