@@ -87,6 +87,7 @@ struct ssht_plan_s {
   size_t elem = 16;  // bytes per complex element of the I/O and workspaces
   DeltaWork delta;
   double* U = nullptr;
+  float* Uf = nullptr;  // U in FP32 (tensor-core operand packing)
   void* W1 = nullptr;
   void* W2 = nullptr;
   void* W3 = nullptr;
@@ -216,7 +217,7 @@ int set_streams(ssht_plan_t p, cudaStream_t st) {
 int run_delta(ssht_plan_t p, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_DELTA, st);
   SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
-  SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, st), "spin column launch");
+  SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, p->Uf, st), "spin column launch");
   p->launches += 2;
   return 0;
 }
@@ -224,7 +225,7 @@ int run_delta(ssht_plan_t p, cudaStream_t st) {
 int pack_a(ssht_plan_t p, int forward, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_PACK, st);
   int n = 0;
-  SSHT_CUDA(tc_pack_a(p->tc, forward, p->delta.table, p->U, st, &n), "tensor-core operand packing");
+  SSHT_CUDA(tc_pack_a(p->tc, forward, p->delta.table, p->Uf, st, &n), "tensor-core operand packing");
   p->launches += n;
   return 0;
 }
@@ -464,7 +465,7 @@ void release(ssht_plan_t p) {
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
   void* ptrs[] = {p->delta.table, p->delta.slab[0], p->delta.slab[1], p->delta.sqrt_tab, p->delta.barrier,
-                  p->delta.status, p->U, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
+                  p->delta.status, p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -521,6 +522,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
   }
   p->bytes += p->delta.bytes;
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
+  if ((rc = dalloc(p, (void**)&p->Uf, tri(L) * sizeof(float), "spin column (FP32)"))) return bail(rc);
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
   // rows of N x L only.
   const size_t torus = (size_t)B * d.N * (p->f64 ? d.N : d.L) * p->elem;

@@ -84,31 +84,55 @@ __device__ __forceinline__ float2 ipow_signed(int s, int k) {
 // Packing: A tiles from the FP64 Delta table
 // ---------------------------------------------------------------------------------------------
 
+// FP64 -> FP32, round to nearest even, by integer operations on the bit pattern (IEEE 754
+// rounding; the FP64 pipe is the scarce one on this part).  |x| below the FP32 normal range
+// becomes a signed zero; |x| must stay below 2^128 (entries here are at most ~13 in magnitude).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
+  unsigned m23 = (unsigned)(mant >> 29);
+  const unsigned long long rest = mant & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rest > half || (rest == half && (m23 & 1u))) ++m23;
+  // a carry out of the 23 fraction bits moves into the exponent field, as rounding requires
+  return __uint_as_float((sign | ((unsigned)e << 23)) + m23);
+}
+
 // Inverse A tile (m, i, c): rows m' = 128 i + r, columns l = 32 c + k (K-major).
 // Forward A tile (m, i, c): rows l = 128 i + r, columns m' = 32 c + k.
+// Every thread issues its 16 table loads before converting any of them.
 template <bool FWD, bool BF>
 __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* __restrict__ items,
-                                                     const double* __restrict__ table, const double* __restrict__ U,
+                                                     const double* __restrict__ table, const float* __restrict__ Uf,
                                                      uint8_t* __restrict__ A) {
   __shared__ __align__(16) uint8_t tile[A_TILE];
+  constexpr int PER = TM * TK / 256;
   const Item it = items[blockIdx.y];
   const int c = it.c0 + blockIdx.x;
   if (c >= it.c1) return;
   const int m = it.m, Lp = L - 1, as = s < 0 ? -s : s;
-  for (int e = threadIdx.x; e < TM * TK; e += blockDim.x) {
-    int r, k;
-    if (FWD) { k = e % TK; r = e / TK; } else { r = e % TM; k = e / TM; }
+  double d[PER];
+  float u[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    const int r = FWD ? e / TK : e % TM, k = FWD ? e % TK : e / TM;
     const int rowv = it.i * TM + r, colv = c * TK + k;
-    const int mp = FWD ? colv : rowv;
-    const int l = FWD ? rowv : colv;
-    float x = 0.f;
-    if (l <= Lp && mp <= Lp && l >= m && l >= mp && l >= as) {
-      // Delta^l_{m' m} = (-1)^{m'-m} Delta^l_{m m'}: row m of degree l, contiguous in m'
-      const double d = table[doff(l) + (size_t)m * (l + 1) + mp];
-      const double a = U[tri_ll(l) + mp] * d;
-      x = (float)(((mp - m) & 1) ? -a : a);
-    }
-    put_split<BF>(tile, A_PART, r, k, x);
+    const int mp = FWD ? colv : rowv, l = FWD ? rowv : colv;
+    const bool ok = l <= Lp && mp <= Lp && l >= m && l >= mp && l >= as;
+    // Delta^l_{m' m} = (-1)^{m'-m} Delta^l_{m m'}: row m of degree l, contiguous in m'
+    d[q] = ok ? __ldg(&table[doff(l) + (size_t)m * (l + 1) + mp]) : 0.0;
+    u[q] = ok ? __ldg(&Uf[tri_ll(l) + mp]) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    const int r = FWD ? e / TK : e % TM, k = FWD ? e % TK : e / TM;
+    const int mp = FWD ? c * TK + k : it.i * TM + r;
+    const float a = u[q] * f64_to_f32_rn(d[q]);
+    put_split<BF>(tile, A_PART, r, k, ((mp - m) & 1) ? -a : a);
   }
   __syncthreads();
   uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * A_TILE);
@@ -501,7 +525,7 @@ void tc_destroy(TcPlan* p) {
 
 size_t tc_bytes(const TcPlan* p) { return p ? p->bytes : 0; }
 
-cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double* U, cudaStream_t st, int* launches) {
+cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* U, cudaStream_t st, int* launches) {
   // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
   const dim3 gf(p->nC, p->n_fwd), gi(p->nC, p->n_inv);
   if (forward && p->bf16)

@@ -450,7 +450,8 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
 }
 
 // U[tri(l) + m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s} for l >= |s|, 0 otherwise.
-__global__ void spin_column_kernel(const double* __restrict__ table, int L, int s, double* __restrict__ U) {
+__global__ void spin_column_kernel(const double* __restrict__ table, int L, int s, double* __restrict__ U,
+                                   float* __restrict__ Uf) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= tri_ll(L)) return;
   int l = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
@@ -467,6 +468,7 @@ __global__ void spin_column_kernel(const double* __restrict__ table, int L, int 
     v *= sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
   }
   U[e] = v;
+  Uf[e] = (float)v;
 }
 
 }  // namespace
@@ -533,10 +535,10 @@ cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   return cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(w.blocks), dim3(w.threads), args, w.smem, st);
 }
 
-cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cudaStream_t st) {
+cudaError_t delta_spin_column(const double* table, int L, int s, double* U, float* Uf, cudaStream_t st) {
   const long long n = tri_ll(L);
   const int threads = 256;
-  spin_column_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(table, L, s, U);
+  spin_column_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(table, L, s, U, Uf);
   return cudaGetLastError();
 }
 

@@ -47,8 +47,9 @@ struct DeltaWork {
 
 cudaError_t delta_setup(DeltaWork& w, int L, int device);
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st);
-// U[l][m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s}, l < L, 0 <= m' <= l, at tri(l) + m'.
-cudaError_t delta_spin_column(const double* table, int L, int s, double* U, cudaStream_t st);
+// U[l][m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s}, l < L, 0 <= m' <= l, at tri(l) + m'; Uf is the
+// same in FP32 (rounded to nearest).
+cudaError_t delta_spin_column(const double* table, int L, int s, double* U, float* Uf, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // SIMT contractions (contract_simt.cu); T is double or float
@@ -72,8 +73,9 @@ struct TcPlan;
 cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device);
 void tc_destroy(TcPlan* p);
 size_t tc_bytes(const TcPlan* p);
-// Pack the A operand (U_l[m'] Delta^l_{m'm}, split hi/lo) of one direction from the FP64 table.
-cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const double* U, cudaStream_t st, int* launches);
+// Pack the A operand (U_l[m'] Delta^l_{m'm} in FP32, then split) of one direction from the FP64
+// table and the FP32 copy of U.
+cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* U, cudaStream_t st, int* launches);
 // Pack the data operand: forward = 0: V from flm (float2 [B][L*L]); forward = 1: Y from the
 // folded torus sums H (float2 [B][N][L]).
 cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches);
