@@ -61,6 +61,17 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank, B):
+    """First field seed of a rank: rank r transforms fields r*B .. r*B+B-1 (field b of the rank
+    draws from default_rng(r*B + b)), so the shards of the ranks are disjoint."""
+    return rank * B
+
+
+def throughput(world, B, steps, ms):
+    """Whole-job transforms/s: the fields of all ranks over the slowest rank's time."""
+    return world * B * steps / (ms / 1e3)
+
+
 def max_over_ranks(x, world, device):
     if world == 1:
         return x
@@ -207,7 +218,7 @@ def run_ssht(args):
         prec = "tf32x3" if B <= 64 else "fp32"
     plan = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode)
     cdt = plan.dtype
-    flm_np = inputs.coeffs(L, s, B, seed=rank * B, spectrum="cmb")
+    flm_np = inputs.coeffs(L, s, B, seed=rank_seed(rank, B), spectrum="cmb")
     flm = torch.from_numpy(flm_np).to(cdt).to(device)
     grid = torch.empty(plan.grid_shape(), dtype=cdt, device=device)
     back = torch.empty(plan.coeff_shape(), dtype=cdt, device=device)
@@ -242,7 +253,7 @@ def run_ssht(args):
     plan.profile(False)
     plan.check()
     ms = max_over_ranks(ms_local, world, device)
-    value = world * B * args.steps / (ms / 1e3)
+    value = throughput(world, B, args.steps, ms)
     ms_step = ms / args.steps
 
     # roundtrip error over the whole batch, and the oracle check on sampled fields
