@@ -324,13 +324,17 @@ def run_ssht(args):
         ms_d, n_d = own[dom]
         per_launch_s = ms_d / n_d / 1e3
         if dom == "delta":
-            flops = 10.0 * recursion_updates(L)
+            # 9 flops per octant update: 3 products and 3 fused multiply-adds, i.e. 6 FP64-pipe
+            # instructions; at full pipe this mix reaches 9/12 of the FMA-only peak.
+            flops = 9.0 * recursion_updates(L)
             ach = flops / per_launch_s / 1e12
             peak, src = pk["fp64_tflops"]
             roof = {"bound": "alu", "kernel": "risbo_kernel (FP64)", "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                    "fp64_pipe_frac": (6.0 * recursion_updates(L) / per_launch_s) / (peak * 1e12 / 2.0),
                     "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
-                    "work_per_launch": "%.3g flops = 10 x %.3g octant updates" % (flops, recursion_updates(L))}
+                    "work_per_launch": "%.3g flops = 9 x %.3g octant updates (6 FP64 instructions each)" % (
+                        flops, recursion_updates(L))}
         elif dom in ("inverse", "project") and prec in ("tf32x3", "bf16x6"):
             # useful flops (4 per complex x real MAC) and the issued split-product tensor flops
             flops = 4.0 * B * contraction_macs(L, s)
