@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cache-line", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip the other split precision's line")
+    ap.add_argument("--error-sweep", action="store_true",
+                    help="print errors vs the FP64 oracle for L = 32 .. 2048 and every precision, then exit")
     return ap.parse_args()
 
 
@@ -494,9 +496,41 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def error_sweep(args):
+    """Error vs band-limit (max-norm relative, vs the FP64 oracle) of every precision, one field of
+    the CMB-like spectrum (seed 0) per L: inverse, forward of the GPU's own grid, roundtrip."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import transforms as T
+    from paper_0807_4494_gb300 import inputs, ssht
+    s = args.s
+    for L in (32, 64, 128, 256, 512, 1024, 2048):
+        flm = inputs.coeffs(L, s, 1, seed=0, spectrum="cmb")
+        f_or = T.inverse(flm[0], L, s)
+        for prec in ("fp64", "fp32", "tf32x3", "bf16x6"):
+            plan = ssht.Plan(L, s, 1, precision=prec)
+            x = torch.from_numpy(flm).to(plan.dtype).cuda()
+            f = plan.inverse(x)
+            back = plan.forward(f)
+            plan.check()
+            f0 = f[0].cpu().numpy()
+            fw = T.forward(f0.astype(np.complex128), L, s)
+            line = {"L": L, "s": s, "precision": prec,
+                    "inverse": float(np.abs(f0 - f_or).max() / np.abs(f_or).max()),
+                    "forward": float(np.abs(back[0].cpu().numpy() - fw).max() / np.abs(fw).max()),
+                    "roundtrip": float((back - x).abs().max() / x.abs().max())}
+            print(json.dumps(line), flush=True)
+            plan.close()
+            del f, back, x
+            torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.error_sweep:
+        error_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ssht(args)
