@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cache-line", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip the other split precision's line")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (captured graph) line")
     ap.add_argument("--error-sweep", action="store_true",
                     help="print errors vs the FP64 oracle for L = 32 .. 2048 and every precision, then exit")
     return ap.parse_args()
@@ -415,6 +416,13 @@ def run_ssht(args):
                       "ms_per_step": cms / args.steps, "plan_build_s": build_s}
         cplan.close()
 
+    # the uneven batch: 256 fields, L ~ U{128,256,512,1024}, s ~ U{0,+-1,+-2}, N(0,1) coefficients,
+    # one group (buckets by (L, s), shared Delta per L, tuned contraction per bucket), inverse +
+    # forward captured into one CUDA graph and replayed
+    uneven = None
+    if not args.no_uneven:
+        uneven = run_uneven(args, torch, inputs, ssht, world, device, stream, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(L, s, flm_np[0])
@@ -437,6 +445,7 @@ def run_ssht(args):
             "e2e": e2e,
             "gpu_launches": int(launches1 - launches0),
             "delta_cache": cache_line,
+            "uneven_batch": uneven,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -444,6 +453,50 @@ def run_ssht(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_uneven(args, torch, inputs, ssht, world, device, stream, rank):
+    n = 256
+    Ls, ss = inputs.uneven_batch(n, seed=rank_seed(rank, n))
+    t0 = time.perf_counter()
+    g = ssht.Group(Ls, ss, precision="fp32", delta_mode="recompute", tune=True)
+    build_s = time.perf_counter() - t0
+    flms = [inputs.coeffs(L, s_, 1, seed=rank_seed(rank, n) + i)[0] for i, (L, s_) in enumerate(zip(Ls, ss))]
+    flat = g.pack_coeffs([torch.from_numpy(x).to(torch.complex64).to(device) for x in flms])
+    f = g.empty_grid()
+    back = g.empty_coeffs()
+    g.capture(flat, f, back)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    barrier(world, device)
+    nrep = min(args.steps, 10)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nrep):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    res = {"fields": n, "value": throughput(world, n, nrep, ms), "unit": "transforms/s", "ms_per_step": ms / nrep,
+           "steps": nrep, "graph": "one CUDA graph per step (inverse + forward of all fields)",
+           "group_build_s": build_s,
+           "buckets": [{"L": L, "s": s_, "fields": c, "contraction": {0: "fp64", 1: "fp32", 2: "tf32x3", 3: "bf16x6"}[p]}
+                       for (L, s_, c, p) in g.buckets()],
+           "roundtrip": float((back - flat).abs().max() / flat.abs().max())}
+    if rank == 0 and not args.no_check:
+        from oracle import transforms as T
+        fs = g.unpack_grid(f)
+        errs = []
+        for Lq in (128, 256, 512, 1024):
+            i = next(k for k, L in enumerate(Ls) if L == Lq)
+            f_or = T.inverse(flms[i], Lq, ss[i])
+            errs.append(float(np.abs(fs[i].cpu().numpy() - f_or).max() / np.abs(f_or).max()))
+        res["inverse_max_err_one_field_per_L"] = max(errs)
+    g.close()
+    return res
 
 
 def cpu_baseline(L, s, flm1):

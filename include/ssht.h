@@ -151,7 +151,7 @@ SSHT_API int ssht_plan_check(ssht_plan_t plan);
 #define SSHT_STAGE_DELTA 0      /* Risbo recursion of Delta^l (and the spin column)       */
 #define SSHT_STAGE_INVERSE 1    /* inverse contraction (eqn fourier_coeff)                */
 #define SSHT_STAGE_PROJECT 2    /* forward / adjoint contraction (harmonic projection)    */
-#define SSHT_STAGE_FFT 3        /* torus DFTs (cuFFT) and the weight convolution FFTs     */
+#define SSHT_STAGE_FFT 3        /* torus DFTs: fused torus passes (FP32 plans) or cuFFT   */
 #define SSHT_STAGE_TORUS 4      /* extension, phase, transpose and weight-product kernels */
 #define SSHT_STAGE_PACK 5       /* operand packing for the tensor-core contraction        */
 #define SSHT_NUM_STAGES 6
@@ -166,6 +166,49 @@ SSHT_API int ssht_plan_profile(ssht_plan_t plan, int enable);
  * the plan since it was created (cuFFT's kernels are not counted). */
 SSHT_API int ssht_plan_profile_read(ssht_plan_t plan, double* ms, long long* count, int nstages,
                                     long long* launches);
+
+/* ---------------------------------------------------------------------------------------
+ * Groups: many fields of uneven band-limit and spin in one call.  This extends the paper's
+ * single-field transform (which has no batching) to a heterogeneous batch.
+ * --------------------------------------------------------------------------------------- */
+typedef struct ssht_group_s* ssht_group_t;
+
+/* Create a group of n fields with band-limits L[i] (1..2048) and spins s[i] (|s[i]| < L[i]).
+ * Fields are bucketed by (L, s) and each bucket is transformed by one plan of the given
+ * precision and Delta mode; buckets of the same L share one Delta table (recompute mode: one
+ * recursion per distinct L per call; cache mode: made here).  tune != 0 (FP32-class
+ * precisions only) times the FP32, 3xTF32 and split-BF16 contractions on each bucket (the
+ * tensor-core forms up to 64 fields) and keeps the fastest.  Synchronises the device. */
+SSHT_API int ssht_group_create(ssht_group_t* out, int n, const int* L, const int* s, int precision,
+                               int delta_mode, int tune);
+SSHT_API int ssht_group_destroy(ssht_group_t group);
+
+/* Group order of the fields and their offsets in the flat buffers of the group calls:
+ * order[k] (n entries) = caller's index of the k-th field; coeff_offset[k], grid_offset[k]
+ * (n + 1 entries, the last = total) = complex-element offsets of field k's coefficients
+ * [L^2] and samples [L][2L-1].  Any pointer may be NULL. */
+SSHT_API int ssht_group_layout(ssht_group_t group, int* order, long long* coeff_offset, long long* grid_offset);
+
+/* Buckets: on entry *nbuckets = capacity of the arrays (may be 0); on return the number of
+ * buckets, and for the first min(capacity, number) buckets their L, s, field count and the
+ * precision their plan uses (after tuning).  Array pointers may be NULL. */
+SSHT_API int ssht_group_buckets(ssht_group_t group, int* nbuckets, int* L, int* s, int* count, int* precision);
+
+/* Transforms of every field of the group; flat DEVICE buffers in group order (ssht_group_layout),
+ * complex float (FP32-class precisions) or double (SSHT_FP64).  Buckets run concurrently on
+ * group-owned streams forked from and joined back to `stream`. */
+SSHT_API int ssht_group_inverse(ssht_group_t group, const void* flm, void* f, void* stream);
+SSHT_API int ssht_group_forward(ssht_group_t group, const void* f, void* flm, void* stream);
+SSHT_API int ssht_group_adjoint(ssht_group_t group, const void* f, void* flm, void* stream);
+
+/* Capture inverse (flm -> f) followed by forward (f -> flm_out) of the whole group into one
+ * CUDA graph (replacing a previous capture); ssht_group_replay launches it on `stream`.  The
+ * buffers are bound at capture time. */
+SSHT_API int ssht_group_capture(ssht_group_t group, const void* flm, void* f, void* flm_out, void* stream);
+SSHT_API int ssht_group_replay(ssht_group_t group, void* stream);
+
+/* Wait for the group's work and report a latched kernel-side timeout (SSHT_ETIMEOUT). */
+SSHT_API int ssht_group_check(ssht_group_t group);
 
 /* Message describing the last error on the calling host thread ("" if none). */
 SSHT_API const char* ssht_last_error(void);

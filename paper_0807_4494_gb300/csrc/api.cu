@@ -2,6 +2,7 @@
 // stages of each transform, host-pointer staging and error reporting.
 #include "ssht_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -111,6 +112,10 @@ struct ssht_plan_s {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool join_pending = false;
+  // A plan of a group shares the Delta table of its band-limit with the group's other plans:
+  // the group runs the recursion (recorded by delta_event), the plan only its spin column.
+  bool delta_shared = false;
+  cudaEvent_t delta_event = nullptr;
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -216,9 +221,12 @@ int set_streams(ssht_plan_t p, cudaStream_t st) {
 
 int run_delta(ssht_plan_t p, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_DELTA, st);
-  SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
+  if (!p->delta_shared) {
+    SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
+    p->launches += 1;
+  }
   SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, p->Uf, st), "spin column launch");
-  p->launches += 2;
+  p->launches += 1;
   return 0;
 }
 
@@ -244,6 +252,7 @@ int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
   SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
   SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
+  if (p->delta_shared && p->delta_event) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->delta_event, 0), "shared Delta wait");
   int rc = run_delta(p, p->aux);
   if (rc) return rc;
   if (p->tc && (rc = pack_a(p, forward, p->aux))) return rc;
@@ -464,14 +473,14 @@ void release(ssht_plan_t p) {
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
-  void* ptrs[] = {p->delta.table, p->delta.slab[0], p->delta.slab[1], p->delta.sqrt_tab, p->delta.barrier,
-                  p->delta.status, p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
+  if (!p->delta_shared) delta_free(p->delta);
+  void* ptrs[] = {p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
 }
 
-int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
+int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared = nullptr) {
   if (!out || !desc) return fail(SSHT_EINVAL, "null argument");
   *out = nullptr;
   const int L = desc->L, s = desc->s, B = desc->batch;
@@ -514,13 +523,18 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc) {
     release(p);
     return code;
   };
-  ce = delta_setup(p->delta, L, p->device);
-  if (ce != cudaSuccess) {
-    release(p);
-    return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
-                std::string("Delta recursion setup: ") + cudaGetErrorString(ce));
+  if (shared) {
+    p->delta = *shared;
+    p->delta_shared = true;
+  } else {
+    ce = delta_setup(p->delta, L, p->device);
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                  std::string("Delta recursion setup: ") + cudaGetErrorString(ce));
+    }
+    p->bytes += p->delta.bytes;
   }
-  p->bytes += p->delta.bytes;
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
   if ((rc = dalloc(p, (void**)&p->Uf, tri(L) * sizeof(float), "spin column (FP32)"))) return bail(rc);
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
@@ -745,5 +759,349 @@ int ssht_plan_profile_read(ssht_plan_t p, double* ms, long long* count, int nsta
 const char* ssht_last_error(void) { return g_last_error.c_str(); }
 
 int ssht_version(void) { return 100; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Groups: many fields of uneven band-limit and spin in one call (and one CUDA graph).
+//
+// Fields are bucketed by (L, s); each bucket is one plan over its fields, which sit contiguously
+// in the caller's flat buffers in group order (ssht_group_layout).  All buckets of one L share one
+// Delta table: in recompute mode each call runs one recursion per distinct L, on its own stream,
+// and the buckets wait for it before their spin column and packing; in cache mode the tables are
+// made once here.  Buckets run on their own streams, forked from and joined to the caller's.
+// With tuning on, each bucket times every contraction form of the group's precision class
+// (FP32, 3xTF32, split-BF16 for FP32-class groups; tensor-core forms only up to 64 fields) on
+// its own shape and keeps the fastest.
+// ---------------------------------------------------------------------------------------------
+
+struct ssht_group_s {
+  int device = 0;
+  int n = 0;
+  int precision = 0, delta_mode = 0;
+  size_t elem = 8;
+  std::vector<int> order;            // group position -> caller's field index
+  std::vector<long long> coff, goff; // per group position: element offsets of coefficients / samples
+  struct Holder {
+    int L = 0;
+    DeltaWork dw{};
+    cudaEvent_t ev = nullptr;
+  };
+  // The shared recursions run one after another on one stream: each is a cooperative grid over
+  // every SM, so running two at once would only make them wait for each other's SMs.
+  cudaStream_t rec_st = nullptr;
+  std::vector<Holder> holders;
+  struct Bucket {
+    int L = 0, s = 0, first = 0, count = 0, holder = 0;
+    ssht_plan_t plan = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+  };
+  std::vector<Bucket> buckets;
+  cudaEvent_t ev_start = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void group_release(ssht_group_t g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (auto& b : g->buckets) {
+    if (b.plan) release(b.plan);
+    if (b.st) cudaStreamDestroy(b.st);
+    if (b.ev) cudaEventDestroy(b.ev);
+  }
+  for (auto& h : g->holders) {
+    delta_free(h.dw);
+    if (h.ev) cudaEventDestroy(h.ev);
+  }
+  if (g->rec_st) cudaStreamDestroy(g->rec_st);
+  if (g->ev_start) cudaEventDestroy(g->ev_start);
+  delete g;
+}
+
+// One call of every bucket; which: 0 inverse, 1 forward, 2 adjoint.
+int group_call(ssht_group_t g, int which, const void* in, void* out, cudaStream_t st) {
+  SSHT_CUDA(cudaEventRecord(g->ev_start, st), "group fork");
+  if (g->delta_mode == SSHT_DELTA_RECOMPUTE) {
+    SSHT_CUDA(cudaStreamWaitEvent(g->rec_st, g->ev_start, 0), "group fork wait");
+    for (auto& h : g->holders) {
+      SSHT_CUDA(delta_run(h.dw, h.L, g->rec_st), "shared Delta recursion");
+      SSHT_CUDA(cudaEventRecord(h.ev, g->rec_st), "shared Delta event");
+    }
+  }
+  for (auto& b : g->buckets) {
+    ssht_plan_t p = b.plan;
+    SSHT_CUDA(cudaStreamWaitEvent(b.st, g->ev_start, 0), "group fork wait");
+    p->delta_event = g->delta_mode == SSHT_DELTA_RECOMPUTE ? g->holders[b.holder].ev : nullptr;
+    int rc = set_streams(p, b.st);
+    if (rc) return rc;
+    const long long ci = g->coff[b.first], gi = g->goff[b.first];
+    const char* src = (const char*)in + (which == 0 ? ci : gi) * g->elem;
+    char* dst = (char*)out + (which == 0 ? gi : ci) * g->elem;
+    if (which == 0)
+      rc = p->f64 ? inverse_impl<double>(p, src, dst, b.st) : inverse_impl<float>(p, src, dst, b.st);
+    else if (which == 1)
+      rc = p->f64 ? forward_impl<double>(p, src, dst, b.st) : forward_impl<float>(p, src, dst, b.st);
+    else
+      rc = p->f64 ? adjoint_impl<double>(p, src, dst, b.st) : adjoint_impl<float>(p, src, dst, b.st);
+    if (rc) return rc;
+    SSHT_CUDA(cudaEventRecord(b.ev, b.st), "group join event");
+  }
+  for (auto& b : g->buckets) SSHT_CUDA(cudaStreamWaitEvent(st, b.ev, 0), "group join wait");
+  return 0;
+}
+
+// Mean milliseconds of inverse + forward of one plan on zero data (shapes decide the time).
+int time_plan(ssht_plan_t p, float* ms) {
+  void *a = nullptr, *b = nullptr, *c = nullptr;
+  const size_t cb = p->coeff_bytes(), gb = p->grid_bytes();
+  int rc = 0;
+  if ((rc = dalloc(p, &a, cb, "tuning input")) || (rc = dalloc(p, &b, gb, "tuning grid")) ||
+      (rc = dalloc(p, &c, cb, "tuning output"))) {
+    cudaFree(a);
+    cudaFree(b);
+    return rc;
+  }
+  p->bytes -= cb + gb + cb;
+  cudaMemset(a, 0, cb);
+  cudaEvent_t e0, e1;
+  cudaStream_t st = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (int it = 0; it < 6 && !rc; ++it) {
+    if (it == 2) cudaEventRecord(e0, st);
+    rc = p->f64 ? inverse_impl<double>(p, a, b, st) : inverse_impl<float>(p, a, b, st);
+    if (!rc) rc = p->f64 ? forward_impl<double>(p, b, c, st) : forward_impl<float>(p, b, c, st);
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / 4.f;
+  cudaStreamDestroy(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(a);
+  cudaFree(b);
+  cudaFree(c);
+  return rc;
+}
+
+int group_create(ssht_group_t* out, int n, const int* Ls, const int* ss, int precision, int delta_mode, int tune) {
+  if (!out || !Ls || !ss) return fail(SSHT_EINVAL, "null argument");
+  *out = nullptr;
+  if (n < 1) return fail(SSHT_EINVAL, "a group needs at least one field");
+  if (precision != SSHT_FP64 && precision != SSHT_FP32 && precision != SSHT_TF32X3 && precision != SSHT_BF16X6)
+    return fail(SSHT_EINVAL, "unknown precision");
+  if (delta_mode != SSHT_DELTA_RECOMPUTE && delta_mode != SSHT_DELTA_CACHE) return fail(SSHT_EINVAL, "unknown Delta mode");
+  for (int i = 0; i < n; ++i) {
+    if (Ls[i] < 1 || Ls[i] > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
+    if (ss[i] <= -Ls[i] || ss[i] >= Ls[i]) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
+  }
+  ssht_group_t g = new (std::nothrow) ssht_group_s();
+  if (!g) return fail(SSHT_ENOMEM, "host allocation of the group");
+  auto bail = [&](int code) {
+    group_release(g);
+    return code;
+  };
+  cudaError_t ce = cudaGetDevice(&g->device);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&g->ev_start, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&g->rec_st, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(fail(SSHT_ECUDA, std::string("group setup: ") + cudaGetErrorString(ce)));
+  g->n = n;
+  g->precision = precision;
+  g->delta_mode = delta_mode;
+  g->elem = precision == SSHT_FP64 ? 16 : 8;
+  // group order: by L, then s, then the caller's index
+  g->order.resize(n);
+  for (int i = 0; i < n; ++i) g->order[i] = i;
+  std::stable_sort(g->order.begin(), g->order.end(),
+                   [&](int a, int b) { return Ls[a] != Ls[b] ? Ls[a] < Ls[b] : ss[a] < ss[b]; });
+  g->coff.resize(n + 1);
+  g->goff.resize(n + 1);
+  long long c = 0, q = 0;
+  for (int k = 0; k < n; ++k) {
+    const int L = Ls[g->order[k]];
+    g->coff[k] = c;
+    g->goff[k] = q;
+    c += (long long)L * L;
+    q += (long long)L * (2 * L - 1);
+  }
+  g->coff[n] = c;
+  g->goff[n] = q;
+  // shared Delta tables, one per distinct L
+  for (int k = 0; k < n; ++k) {
+    const int L = Ls[g->order[k]];
+    if (g->holders.empty() || g->holders.back().L != L) {
+      g->holders.emplace_back();
+      auto& h = g->holders.back();
+      h.L = L;
+      ce = delta_setup(h.dw, L, g->device);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h.ev, cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = delta_run(h.dw, L, 0);  // valid tables for tuning and cache mode
+      if (ce != cudaSuccess)
+        return bail(fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                         std::string("shared Delta setup: ") + cudaGetErrorString(ce)));
+    }
+  }
+  ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return bail(fail(SSHT_ECUDA, std::string("shared Delta: ") + cudaGetErrorString(ce)));
+  // buckets
+  for (int k = 0; k < n;) {
+    const int L = Ls[g->order[k]], s = ss[g->order[k]];
+    int e = k;
+    while (e < n && Ls[g->order[e]] == L && ss[g->order[e]] == s) ++e;
+    g->buckets.emplace_back();
+    auto& b = g->buckets.back();
+    b.L = L;
+    b.s = s;
+    b.first = k;
+    b.count = e - k;
+    b.holder = (int)g->holders.size() - 1;
+    while (g->holders[b.holder].L != L) --b.holder;
+    ce = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(fail(SSHT_ECUDA, "bucket stream setup"));
+    std::vector<int> cands;
+    if (!tune || precision == SSHT_FP64) {
+      cands.push_back(precision);
+    } else {
+      cands.push_back(SSHT_FP32);
+      if (b.count <= 64) {
+        cands.push_back(SSHT_TF32X3);
+        cands.push_back(SSHT_BF16X6);
+      }
+    }
+    if ((precision == SSHT_TF32X3 || precision == SSHT_BF16X6) && b.count > 64 && !tune)
+      return bail(fail(SSHT_EUNSUPPORTED, "tensor-core buckets take at most 64 fields"));
+    float best = 0.f;
+    for (int cand : cands) {
+      ssht_plan_desc d{L, s, b.count, cand, delta_mode, 0};
+      ssht_plan_t p = nullptr;
+      int rc = create(&p, &d, &g->holders[b.holder].dw);
+      if (rc) return bail(rc);
+      float ms = 0.f;
+      if (cands.size() > 1 && (rc = time_plan(p, &ms))) {
+        release(p);
+        return bail(rc);
+      }
+      if (!b.plan || ms < best) {
+        if (b.plan) release(b.plan);
+        b.plan = p;
+        best = ms;
+      } else {
+        release(p);
+      }
+    }
+    k = e;
+  }
+  *out = g;
+  g_last_error.clear();
+  return SSHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssht_group_create(ssht_group_t* out, int n, const int* L, const int* s, int precision, int delta_mode, int tune) {
+  return group_create(out, n, L, s, precision, delta_mode, tune);
+}
+
+int ssht_group_destroy(ssht_group_t g) {
+  group_release(g);
+  return SSHT_OK;
+}
+
+int ssht_group_layout(ssht_group_t g, int* order, long long* coeff_offset, long long* grid_offset) {
+  if (!g) return fail(SSHT_EINVAL, "null group");
+  for (int k = 0; k < g->n; ++k) {
+    if (order) order[k] = g->order[k];
+    if (coeff_offset) coeff_offset[k] = g->coff[k];
+    if (grid_offset) grid_offset[k] = g->goff[k];
+  }
+  if (coeff_offset) coeff_offset[g->n] = g->coff[g->n];
+  if (grid_offset) grid_offset[g->n] = g->goff[g->n];
+  return SSHT_OK;
+}
+
+int ssht_group_buckets(ssht_group_t g, int* nbuckets, int* L, int* s, int* count, int* precision) {
+  if (!g || !nbuckets) return fail(SSHT_EINVAL, "null argument");
+  const int nb = (int)g->buckets.size();
+  const int cap = *nbuckets;
+  *nbuckets = nb;
+  for (int i = 0; i < nb && i < cap; ++i) {
+    if (L) L[i] = g->buckets[i].L;
+    if (s) s[i] = g->buckets[i].s;
+    if (count) count[i] = g->buckets[i].count;
+    if (precision) precision[i] = g->buckets[i].plan->precision;
+  }
+  return SSHT_OK;
+}
+
+static int group_entry(ssht_group_t g, int which, const void* in, void* out, void* stream) {
+  if (!g || !in || !out) return fail(SSHT_EINVAL, "null argument");
+  int cur = -1;
+  SSHT_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+  if (cur != g->device) return fail(SSHT_EINVAL, "group used on another device");
+  if (!is_device_pointer(in) || !is_device_pointer(out)) return fail(SSHT_EINVAL, "group buffers must be device memory");
+  return group_call(g, which, in, out, (cudaStream_t)stream);
+}
+
+int ssht_group_inverse(ssht_group_t g, const void* flm, void* f, void* stream) { return group_entry(g, 0, flm, f, stream); }
+int ssht_group_forward(ssht_group_t g, const void* f, void* flm, void* stream) { return group_entry(g, 1, f, flm, stream); }
+int ssht_group_adjoint(ssht_group_t g, const void* f, void* flm, void* stream) { return group_entry(g, 2, f, flm, stream); }
+
+int ssht_group_capture(ssht_group_t g, const void* flm, void* f, void* flm_out, void* stream) {
+  if (!g || !flm || !f || !flm_out) return fail(SSHT_EINVAL, "null argument");
+  if (!is_device_pointer(flm) || !is_device_pointer(f) || !is_device_pointer(flm_out))
+    return fail(SSHT_EINVAL, "group buffers must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t cap = nullptr;
+  SSHT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  int rc = 0;
+  if (ce == cudaSuccess) {
+    rc = group_call(g, 0, flm, f, cap);
+    if (!rc) rc = group_call(g, 1, f, flm_out, cap);
+    ce = cudaStreamEndCapture(cap, &graph);
+  }
+  if (ce == cudaSuccess && !rc) ce = cudaGraphInstantiate(&g->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (rc) return rc;
+  if (ce != cudaSuccess) return fail(SSHT_ECUDA, std::string("group graph capture: ") + cudaGetErrorString(ce));
+  (void)st;
+  return SSHT_OK;
+}
+
+int ssht_group_replay(ssht_group_t g, void* stream) {
+  if (!g || !g->exec) return fail(SSHT_EINVAL, "no captured graph");
+  SSHT_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "graph launch");
+  return SSHT_OK;
+}
+
+int ssht_group_check(ssht_group_t g) {
+  if (!g) return fail(SSHT_EINVAL, "null group");
+  SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
+  for (auto& h : g->holders) {
+    int st = 0;
+    SSHT_CUDA(cudaMemcpy(&st, h.dw.status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (st != 0) {
+      cudaMemset(h.dw.status, 0, sizeof(int));
+      return fail(SSHT_ETIMEOUT, "a Delta recursion wait exceeded its spin limit");
+    }
+  }
+  return SSHT_OK;
+}
 
 }  // extern "C"

@@ -519,6 +519,15 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
+void delta_free(DeltaWork& w) {
+  void* ptrs[] = {w.table, w.slab[0], w.slab[1], w.sqrt_tab, w.barrier, w.status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  w.table = w.slab[0] = w.slab[1] = w.sqrt_tab = nullptr;
+  w.barrier = nullptr;
+  w.status = nullptr;
+}
+
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, (4 + (size_t)w.blocks) * sizeof(unsigned int), st)) != cudaSuccess) return e;

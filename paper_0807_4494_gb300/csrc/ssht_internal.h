@@ -46,6 +46,7 @@ struct DeltaWork {
 };
 
 cudaError_t delta_setup(DeltaWork& w, int L, int device);
+void delta_free(DeltaWork& w);
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st);
 // U[l][m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s}, l < L, 0 <= m' <= l, at tri(l) + m'; Uf is the
 // same in FP32 (rounded to nearest).

@@ -20,7 +20,10 @@ ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", 
           -5: "SSHT_EUNSUPPORTED"}
 EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspace_bytes", "ssht_inverse",
            "ssht_forward", "ssht_adjoint", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
-           "ssht_plan_profile_read", "ssht_wigner_delta_noalloc", "ssht_last_error", "ssht_version")
+           "ssht_plan_profile_read", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
+           "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
+           "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
+           "ssht_last_error", "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
 
 
@@ -59,6 +62,18 @@ def _lib():
             "ssht_plan_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), i,
                                         ctypes.POINTER(ctypes.c_longlong)], i),
             "ssht_wigner_delta_noalloc": ([i, vp, vp], i),
+            "ssht_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), i, i, i], i),
+            "ssht_group_destroy": ([vp], i),
+            "ssht_group_layout": ([vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)], i),
+            "ssht_group_buckets": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                    ctypes.POINTER(i)], i),
+            "ssht_group_inverse": ([vp, vp, vp, vp], i),
+            "ssht_group_forward": ([vp, vp, vp, vp], i),
+            "ssht_group_adjoint": ([vp, vp, vp, vp], i),
+            "ssht_group_capture": ([vp, vp, vp, vp, vp], i),
+            "ssht_group_replay": ([vp, vp], i),
+            "ssht_group_check": ([vp], i),
             "ssht_last_error": ([], ctypes.c_char_p),
             "ssht_version": ([], i),
         }
@@ -267,3 +282,122 @@ class InverseFunction(torch.autograd.Function):
 def inverse(flm, plan):
     """Inverse transform with autograd support."""
     return InverseFunction.apply(flm, plan)
+
+
+# ---- groups of uneven fields ------------------------------------------------------------------
+
+def ssht_group_create(Ls, ss, precision=FP32, delta_mode=RECOMPUTE, tune=True):
+    n = len(Ls)
+    h = ctypes.c_void_p()
+    La = (ctypes.c_int * n)(*[int(x) for x in Ls])
+    sa = (ctypes.c_int * n)(*[int(x) for x in ss])
+    _check(_lib().ssht_group_create(ctypes.byref(h), n, La, sa, int(precision), int(delta_mode), int(bool(tune))),
+           "ssht_group_create")
+    return h
+
+
+def ssht_group_layout(h, n):
+    order = (ctypes.c_int * n)()
+    co = (ctypes.c_longlong * (n + 1))()
+    go = (ctypes.c_longlong * (n + 1))()
+    _check(_lib().ssht_group_layout(h, order, co, go), "ssht_group_layout")
+    return list(order), list(co), list(go)
+
+
+def ssht_group_buckets(h):
+    cap = ctypes.c_int(0)
+    _check(_lib().ssht_group_buckets(h, ctypes.byref(cap), None, None, None, None), "ssht_group_buckets")
+    nb = cap.value
+    arr = [(ctypes.c_int * nb)() for _ in range(4)]
+    cap = ctypes.c_int(nb)
+    _check(_lib().ssht_group_buckets(h, ctypes.byref(cap), *arr), "ssht_group_buckets")
+    return [(arr[0][k], arr[1][k], arr[2][k], arr[3][k]) for k in range(nb)]
+
+
+class Group:
+    """Fields of uneven band-limit L_i and spin s_i transformed together (buckets by (L, s), one
+    shared Delta table per L, buckets on concurrent streams, optional autotuned contraction per
+    bucket, and inverse + forward capturable into one CUDA graph).
+
+    Data travels in flat complex tensors in the group's order: ``pack_coeffs`` / ``unpack_*``
+    convert from and to per-field lists (on the device, by slicing)."""
+
+    def __init__(self, Ls, ss, precision="fp32", delta_mode="recompute", tune=True):
+        self.Ls, self.ss = [int(x) for x in Ls], [int(x) for x in ss]
+        self.n = len(self.Ls)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        dm = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
+        self._h = ssht_group_create(self.Ls, self.ss, self.precision, dm, tune)
+        self.order, self.coff, self.goff = ssht_group_layout(self._h, self.n)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().ssht_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def buckets(self):
+        """[(L, s, fields, precision)] per bucket, precision after tuning."""
+        return ssht_group_buckets(self._h)
+
+    def empty_coeffs(self):
+        return torch.empty(self.coff[-1], dtype=self.dtype, device=self.device)
+
+    def empty_grid(self):
+        return torch.empty(self.goff[-1], dtype=self.dtype, device=self.device)
+
+    def pack_coeffs(self, flms, out=None):
+        """Per-field coefficient tensors [L_i^2] (caller's order) -> one flat tensor (group order)."""
+        out = self.empty_coeffs() if out is None else out
+        for k, i in enumerate(self.order):
+            out[self.coff[k]:self.coff[k + 1]].copy_(flms[i].reshape(-1))
+        return out
+
+    def unpack_coeffs(self, flat):
+        res = [None] * self.n
+        for k, i in enumerate(self.order):
+            res[i] = flat[self.coff[k]:self.coff[k + 1]]
+        return res
+
+    def unpack_grid(self, flat):
+        res = [None] * self.n
+        for k, i in enumerate(self.order):
+            L = self.Ls[i]
+            res[i] = flat[self.goff[k]:self.goff[k + 1]].view(L, 2 * L - 1)
+        return res
+
+    def _stream(self):
+        return torch.cuda.current_stream().cuda_stream
+
+    def inverse(self, flm_flat, out=None):
+        out = self.empty_grid() if out is None else out
+        _check(_lib().ssht_group_inverse(self._h, flm_flat.data_ptr(), out.data_ptr(), self._stream()), "ssht_group_inverse")
+        return out
+
+    def forward(self, f_flat, out=None):
+        out = self.empty_coeffs() if out is None else out
+        _check(_lib().ssht_group_forward(self._h, f_flat.data_ptr(), out.data_ptr(), self._stream()), "ssht_group_forward")
+        return out
+
+    def adjoint(self, f_flat, out=None):
+        out = self.empty_coeffs() if out is None else out
+        _check(_lib().ssht_group_adjoint(self._h, f_flat.data_ptr(), out.data_ptr(), self._stream()), "ssht_group_adjoint")
+        return out
+
+    def capture(self, flm_flat, f_flat, flm_out_flat):
+        """Capture inverse (flm -> f) then forward (f -> flm_out) into one CUDA graph."""
+        _check(_lib().ssht_group_capture(self._h, flm_flat.data_ptr(), f_flat.data_ptr(), flm_out_flat.data_ptr(),
+                                         self._stream()), "ssht_group_capture")
+
+    def replay(self):
+        _check(_lib().ssht_group_replay(self._h, self._stream()), "ssht_group_replay")
+
+    def check(self):
+        _check(_lib().ssht_group_check(self._h), "ssht_group_check")
