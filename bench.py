@@ -573,6 +573,12 @@ def error_sweep(args):
                     "inverse": float(np.abs(f0 - f_or).max() / np.abs(f_or).max()),
                     "forward": float(np.abs(back[0].cpu().numpy() - fw).max() / np.abs(fw).max()),
                     "roundtrip": float((back - x).abs().max() / x.abs().max())}
+            if prec == "fp64":
+                # the paper's triangular forward of the same grid: its five error metrics against
+                # the coefficients the grid was made from, next to the quadrature forward's
+                tri = plan.forward_triangular(f)[0].cpu().numpy()
+                line["triangular_forward_vs_true"] = T.error_metrics(flm[0], tri)
+                line["quadrature_forward_vs_true"] = T.error_metrics(flm[0], back[0].cpu().numpy())
             print(json.dumps(line), flush=True)
             plan.close()
             del f, back, x

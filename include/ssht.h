@@ -121,6 +121,14 @@ SSHT_API int ssht_forward(ssht_plan_t plan, const void* f, void* flm, void* stre
  * g: [batch][L][2L-1] complex in; flm: [batch][L*L] complex out. */
 SSHT_API int ssht_adjoint(ssht_plan_t plan, const void* g, void* flm, void* stream);
 
+/* The paper's own forward transform (Sec. 3.4.2, eqn matrix_fwd): F_{m m'} (m' >= 0) of the
+ * extended signal (the torus stage of ssht_forward without the weight convolution), then for each
+ * m the upper triangular system in l solved by back substitution.  Exact in exact arithmetic for
+ * band-limited f, but it loses accuracy as L grows (the instability the paper reports); it is
+ * here to reproduce that behaviour next to ssht_forward.  FP64 plans only (SSHT_EUNSUPPORTED
+ * otherwise).  f: [batch][L][2L-1] complex in; flm: [batch][L*L] complex out. */
+SSHT_API int ssht_forward_triangular(ssht_plan_t plan, const void* f, void* flm, void* stream);
+
 /* The table of Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 2.2, Risbo recursion) for
  * 0 <= l < L and 0 <= m', m <= l (the non-negative quadrant the paper precomputes, Sec. 4.1),
  * FP64, entry (l, m', m) at offset(l) + m'(l+1) + m with offset(l) = l(l+1)(2l+1)/6.

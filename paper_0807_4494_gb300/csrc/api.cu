@@ -690,6 +690,28 @@ int ssht_adjoint(ssht_plan_t p, const void* g, void* flm, void* stream) {
   return io_end(p, io, st);
 }
 
+int ssht_forward_triangular(ssht_plan_t p, const void* f, void* flm, void* stream) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  if (!p->f64) return fail(SSHT_EUNSUPPORTED, "the triangular forward is built for FP64 plans only");
+  if (p->d.L > 2048) return fail(SSHT_EUNSUPPORTED, "band-limit too large for the triangular solve");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = set_streams(p, st))) return rc;
+  IO io;
+  if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
+  if ((rc = begin_operands(p, 1, st))) return rc;
+  if ((rc = analysis_front<double>(p, io.in_dev, 0, st))) return rc;
+  if ((rc = join_operands(p, st))) return rc;
+  {
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(triangular_solve(p->d, p->s, p->B, p->delta.table, p->U, p->W1, p->ph64, io.out_dev, st),
+              "triangular solve");
+    p->launches += 2;
+  }
+  return io_end(p, io, st);
+}
+
 int ssht_wigner_delta(ssht_plan_t p, double* out, void* stream) {
   if (!p || !out) return fail(SSHT_EINVAL, "null argument");
   int rc = check_device(p);

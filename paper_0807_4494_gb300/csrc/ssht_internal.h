@@ -66,6 +66,11 @@ template <typename T>
 cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* table, const double* U,
                                   const void* H, void* flm, cudaStream_t st);
 
+// The paper's triangular forward (triangular.cu), FP64: Fk = theta-DFT bins of the extended
+// columns [B][N][N] (no phase, no 1/N), flm [B][L*L] double2.
+cudaError_t triangular_solve(const Dims& d, int s, int B, const double* table, const double* U, const void* Fk,
+                             const double2* ph, void* flm, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16, at most 64 fields per plan
 // ---------------------------------------------------------------------------

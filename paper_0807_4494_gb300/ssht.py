@@ -19,7 +19,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
 ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
           -5: "SSHT_EUNSUPPORTED"}
 EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspace_bytes", "ssht_inverse",
-           "ssht_forward", "ssht_adjoint", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
+           "ssht_forward", "ssht_adjoint", "ssht_forward_triangular", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
            "ssht_plan_profile_read", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
@@ -56,6 +56,7 @@ def _lib():
             "ssht_inverse": ([vp, vp, vp, vp], i),
             "ssht_forward": ([vp, vp, vp, vp], i),
             "ssht_adjoint": ([vp, vp, vp, vp], i),
+            "ssht_forward_triangular": ([vp, vp, vp, vp], i),
             "ssht_wigner_delta": ([vp, vp, vp], i),
             "ssht_plan_check": ([vp], i),
             "ssht_plan_profile": ([vp, i], i),
@@ -119,6 +120,10 @@ def ssht_forward(h, f_ptr, flm_ptr, stream=0):
 
 def ssht_adjoint(h, g_ptr, flm_ptr, stream=0):
     _check(_lib().ssht_adjoint(h, g_ptr, flm_ptr, stream), "ssht_adjoint")
+
+
+def ssht_forward_triangular(h, f_ptr, flm_ptr, stream=0):
+    _check(_lib().ssht_forward_triangular(h, f_ptr, flm_ptr, stream), "ssht_forward_triangular")
 
 
 def ssht_wigner_delta(h, out_ptr, stream=0):
@@ -241,6 +246,13 @@ class Plan:
         out = self._out(out, g, self.grid_shape(), self.coeff_shape())
         ssht_adjoint(self._h, self._arg(g, self.grid_shape(), "g"), self._arg(out, self.coeff_shape(), "flm"),
                      self._stream(stream, g))
+        return out
+
+    def forward_triangular(self, f, out=None, stream=None):
+        """The paper's triangular forward (FP64 plans; unstable at high band-limit)."""
+        out = self._out(out, f, self.grid_shape(), self.coeff_shape())
+        ssht_forward_triangular(self._h, self._arg(f, self.grid_shape(), "f"), self._arg(out, self.coeff_shape(), "flm"),
+                                self._stream(stream, f))
         return out
 
     def wigner_delta(self, out=None, stream=None):
