@@ -116,6 +116,12 @@ struct ssht_plan_s {
   // the group runs the recursion (recorded by delta_event), the plan only its spin column.
   bool delta_shared = false;
   cudaEvent_t delta_event = nullptr;
+  // Recorded after the last kernel of a call that reads the Delta table, U or the A tiles: the
+  // next call's recursion and packing only wait for it (not for the rest of the previous call,
+  // e.g. the inverse's torus stage), within the same capture sequence (0 = not capturing).
+  cudaEvent_t ev_free = nullptr;
+  bool free_valid = false;
+  unsigned long long free_capture = 0;
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -248,10 +254,33 @@ int ensure_delta(ssht_plan_t p, cudaStream_t st) {
 
 // Start making Delta (and, for the tensor-core path, the packed A operand of one direction) on
 // the plan's second stream, after everything already queued on st; join_operands makes st wait.
+unsigned long long capture_id(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  unsigned long long id = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, &id) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return cs == cudaStreamCaptureStatusActive ? id : 0;
+}
+
+// After the last reader of the table, U and the A tiles in a call.
+int mark_free(ssht_plan_t p, cudaStream_t st) {
+  SSHT_CUDA(cudaEventRecord(p->ev_free, st), "operands-free event");
+  p->free_valid = true;
+  p->free_capture = capture_id(st);
+  return 0;
+}
+
 int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
-  SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
-  SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
+  if (p->free_valid && p->free_capture == capture_id(st)) {
+    // the previous call's readers are done once ev_free fires; its later work may still run
+    SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free, 0), "operands-free wait");
+  } else {
+    SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
+    SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
+  }
   if (p->delta_shared && p->delta_event) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->delta_event, 0), "shared Delta wait");
   int rc = run_delta(p, p->aux);
   if (rc) return rc;
@@ -289,14 +318,16 @@ template <typename T>
 int project(ssht_plan_t p, const void* H, void* flm, cudaStream_t st) {
   int rc;
   if (p->tc) {
-    if ((rc = tc_pack(p, 1, H, st)) || (rc = join_operands(p, st))) return rc;
-    return tc_multiply(p, 1, flm, st);
+    if ((rc = tc_pack(p, 1, H, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
+    return mark_free(p, st);
   }
   if ((rc = join_operands(p, st))) return rc;
-  StageScope sc(p, SSHT_STAGE_PROJECT, st);
-  SSHT_CUDA(contract_project_simt<T>(p->d, p->s, p->B, p->delta.table, p->U, H, flm, st), "projection");
-  p->launches += 1;
-  return 0;
+  {
+    StageScope sc(p, SSHT_STAGE_PROJECT, st);
+    SSHT_CUDA(contract_project_simt<T>(p->d, p->s, p->B, p->delta.table, p->U, H, flm, st), "projection");
+    p->launches += 1;
+  }
+  return mark_free(p, st);
 }
 
 int check_device(ssht_plan_t p) {
@@ -370,7 +401,8 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   int rc = begin_operands(p, 0, st);
   if (rc) return rc;
   if (p->tc) {
-    if ((rc = tc_pack(p, 0, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)))
+    if ((rc = tc_pack(p, 0, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)) ||
+        (rc = mark_free(p, st)))
       return rc;
   } else {
     if ((rc = join_operands(p, st))) return rc;
@@ -379,6 +411,7 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
               "inverse contraction");
     p->launches += 1;
   }
+  if (!p->tc && (rc = mark_free(p, st))) return rc;
   if (p->torus) {
     if ((rc = run_torus(p, 0, p->W1, p->W2, st))) return rc;
     return run_torus(p, 1, p->W2, f, st);
@@ -469,6 +502,7 @@ void release(ssht_plan_t p) {
   if (p->torus) torus_destroy(p->torus);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_free) cudaEventDestroy(p->ev_free);
   if (p->aux) cudaStreamDestroy(p->aux);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
@@ -503,6 +537,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_free, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     release(p);
     return fail(SSHT_ECUDA, std::string("plan stream/event setup: ") + cudaGetErrorString(ce));
@@ -709,6 +744,7 @@ int ssht_forward_triangular(ssht_plan_t p, const void* f, void* flm, void* strea
               "triangular solve");
     p->launches += 2;
   }
+  if ((rc = mark_free(p, st))) return rc;
   return io_end(p, io, st);
 }
 
@@ -725,6 +761,7 @@ int ssht_wigner_delta(ssht_plan_t p, double* out, void* stream) {
     SSHT_CUDA(cudaMemcpyAsync(out, p->delta.table, bytes, cudaMemcpyDeviceToHost, st), "Delta table copy");
     SSHT_CUDA(cudaStreamSynchronize(st), "stream synchronize");
   }
+  if ((rc = mark_free(p, st))) return rc;  // the recursion above ran on st: later calls wait for it
   SSHT_CUDA(cudaGetLastError(), "kernel launch");
   return SSHT_OK;
 }

@@ -292,3 +292,35 @@ def test_plans_of_different_sizes_interleave(precision):
     assert torch.equal(f1, f2)
     big.check()
     small.check()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_back_to_back_calls_without_host_sync(precision):
+    """A call's recursion may start while the previous call's torus stage still runs; calls queued
+    back to back (with a Delta table copy between them) give what synchronised calls give."""
+    L, s, B = 96, 1, 4
+    plan = S().Plan(L, s, B, precision=precision)
+    dt = plan.dtype
+    flm = torch.from_numpy(inputs.coeffs(L, s, B, seed=21)).to(dt).cuda()
+    f_ref = plan.inverse(flm)
+    torch.cuda.synchronize()
+    b_ref = plan.forward(f_ref)
+    torch.cuda.synchronize()
+    t_ref = plan.wigner_delta()
+    torch.cuda.synchronize()
+    outs = []
+    for _ in range(3):
+        f = plan.inverse(flm)
+        t = plan.wigner_delta()
+        b = plan.forward(f)
+        a = plan.adjoint(f)
+        outs.append((f, t, b, a))
+    torch.cuda.synchronize()
+    plan.check()
+    a_ref = plan.adjoint(f_ref)
+    torch.cuda.synchronize()
+    for f, t, b, a in outs:
+        assert torch.equal(f, f_ref)
+        assert torch.equal(t, t_ref)
+        assert torch.equal(b, b_ref)
+        assert torch.equal(a, a_ref)
