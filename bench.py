@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cache-line", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip the other split precision's line")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (captured graph) line")
+    ap.add_argument("--no-real", action="store_true", help="skip the real spin-0 fields line")
     ap.add_argument("--error-sweep", action="store_true",
                     help="print errors vs the FP64 oracle for L = 32 .. 2048 and every precision, then exit")
     return ap.parse_args()
@@ -423,6 +424,12 @@ def run_ssht(args):
     if not args.no_uneven:
         uneven = run_uneven(args, torch, inputs, ssht, world, device, stream, rank)
 
+    # the paper's real workload: real spin-0 fields (U[-1,1] coefficients with the reality
+    # condition), 2B real fields per step, two per complex transform
+    real_line = None
+    if not args.no_real and prec in ("tf32x3", "bf16x6", "fp32", "fp64"):
+        real_line = run_real(args, torch, inputs, ssht, world, device, stream, rank, prec)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(L, s, flm_np[0])
@@ -446,6 +453,7 @@ def run_ssht(args):
             "gpu_launches": int(launches1 - launches0),
             "delta_cache": cache_line,
             "uneven_batch": uneven,
+            "real_fields": real_line,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -453,6 +461,43 @@ def run_ssht(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_real(args, torch, inputs, ssht, world, device, stream, rank, prec):
+    L, nreal = args.L, 2 * args.batch
+    plan = ssht.Plan(L, 0, nreal, precision=prec, delta_mode=args.delta_mode, real=True)
+    flm_np = inputs.coeffs(L, 0, nreal, seed=rank_seed(rank, nreal), spectrum="paper", real=True)
+    flm = torch.from_numpy(flm_np).to(plan.dtype).to(device)
+    f = torch.empty(plan.grid_shape(), dtype=plan.grid_dtype, device=device)
+    back = torch.empty(plan.coeff_shape(), dtype=plan.dtype, device=device)
+
+    def step():
+        plan.inverse(flm, out=f)
+        plan.forward(f, out=back)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world, device)
+    nrep = min(args.steps, 10)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nrep):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    res = {"workload": "L=%d s=0, %d real fields per step (U[-1,1] with the reality condition), two per complex "
+                       "transform" % (L, nreal), "precision": prec, "value": throughput(world, nreal, nrep, ms),
+           "unit": "transforms/s", "ms_per_step": ms / nrep, "steps": nrep,
+           "roundtrip": float((back - flm).abs().max() / flm.abs().max())}
+    if rank == 0 and not args.no_check:
+        from oracle import transforms as T
+        f_or = T.inverse(flm_np[0], L, 0)
+        res["inverse"] = float(np.abs(f[0].cpu().numpy() - f_or.real).max() / np.abs(f_or).max())
+    plan.close()
+    return res
 
 
 def run_uneven(args, torch, inputs, ssht, world, device, stream, rank):

@@ -72,13 +72,20 @@ typedef enum {
   SSHT_DELTA_CACHE = 1      /* the recursion runs once at plan creation; calls reuse it  */
 } ssht_delta_mode;
 
+/* Plan flags. */
+#define SSHT_FLAG_REAL 1 /* real fields of spin 0: f real, sf_{l,-m} = (-1)^m conj(sf_lm) (the
+                          * conjugate symmetry of Sec. 3.3).  batch counts real fields; two ride in
+                          * one complex transform (half the work).  Samples f are real arrays
+                          * [batch][L][2L-1] (double or float); coefficients stay complex and the
+                          * inverse reads them as given (they must have the symmetry). */
+
 typedef struct {
   int L;          /* exclusive band-limit, 1 <= L <= 2048                      */
   int s;          /* spin, |s| < L                                              */
   int batch;      /* number of fields per call, 1 <= batch <= 65535            */
   int precision;  /* ssht_precision                                            */
   int delta_mode; /* ssht_delta_mode                                           */
-  int flags;      /* reserved, must be 0                                       */
+  int flags;      /* 0 or SSHT_FLAG_REAL                                       */
 } ssht_plan_desc;
 
 typedef struct ssht_plan_s* ssht_plan_t;

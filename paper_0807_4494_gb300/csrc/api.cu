@@ -133,8 +133,18 @@ struct ssht_plan_s {
   long long prof_n[SSHT_NUM_STAGES] = {};
   long long launches = 0;
 
-  size_t coeff_bytes() const { return (size_t)B * d.L * d.L * elem; }
-  size_t grid_bytes() const { return (size_t)B * d.L * d.N * elem; }
+  // Real spin-0 fields (SSHT_FLAG_REAL): nreal caller fields ride two to a complex field; B is
+  // the number of complex fields the transforms see, rc / rg their coefficients and samples.
+  bool real = false;
+  int nreal = 0;
+  void* rc = nullptr;
+  void* rg = nullptr;
+
+  // bytes of the caller's buffers
+  size_t coeff_bytes() const { return (size_t)(real ? nreal : B) * d.L * d.L * elem; }
+  size_t grid_bytes() const { return real ? (size_t)nreal * d.L * d.N * (elem / 2) : (size_t)B * d.L * d.N * elem; }
+  size_t pair_coeff_bytes() const { return (size_t)B * d.L * d.L * elem; }
+  size_t pair_grid_bytes() const { return (size_t)B * d.L * d.N * elem; }
 };
 
 namespace {
@@ -491,6 +501,28 @@ int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
   return project<T>(p, p->W2, flm, st);
 }
 
+// Real spin-0 fields, two to a complex field: which = 0 inverse, 1 forward, 2 adjoint.
+template <typename T>
+int real_call(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t st) {
+  const int L = p->d.L;
+  int rc;
+  {
+    StageScope sc(p, SSHT_STAGE_PACK, st);
+    if (which == 0) SSHT_CUDA(real_pack_coeffs<T>(L, p->nreal, in, p->rc, st), "real-field packing");
+    else SSHT_CUDA(real_pack_grid<T>(L, p->nreal, in, p->rg, st), "real-field packing");
+    p->launches += 1;
+  }
+  if (which == 0) rc = inverse_impl<T>(p, p->rc, p->rg, st);
+  else if (which == 1) rc = forward_impl<T>(p, p->rg, p->rc, st);
+  else rc = adjoint_impl<T>(p, p->rg, p->rc, st);
+  if (rc) return rc;
+  StageScope sc(p, SSHT_STAGE_PACK, st);
+  if (which == 0) SSHT_CUDA(real_unpack_grid<T>(L, p->nreal, p->rg, out, st), "real-field unpacking");
+  else SSHT_CUDA(real_unpack_coeffs<T>(L, p->nreal, p->rc, out, st), "real-field unpacking");
+  p->launches += 1;
+  return 0;
+}
+
 void release(ssht_plan_t p) {
   if (!p) return;
   cudaDeviceSynchronize();
@@ -508,7 +540,7 @@ void release(ssht_plan_t p) {
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
   if (!p->delta_shared) delta_free(p->delta);
-  void* ptrs[] = {p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out};
+  void* ptrs[] = {p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out, p->rc, p->rg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -517,18 +549,22 @@ void release(ssht_plan_t p) {
 int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared = nullptr) {
   if (!out || !desc) return fail(SSHT_EINVAL, "null argument");
   *out = nullptr;
-  const int L = desc->L, s = desc->s, B = desc->batch;
+  const int L = desc->L, s = desc->s, nfields = desc->batch;
   if (L < 1 || L > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
   if (s <= -L || s >= L) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
-  if (B < 1 || B > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
-  if (desc->flags != 0) return fail(SSHT_EINVAL, "flags must be 0");
+  if (nfields < 1 || nfields > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
+  if ((desc->flags & ~SSHT_FLAG_REAL) != 0) return fail(SSHT_EINVAL, "unknown flags");
+  const bool real = (desc->flags & SSHT_FLAG_REAL) != 0;
+  if (real && s != 0) return fail(SSHT_EINVAL, "real fields (SSHT_FLAG_REAL) need spin 0");
+  if (real && shared) return fail(SSHT_EINVAL, "groups take complex fields only");
+  const int B = real ? (nfields + 1) / 2 : nfields;  // complex fields the transforms see
   if (desc->delta_mode != SSHT_DELTA_RECOMPUTE && desc->delta_mode != SSHT_DELTA_CACHE)
     return fail(SSHT_EINVAL, "unknown Delta mode");
   if (desc->precision != SSHT_FP64 && desc->precision != SSHT_FP32 && desc->precision != SSHT_TF32X3 &&
       desc->precision != SSHT_BF16X6)
     return fail(SSHT_EINVAL, "unknown precision");
   if ((desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6) && B > 64)
-    return fail(SSHT_EUNSUPPORTED, "tensor-core plans take at most 64 fields per plan in this version");
+    return fail(SSHT_EUNSUPPORTED, "tensor-core plans take at most 64 complex fields (128 real fields) per plan");
 
   ssht_plan_t p = new (std::nothrow) ssht_plan_s();
   if (!p) return fail(SSHT_ENOMEM, "host allocation of the plan");
@@ -550,6 +586,8 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   p->B = B;
   p->precision = desc->precision;
   p->delta_mode = desc->delta_mode;
+  p->real = real;
+  p->nreal = real ? nfields : 0;
   p->f64 = desc->precision == SSHT_FP64;
   p->elem = p->f64 ? 16 : 8;
   const Dims& d = p->d;
@@ -575,6 +613,10 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
   // rows of N x L only.
   const size_t torus = (size_t)B * d.N * (p->f64 ? d.N : d.L) * p->elem;
+  if (real) {
+    if ((rc = dalloc(p, &p->rc, p->pair_coeff_bytes(), "real-field pair coefficients"))) return bail(rc);
+    if ((rc = dalloc(p, &p->rg, p->pair_grid_bytes(), "real-field pair samples"))) return bail(rc);
+  }
   if ((rc = dalloc(p, &p->W1, torus, "torus workspace 1"))) return bail(rc);
   if ((rc = dalloc(p, &p->W2, torus, "torus workspace 2"))) return bail(rc);
   if (p->f64) {
@@ -694,7 +736,10 @@ int ssht_inverse(ssht_plan_t p, const void* flm, void* f, void* stream) {
   if ((rc = set_streams(p, st))) return rc;
   IO io;
   if ((rc = io_begin(p, flm, p->coeff_bytes(), f, p->grid_bytes(), st, &io))) return rc;
-  rc = p->f64 ? inverse_impl<double>(p, io.in_dev, io.out_dev, st) : inverse_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (p->real)
+    rc = p->f64 ? real_call<double>(p, 0, io.in_dev, io.out_dev, st) : real_call<float>(p, 0, io.in_dev, io.out_dev, st);
+  else
+    rc = p->f64 ? inverse_impl<double>(p, io.in_dev, io.out_dev, st) : inverse_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;
   return io_end(p, io, st);
 }
@@ -707,7 +752,10 @@ int ssht_forward(ssht_plan_t p, const void* f, void* flm, void* stream) {
   if ((rc = set_streams(p, st))) return rc;
   IO io;
   if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
-  rc = p->f64 ? forward_impl<double>(p, io.in_dev, io.out_dev, st) : forward_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (p->real)
+    rc = p->f64 ? real_call<double>(p, 1, io.in_dev, io.out_dev, st) : real_call<float>(p, 1, io.in_dev, io.out_dev, st);
+  else
+    rc = p->f64 ? forward_impl<double>(p, io.in_dev, io.out_dev, st) : forward_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;
   return io_end(p, io, st);
 }
@@ -720,7 +768,10 @@ int ssht_adjoint(ssht_plan_t p, const void* g, void* flm, void* stream) {
   if ((rc = set_streams(p, st))) return rc;
   IO io;
   if ((rc = io_begin(p, g, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
-  rc = p->f64 ? adjoint_impl<double>(p, io.in_dev, io.out_dev, st) : adjoint_impl<float>(p, io.in_dev, io.out_dev, st);
+  if (p->real)
+    rc = p->f64 ? real_call<double>(p, 2, io.in_dev, io.out_dev, st) : real_call<float>(p, 2, io.in_dev, io.out_dev, st);
+  else
+    rc = p->f64 ? adjoint_impl<double>(p, io.in_dev, io.out_dev, st) : adjoint_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;
   return io_end(p, io, st);
 }
@@ -735,16 +786,29 @@ int ssht_forward_triangular(ssht_plan_t p, const void* f, void* flm, void* strea
   if ((rc = set_streams(p, st))) return rc;
   IO io;
   if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
+  const void* src = io.in_dev;
+  void* dst = io.out_dev;
+  if (p->real) {
+    StageScope sc(p, SSHT_STAGE_PACK, st);
+    SSHT_CUDA(real_pack_grid<double>(p->d.L, p->nreal, io.in_dev, p->rg, st), "real-field packing");
+    p->launches += 1;
+    src = p->rg;
+    dst = p->rc;
+  }
   if ((rc = begin_operands(p, 1, st))) return rc;
-  if ((rc = analysis_front<double>(p, io.in_dev, 0, st))) return rc;
+  if ((rc = analysis_front<double>(p, src, 0, st))) return rc;
   if ((rc = join_operands(p, st))) return rc;
   {
     StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(triangular_solve(p->d, p->s, p->B, p->delta.table, p->U, p->W1, p->ph64, io.out_dev, st),
-              "triangular solve");
+    SSHT_CUDA(triangular_solve(p->d, p->s, p->B, p->delta.table, p->U, p->W1, p->ph64, dst, st), "triangular solve");
     p->launches += 2;
   }
   if ((rc = mark_free(p, st))) return rc;
+  if (p->real) {
+    StageScope sc(p, SSHT_STAGE_PACK, st);
+    SSHT_CUDA(real_unpack_coeffs<double>(p->d.L, p->nreal, p->rc, io.out_dev, st), "real-field unpacking");
+    p->launches += 1;
+  }
   return io_end(p, io, st);
 }
 

@@ -1,0 +1,139 @@
+// Real fields of spin 0: f real, so sf_{l,-m} = (-1)^m conj(sf_lm) (the second conjugate symmetry
+// of Sec. 3.3: with the theta parity already used by every plan, a factor of four over a transform
+// that uses neither).  Two real fields ride in one complex field, f = f1 + i f2, whose
+// coefficients are sf = sf1 + i sf2 by linearity; the transforms are the complex ones and these
+// kernels only pack and unpack:
+//   inverse:  sf = sf1 + i sf2  ->  f  ->  f1 = Re f, f2 = Im f
+//   forward / adjoint:  f = f1 + i f2  ->  c  ->  sf1_lm = (c_lm + e_lm)/2, sf2_lm = (c_lm - e_lm)/(2i),
+//             e_lm = (-1)^m conj(c_{l,-m})
+// (e = sf1 - i sf2 because each of sf1, sf2 has the symmetry).  Field 2p and 2p+1 of the caller
+// pair into complex field p; an odd count pairs the last field with zero.
+#include "ssht_internal.h"
+
+namespace ssht {
+namespace {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <typename T>
+__global__ void pack_coeffs_kernel(long long n2, long long npair, int nreal, const typename Cx<T>::type* __restrict__ flm,
+                                   typename Cx<T>::type* __restrict__ rc) {
+  using C = typename Cx<T>::type;
+  const long long total = npair * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / n2, e = i - p * n2;
+    const C a = flm[2 * p * n2 + e];
+    C b;
+    b.x = 0;
+    b.y = 0;
+    if (2 * p + 1 < nreal) b = flm[(2 * p + 1) * n2 + e];
+    C r;
+    r.x = a.x - b.y;  // a + i b
+    r.y = a.y + b.x;
+    rc[i] = r;
+  }
+}
+
+template <typename T>
+__global__ void pack_grid_kernel(long long n2, long long npair, int nreal, const T* __restrict__ f,
+                                 typename Cx<T>::type* __restrict__ rg) {
+  using C = typename Cx<T>::type;
+  const long long total = npair * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / n2, e = i - p * n2;
+    C r;
+    r.x = f[2 * p * n2 + e];
+    r.y = (2 * p + 1 < nreal) ? f[(2 * p + 1) * n2 + e] : T(0);
+    rg[i] = r;
+  }
+}
+
+template <typename T>
+__global__ void unpack_grid_kernel(long long n2, long long npair, int nreal, const typename Cx<T>::type* __restrict__ rg,
+                                   T* __restrict__ f) {
+  const long long total = npair * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / n2, e = i - p * n2;
+    const auto z = rg[i];
+    f[2 * p * n2 + e] = z.x;
+    if (2 * p + 1 < nreal) f[(2 * p + 1) * n2 + e] = z.y;
+  }
+}
+
+template <typename T>
+__global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const typename Cx<T>::type* __restrict__ rc,
+                                     typename Cx<T>::type* __restrict__ flm) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * L;
+  const long long total = npair * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / n2, e = i - p * n2;
+    int l = (int)sqrtf((float)e);  // e < 2^22: exact float, then an integer correction
+    while ((long long)l * l > e) --l;
+    while ((long long)(l + 1) * (l + 1) <= e) ++l;
+    const int m = (int)(e - (long long)l * l - l);
+    const C c = rc[i];
+    const C d = rc[p * n2 + (long long)l * l + l - m];
+    const T sg = (m & 1) ? T(-1) : T(1);
+    const T ex = sg * d.x, ey = -sg * d.y;  // e = (-1)^m conj(d)
+    C a, b;
+    a.x = T(0.5) * (c.x + ex);
+    a.y = T(0.5) * (c.y + ey);
+    b.x = T(0.5) * (c.y - ey);  // (c - e) / (2i)
+    b.y = -T(0.5) * (c.x - ex);
+    flm[2 * p * n2 + e] = a;
+    if (2 * p + 1 < nreal) flm[(2 * p + 1) * n2 + e] = b;
+  }
+}
+
+unsigned blocks_for(long long n) {
+  const long long b = (n + 255) / 256;
+  return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t real_pack_coeffs(int L, int nreal, const void* flm, void* rc, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * L, np = (nreal + 1) / 2;
+  pack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)flm, (C*)rc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t real_pack_grid(int L, int nreal, const void* f, void* rg, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * (2 * L - 1), np = (nreal + 1) / 2;
+  pack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const T*)f, (C*)rg);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t real_unpack_grid(int L, int nreal, const void* rg, void* f, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * (2 * L - 1), np = (nreal + 1) / 2;
+  unpack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)rg, (T*)f);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * L, np = (nreal + 1) / 2;
+  unpack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(L, np, nreal, (const C*)rc, (C*)flm);
+  return cudaGetLastError();
+}
+
+#define SSHT_REAL_INST(T)                                                                          \
+  template cudaError_t real_pack_coeffs<T>(int, int, const void*, void*, cudaStream_t);          \
+  template cudaError_t real_pack_grid<T>(int, int, const void*, void*, cudaStream_t);            \
+  template cudaError_t real_unpack_grid<T>(int, int, const void*, void*, cudaStream_t);          \
+  template cudaError_t real_unpack_coeffs<T>(int, int, const void*, void*, cudaStream_t);
+SSHT_REAL_INST(double)
+SSHT_REAL_INST(float)
+#undef SSHT_REAL_INST
+
+}  // namespace ssht

@@ -71,6 +71,13 @@ cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* tab
 cudaError_t triangular_solve(const Dims& d, int s, int B, const double* table, const double* U, const void* Fk,
                              const double2* ph, void* flm, cudaStream_t st);
 
+// Real spin-0 fields two to a complex field (real.cu); T is double or float.  flm: [nreal][L*L]
+// complex, f: [nreal][L][2L-1] real; rc, rg: the complex pairs ([ceil(nreal/2)][...]).
+template <typename T> cudaError_t real_pack_coeffs(int L, int nreal, const void* flm, void* rc, cudaStream_t st);
+template <typename T> cudaError_t real_pack_grid(int L, int nreal, const void* f, void* rg, cudaStream_t st);
+template <typename T> cudaError_t real_unpack_grid(int L, int nreal, const void* rg, void* f, cudaStream_t st);
+template <typename T> cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16, at most 64 fields per plan
 // ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libssht.so")
 
 FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
+FLAG_REAL = 1
 RECOMPUTE, CACHE = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
 ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
@@ -99,9 +100,9 @@ def ssht_plan(L, s, batch):
     return h
 
 
-def ssht_plan_ex(L, s, batch, precision=FP64, delta_mode=RECOMPUTE):
+def ssht_plan_ex(L, s, batch, precision=FP64, delta_mode=RECOMPUTE, flags=0):
     h = ctypes.c_void_p()
-    d = PlanDesc(L, s, batch, precision, delta_mode, 0)
+    d = PlanDesc(L, s, batch, precision, delta_mode, flags)
     _check(_lib().ssht_plan_ex(ctypes.byref(h), ctypes.byref(d)), "ssht_plan_ex")
     return h
 
@@ -176,15 +177,19 @@ class Plan:
 
     Tensors: coefficients ``[batch, L*L]``, samples ``[batch, L, 2L-1]`` (complex128 for
     precision ``fp64``, complex64 otherwise), on the plan's CUDA device or on the host.
+    ``real=True`` (spin 0): real fields, samples real (float64 / float32), coefficients complex
+    with sf_{l,-m} = (-1)^m conj(sf_lm).
     """
 
-    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute"):
+    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False):
         self.L, self.s, self.batch = int(L), int(s), int(batch)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.delta_mode = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
+        self.real = bool(real)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
-        self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode)
+        self.grid_dtype = (torch.float64 if self.precision == FP64 else torch.float32) if self.real else self.dtype
+        self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode, FLAG_REAL if self.real else 0)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -207,9 +212,10 @@ class Plan:
     def grid_shape(self):
         return (self.batch, self.L, self.N)
 
-    def _arg(self, t, shape, name):
-        if t.dtype != self.dtype:
-            raise TypeError("%s must be %s, got %s" % (name, self.dtype, t.dtype))
+    def _arg(self, t, shape, name, dtype=None):
+        dtype = self.dtype if dtype is None else dtype
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
         if tuple(t.shape) != shape and not (self.batch == 1 and tuple(t.shape) == shape[1:]):
             raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
         if not t.is_contiguous():
@@ -218,10 +224,11 @@ class Plan:
             raise ValueError("%s is on %s, the plan on %s" % (name, t.device, self.device))
         return t.data_ptr()
 
-    def _out(self, out, ref, ref_shape, shape):
+    def _out(self, out, ref, ref_shape, shape, dtype=None):
         if out is None:
             batched = ref.dim() == len(ref_shape)
-            out = torch.empty(shape if batched else shape[1:], dtype=self.dtype, device=ref.device)
+            out = torch.empty(shape if batched else shape[1:], dtype=self.dtype if dtype is None else dtype,
+                              device=ref.device)
         return out
 
     @staticmethod
@@ -231,28 +238,28 @@ class Plan:
         return torch.cuda.current_stream().cuda_stream if t.is_cuda else 0
 
     def inverse(self, flm, out=None, stream=None):
-        out = self._out(out, flm, self.coeff_shape(), self.grid_shape())
-        ssht_inverse(self._h, self._arg(flm, self.coeff_shape(), "flm"), self._arg(out, self.grid_shape(), "f"),
-                     self._stream(stream, flm))
+        out = self._out(out, flm, self.coeff_shape(), self.grid_shape(), self.grid_dtype)
+        ssht_inverse(self._h, self._arg(flm, self.coeff_shape(), "flm"),
+                     self._arg(out, self.grid_shape(), "f", self.grid_dtype), self._stream(stream, flm))
         return out
 
     def forward(self, f, out=None, stream=None):
         out = self._out(out, f, self.grid_shape(), self.coeff_shape())
-        ssht_forward(self._h, self._arg(f, self.grid_shape(), "f"), self._arg(out, self.coeff_shape(), "flm"),
-                     self._stream(stream, f))
+        ssht_forward(self._h, self._arg(f, self.grid_shape(), "f", self.grid_dtype),
+                     self._arg(out, self.coeff_shape(), "flm"), self._stream(stream, f))
         return out
 
     def adjoint(self, g, out=None, stream=None):
         out = self._out(out, g, self.grid_shape(), self.coeff_shape())
-        ssht_adjoint(self._h, self._arg(g, self.grid_shape(), "g"), self._arg(out, self.coeff_shape(), "flm"),
-                     self._stream(stream, g))
+        ssht_adjoint(self._h, self._arg(g, self.grid_shape(), "g", self.grid_dtype),
+                     self._arg(out, self.coeff_shape(), "flm"), self._stream(stream, g))
         return out
 
     def forward_triangular(self, f, out=None, stream=None):
         """The paper's triangular forward (FP64 plans; unstable at high band-limit)."""
         out = self._out(out, f, self.grid_shape(), self.coeff_shape())
-        ssht_forward_triangular(self._h, self._arg(f, self.grid_shape(), "f"), self._arg(out, self.coeff_shape(), "flm"),
-                                self._stream(stream, f))
+        ssht_forward_triangular(self._h, self._arg(f, self.grid_shape(), "f", self.grid_dtype),
+                                self._arg(out, self.coeff_shape(), "flm"), self._stream(stream, f))
         return out
 
     def wigner_delta(self, out=None, stream=None):
