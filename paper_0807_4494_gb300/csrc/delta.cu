@@ -52,6 +52,7 @@ struct RisboParams {
   double* slab1;
   const double* sq;         // sqrt(k)
   unsigned int* counter;    // [0] barrier counter, [1] abort flag, [4 + c] degree done by CTA c (reset before launch)
+  const int4* part;         // per step l and CTA: r0, r1, o0, o1 (host-made), or null: computed here
   int* status;              // latched status bits
 };
 
@@ -207,29 +208,53 @@ __device__ __forceinline__ double recip(double k) {
   return r;
 }
 
-// Thread 0 waits until every flag of CTAs [o0, o1] has reached `degree` (acquire), one second at
-// most; all threads then learn whether to go on.
+// Step l -> l + 1 of CTA cta: owned rows q[0], q[1] of degree l + 1, and the CTAs q[2] .. q[3]
+// that produced the degree-l rows [r0 - 2, r1 + 1]: the rows staged here, and the rows whose
+// producers also read (one step earlier) the slab rows this CTA overwrites, pad slots included.
+__host__ __device__ inline void step_partition(int l, int cta, int nb, int* q) {
+  int r0, r1;
+  cta_rows(l + 1, cta, nb, &r0, &r1);
+  q[0] = r0;
+  q[1] = r1;
+  const int a = r0 - 2 > 0 ? r0 - 2 : 0, b = r1 + 1 < l ? r1 + 1 : l;
+  q[2] = row_owner(l, a, nb);
+  q[3] = row_owner(l, b, nb);
+}
+
+// Warp 0 waits until every flag of CTAs [o0, o1] has reached `degree` (acquire), one lane per
+// flag so that the polls overlap, one second at most; all threads then learn whether to go on.
 __device__ bool wait_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
                            int* status) {
   __shared__ int ok;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     int good = 1;
     const unsigned long long t0 = globaltimer_ns();
-    unsigned int spins = 0;
-    for (int o = o0; o <= o1 && good; ++o) {
-      while (ld_acquire_u32(done + o) < degree) {
+    for (int base = o0; base <= o1 && good; base += 32) {
+      const int o = base + lane;
+      unsigned int spins = 0;
+      while (true) {
+        const bool mine = o > o1 || ld_acquire_u32(done + o) >= degree;
+        if (__all_sync(0xffffffffu, mine)) break;
         if ((++spins & 63u) == 0u) {
-          if (*(volatile unsigned int*)abort_flag != 0u) { good = 0; break; }
-          if (globaltimer_ns() - t0 > 1000000000ull) {
-            atomicOr(status, kStatusBarrierTimeout);
-            atomicExch(abort_flag, 1u);
+          int stop = 0;
+          if (lane == 0) {
+            if (*(volatile unsigned int*)abort_flag != 0u) {
+              stop = 1;
+            } else if (globaltimer_ns() - t0 > 1000000000ull) {
+              atomicOr(status, kStatusBarrierTimeout);
+              atomicExch(abort_flag, 1u);
+              stop = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, stop, 0)) {
             good = 0;
             break;
           }
         }
       }
     }
-    ok = good;
+    if (lane == 0) ok = good;
   }
   __syncthreads();
   return ok != 0;
@@ -247,15 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
   auto params = [&](int l) {
     int* q = s_par[l & 1];
     const int lp = l + 1;
-    int r0, r1;
-    cta_rows(lp, cta, nb, &r0, &r1);
-    q[0] = r0;
-    q[1] = r1;
-    // Degree-l rows [r0 - 2, r1 + 1]: the rows staged here, and the rows whose producers also
-    // read (one step earlier) the slab rows this CTA overwrites, pad slots included.
-    const int a = r0 - 2 > 0 ? r0 - 2 : 0, b = r1 + 1 < l ? r1 + 1 : l;
-    q[2] = row_owner(l, a, nb);
-    q[3] = row_owner(l, b, nb);
+    if (P.part) {
+      const int4 v = __ldg(&P.part[(size_t)l * nb + cta]);
+      q[0] = v.x;
+      q[1] = v.y;
+      q[2] = v.z;
+      q[3] = v.w;
+    } else {
+      step_partition(l, cta, nb, q);
+    }
     s_sc[l & 1][0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
     s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
   };
@@ -511,18 +536,33 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaMalloc(&w.sqrt_tab, (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.barrier, (4 + (size_t)w.blocks) * sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
+  {
+    // the partition of every step, made once here (the kernel reads one int4 per step)
+    const size_t n = (size_t)(L > 1 ? L - 1 : 1) * w.blocks;
+    std::vector<int4> part(n);
+    for (int l = 0; l + 1 < L; ++l)
+      for (int c = 0; c < w.blocks; ++c) {
+        int q[4];
+        step_partition(l, c, w.blocks, q);
+        part[(size_t)l * w.blocks + c] = make_int4(q[0], q[1], q[2], q[3]);
+      }
+    if ((e = cudaMalloc(&w.part, n * sizeof(int4))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(w.part, part.data(), n * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    w.bytes_part = n * sizeof(int4);
+  }
   if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
   w.bytes = (delta_offset(L) + 2 * slab_doubles(L) + 2 * (size_t)L + 4) * sizeof(double) +
-            (4 + (size_t)w.blocks) * sizeof(unsigned int) + sizeof(int);
+            (4 + (size_t)w.blocks) * sizeof(unsigned int) + sizeof(int) + w.bytes_part;
   std::vector<double> sq(2 * (size_t)L + 4);
   for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
   return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
 void delta_free(DeltaWork& w) {
-  void* ptrs[] = {w.table, w.slab[0], w.slab[1], w.sqrt_tab, w.barrier, w.status};
+  void* ptrs[] = {w.table, w.slab[0], w.slab[1], w.sqrt_tab, w.barrier, w.status, w.part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  w.part = nullptr;
   w.table = w.slab[0] = w.slab[1] = w.sqrt_tab = nullptr;
   w.barrier = nullptr;
   w.status = nullptr;
@@ -539,6 +579,7 @@ cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   P.sq = w.sqrt_tab;
   P.counter = w.barrier;
   P.status = w.status;
+  P.part = w.part;
   long long cap = w.cap;
   void* args[] = {&P, &cap};
   return cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(w.blocks), dim3(w.threads), args, w.smem, st);
@@ -651,6 +692,7 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   P.sq = d.base + 2 * kNoAllocSlab;
   P.counter = words;
   P.status = (int*)(words + 2);
+  P.part = nullptr;  // no table: the kernel computes each step's partition
   long long cap = (long long)(smem / sizeof(double));
   void* args[] = {&P, &cap};
   if (cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(sms), dim3(kThreads), args, smem, st) != cudaSuccess)

@@ -42,6 +42,8 @@ struct DeltaWork {
   int threads = 0;
   size_t smem = 0;
   size_t bytes = 0;   // device memory held (table, slabs, tables, words)
+  int4* part = nullptr;   // per step and CTA: owned rows and the CTAs waited for
+  size_t bytes_part = 0;
   long long cap = 0;  // shared-memory doubles per CTA
 };
 
