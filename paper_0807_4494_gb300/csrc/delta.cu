@@ -498,6 +498,41 @@ __global__ void spin_column_kernel(const double* __restrict__ table, int L, int 
 
 }  // namespace
 
+// Host partition of the integer rows 0 .. l+1 of step l -> l + 1 over nb CTAs into contiguous
+// ranges cuts[c] .. cuts[c+1] that minimise the largest share.  A share costs the 32-column
+// segments of its integer rows and their half rows, plus the half row just below its first row,
+// which it computes too (the neighbour computes it as well).  Binary search on the largest share
+// with first-fit packing; CTAs left over get empty ranges at the top.
+static void optimal_cuts(int l, int nb, int* cuts) {
+  const int rows = l + 2;
+  auto seg = [](long long n) { return (n + 31) / 32; };
+  std::vector<long long> pre(rows + 1, 0);
+  for (int m = 0; m < rows; ++m) pre[m + 1] = pre[m] + (m <= l ? seg(m + 2) : 0) + seg(m + 1);
+  auto share = [&](int a, int b) { return pre[b] - pre[a] + (a > 0 ? seg(a + 1) : 0); };
+  auto pack = [&](long long T, int* out) {
+    int a = 0, c = 0;
+    while (a < rows) {
+      if (c == nb) return false;
+      int b = a + 1;
+      if (share(a, b) > T) return false;
+      while (b < rows && share(a, b + 1) <= T) ++b;
+      if (out) out[c] = a;
+      a = b;
+      ++c;
+    }
+    if (out) {
+      for (int k = c; k <= nb; ++k) out[k] = rows;
+    }
+    return true;
+  };
+  long long lo = 1, hi = share(0, rows);
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    if (pack(mid, nullptr)) hi = mid; else lo = mid + 1;
+  }
+  pack(lo, cuts);
+}
+
 cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   cudaError_t e;
   int sms = 0, per_sm = 0, smem_optin = 0;
@@ -508,12 +543,14 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   // Shared memory: what the largest single-chunk share of any degree needs (so no degree is
   // split into chunks), at most 200 KB.  Staying small leaves room on each SM for the kernels
   // that run beside the recursion on other streams.
+  const int nb = w.blocks, steps = L > 1 ? L - 1 : 0;
+  std::vector<int> cuts((size_t)(steps > 0 ? steps : 1) * (nb + 1));
+  for (int l = 0; l < steps; ++l) optimal_cuts(l, nb, &cuts[(size_t)l * (nb + 1)]);
   {
     long long need = 0;
-    for (int l = 0; l + 1 < L; ++l)
-      for (int c = 0; c < w.blocks; ++c) {
-        int r0, r1;
-        cta_rows(l + 1, c, w.blocks, &r0, &r1);
+    for (int l = 0; l < steps; ++l)
+      for (int c = 0; c < nb; ++c) {
+        const int r0 = cuts[(size_t)l * (nb + 1) + c], r1 = cuts[(size_t)l * (nb + 1) + c + 1];
         if (r0 < r1) need = std::max(need, chunk_need(l, r0, r1));
       }
     const size_t want = (((size_t)need + 16) * sizeof(double) + 1023) / 1024 * 1024;
@@ -538,13 +575,22 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
   {
     // the partition of every step, made once here (the kernel reads one int4 per step)
-    const size_t n = (size_t)(L > 1 ? L - 1 : 1) * w.blocks;
-    std::vector<int4> part(n);
-    for (int l = 0; l + 1 < L; ++l)
-      for (int c = 0; c < w.blocks; ++c) {
-        int q[4];
-        step_partition(l, c, w.blocks, q);
-        part[(size_t)l * w.blocks + c] = make_int4(q[0], q[1], q[2], q[3]);
+    const size_t n = (size_t)(steps > 0 ? steps : 1) * nb;
+    std::vector<int4> part(n, make_int4(0, 0, 0, 0));
+    // the CTA whose range of step l - 1 (which made degree l) holds `row`
+    auto owner = [&](int l, int row) {
+      if (l == 0) return 0;  // degree 0 comes from the initial barrier
+      const int* cp = &cuts[(size_t)(l - 1) * (nb + 1)];
+      int c = (int)(std::upper_bound(cp, cp + nb + 1, row) - cp) - 1;
+      return c < 0 ? 0 : (c > nb - 1 ? nb - 1 : c);
+    };
+    for (int l = 0; l < steps; ++l)
+      for (int c = 0; c < nb; ++c) {
+        const int r0 = cuts[(size_t)l * (nb + 1) + c], r1 = cuts[(size_t)l * (nb + 1) + c + 1];
+        // degree-l rows [r0 - 2, r1 + 1]: the rows staged here, and the rows whose producers also
+        // read (one step earlier) the slab rows this CTA overwrites, pad slots included
+        const int a = r0 - 2 > 0 ? r0 - 2 : 0, b = r1 + 1 < l ? r1 + 1 : l;
+        part[(size_t)l * nb + c] = r0 < r1 ? make_int4(r0, r1, owner(l, a), owner(l, b)) : make_int4(r0, r0, 0, -1);
       }
     if ((e = cudaMalloc(&w.part, n * sizeof(int4))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(w.part, part.data(), n * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
