@@ -500,14 +500,15 @@ __global__ void spin_column_kernel(const double* __restrict__ table, int L, int 
 
 // Host partition of the integer rows 0 .. l+1 of step l -> l + 1 over nb CTAs into contiguous
 // ranges cuts[c] .. cuts[c+1] that minimise the largest share.  A share costs the 32-column
-// segments of its integer rows and their half rows, plus the half row just below its first row,
-// which it computes too (the neighbour computes it as well).  Binary search on the largest share
+// segments of its integer rows and their half rows, one more per row, plus the half row just
+// below its first row, which it computes too (the neighbour computes it as well).  Binary search on the largest share
 // with first-fit packing; CTAs left over get empty ranges at the top.
 static void optimal_cuts(int l, int nb, int* cuts) {
   const int rows = l + 2;
   auto seg = [](long long n) { return (n + 31) / 32; };
   std::vector<long long> pre(rows + 1, 0);
-  for (int m = 0; m < rows; ++m) pre[m + 1] = pre[m] + (m <= l ? seg(m + 2) : 0) + seg(m + 1);
+  // (+1 per row: the fixed cost of starting a row, which counts for the many short rows)
+  for (int m = 0; m < rows; ++m) pre[m + 1] = pre[m] + (m <= l ? seg(m + 2) : 0) + seg(m + 1) + 1;
   auto share = [&](int a, int b) { return pre[b] - pre[a] + (a > 0 ? seg(a + 1) : 0); };
   auto pack = [&](long long T, int* out) {
     int a = 0, c = 0;
