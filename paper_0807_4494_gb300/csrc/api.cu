@@ -116,12 +116,19 @@ struct ssht_plan_s {
   // the group runs the recursion (recorded by delta_event), the plan only its spin column.
   bool delta_shared = false;
   cudaEvent_t delta_event = nullptr;
-  // Recorded after the last kernel of a call that reads the Delta table, U or the A tiles: the
-  // next call's recursion and packing only wait for it (not for the rest of the previous call,
-  // e.g. the inverse's torus stage), within the same capture sequence (0 = not capturing).
+  // What the next call's recursion and packing (on aux) must wait for, instead of the whole of
+  // the previous calls: ev_free after the last kernel on a caller's stream that read the Delta
+  // table or U (SIMT contractions, the triangular solve, the table copy; the tensor-core path reads
+  // them only on aux, in order), and ev_free_a[dir] after the tensor-core contraction that read the
+  // A tiles of that direction.  Each is usable only within the capture sequence it was recorded in
+  // (0 = not capturing); otherwise, or before the first record, the call forks from the caller's
+  // stream as a whole.
   cudaEvent_t ev_free = nullptr;
   bool free_valid = false;
   unsigned long long free_capture = 0;
+  cudaEvent_t ev_free_a[2] = {nullptr, nullptr};
+  bool afree_valid[2] = {false, false};
+  unsigned long long afree_capture[2] = {0, 0};
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
@@ -282,11 +289,26 @@ int mark_free(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
+// After the tensor-core contraction of one direction: the A tiles of that direction are free.
+int mark_free_a(ssht_plan_t p, int forward, cudaStream_t st) {
+  SSHT_CUDA(cudaEventRecord(p->ev_free_a[forward], st), "A-tiles-free event");
+  p->afree_valid[forward] = true;
+  p->afree_capture[forward] = capture_id(st);
+  return 0;
+}
+
 int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
-  if (p->free_valid && p->free_capture == capture_id(st)) {
-    // the previous call's readers are done once ev_free fires; its later work may still run
-    SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free, 0), "operands-free wait");
+  const unsigned long long cap = capture_id(st);
+  // the previous readers of what the aux work overwrites, if they are known
+  const bool table_ok = !p->free_valid || p->free_capture == cap;
+  const bool a_ok = !p->tc || !p->afree_valid[forward] || p->afree_capture[forward] == cap;
+  const bool any = p->free_valid || (p->tc && p->afree_valid[forward]);
+  if (table_ok && a_ok && any) {
+    // only those readers: the rest of the previous calls (e.g. the inverse's torus stage) may
+    // still be running while this call's recursion starts
+    if (p->free_valid) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free, 0), "operands-free wait");
+    if (p->tc && p->afree_valid[forward]) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free_a[forward], 0), "A-free wait");
   } else {
     SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
     SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
@@ -329,7 +351,7 @@ int project(ssht_plan_t p, const void* H, void* flm, cudaStream_t st) {
   int rc;
   if (p->tc) {
     if ((rc = tc_pack(p, 1, H, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
-    return mark_free(p, st);
+    return mark_free_a(p, 1, st);
   }
   if ((rc = join_operands(p, st))) return rc;
   {
@@ -412,7 +434,7 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   if (rc) return rc;
   if (p->tc) {
     if ((rc = tc_pack(p, 0, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)) ||
-        (rc = mark_free(p, st)))
+        (rc = mark_free_a(p, 0, st)))
       return rc;
   } else {
     if ((rc = join_operands(p, st))) return rc;
@@ -535,6 +557,8 @@ void release(ssht_plan_t p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->ev_free) cudaEventDestroy(p->ev_free);
+  for (cudaEvent_t e : p->ev_free_a)
+    if (e) cudaEventDestroy(e);
   if (p->aux) cudaStreamDestroy(p->aux);
   if (p->have_phi) cufftDestroy(p->fft_phi);
   if (p->have_theta) cufftDestroy(p->fft_theta);
@@ -574,6 +598,8 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_free, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_free_a[0], cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_free_a[1], cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     release(p);
     return fail(SSHT_ECUDA, std::string("plan stream/event setup: ") + cudaGetErrorString(ce));

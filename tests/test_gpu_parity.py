@@ -324,3 +324,30 @@ def test_back_to_back_calls_without_host_sync(precision):
         assert torch.equal(t, t_ref)
         assert torch.equal(b, b_ref)
         assert torch.equal(a, a_ref)
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x6", "fp32"])
+def test_pipelined_calls_match_synchronised_calls(precision):
+    """Calls queued back to back let the next call's recursion start before the previous call
+    has finished (it waits only for the readers of what it overwrites); the results must equal
+    those of calls separated by host synchronisation."""
+    L, s, B = 80, 2, 6
+    plan = S().Plan(L, s, B, precision=precision)
+    flm = torch.from_numpy(inputs.coeffs(L, s, B, seed=31)).to(plan.dtype).cuda()
+    f_ref = plan.inverse(flm)
+    torch.cuda.synchronize()
+    b_ref = plan.forward(f_ref)
+    torch.cuda.synchronize()
+    a_ref = plan.adjoint(f_ref)
+    torch.cuda.synchronize()
+    res = []
+    for _ in range(4):
+        f = plan.inverse(flm)
+        res.append((f, plan.forward(f), plan.adjoint(f), plan.forward(f)))
+    torch.cuda.synchronize()
+    plan.check()
+    for f, b, a, b2 in res:
+        assert torch.equal(f, f_ref)
+        assert torch.equal(b, b_ref)
+        assert torch.equal(a, a_ref)
+        assert torch.equal(b2, b_ref)
