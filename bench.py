@@ -380,7 +380,7 @@ def run_ssht(args):
             step_host()
         torch.cuda.synchronize()
         barrier(world, device)
-        nrep = max(3, args.steps // 5)
+        nrep = max(5, args.steps // 2)
         t0 = time.perf_counter()
         for _ in range(nrep):
             step_host()
