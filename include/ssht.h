@@ -182,6 +182,17 @@ SSHT_API int ssht_plan_profile(ssht_plan_t plan, int enable);
 SSHT_API int ssht_plan_profile_read(ssht_plan_t plan, double* ms, long long* count, int nstages,
                                     long long* launches);
 
+/* The stage brackets recorded since profiling was enabled or last read (a timeline; the paper
+ * has no counterpart), in recording order, at most cap of them: *n receives the number written.
+ * stage[i] is an SSHT_STAGE_* id, lane[i] 0 for the caller's stream and 1 for the plan's second
+ * stream (the recursion and the A-operand packing), t0[i] / t1[i] the bracket's start and end
+ * in milliseconds after the first bracket's start.  A bracket starts when its stream reaches it,
+ * which can precede the first kernel's start when that kernel waits for room on the GPU.  The
+ * brackets are then folded into the totals of ssht_plan_profile_read.  Synchronises the device.
+ * At most the last 8192 brackets are kept between reads. */
+SSHT_API int ssht_plan_profile_trace(ssht_plan_t plan, int* stage, int* lane, double* t0, double* t1, int cap,
+                                     int* n);
+
 /* ---------------------------------------------------------------------------------------
  * Groups: many fields of uneven band-limit and spin in one call.  This extends the paper's
  * single-field transform (which has no batching) to a heterogeneous batch.

@@ -132,6 +132,7 @@ struct ssht_plan_s {
   // profiling: events bracketing each stage, folded into per-stage totals on read
   struct Ev {
     int stage;
+    int lane;  // 0: the call's stream, 1: the plan's second stream
     cudaEvent_t a, b;
   };
   bool prof = false;
@@ -186,7 +187,7 @@ struct StageScope {
       return;
     }
     cudaEventRecord(b, st);
-    p->evs.push_back({stage, a, b});
+    p->evs.push_back({stage, st == p->aux ? 1 : 0, a, b});
     if (p->evs.size() > 8192) fold_events(p);
   }
 };
@@ -634,6 +635,10 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     }
     p->bytes += p->delta.bytes;
   }
+  if (real && (ce = real_setup()) != cudaSuccess) {
+    release(p);
+    return fail(SSHT_ECUDA, std::string("real-field kernel attributes: ") + cudaGetErrorString(ce));
+  }
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
   if ((rc = dalloc(p, (void**)&p->Uf, tri(L) * sizeof(float), "spin column (FP32)"))) return bail(rc);
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
@@ -902,6 +907,27 @@ int ssht_plan_profile_read(ssht_plan_t p, double* ms, long long* count, int nsta
     count[i] = p->prof_n[i];
   }
   if (launches) *launches = p->launches;
+  return SSHT_OK;
+}
+
+int ssht_plan_profile_trace(ssht_plan_t p, int* stage, int* lane, double* t0, double* t1, int cap, int* n) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  if (!n || cap < 0 || (cap > 0 && (!stage || !lane || !t0 || !t1))) return fail(SSHT_EINVAL, "bad trace buffers");
+  int rc = check_device(p);
+  if (rc) return rc;
+  SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
+  *n = (int)std::min(p->evs.size(), (size_t)cap);
+  for (int i = 0; i < *n; ++i) {
+    const auto& e = p->evs[i];
+    float a = 0.f, b = 0.f;
+    SSHT_CUDA(cudaEventElapsedTime(&a, p->evs[0].a, e.a), "trace event time");
+    SSHT_CUDA(cudaEventElapsedTime(&b, p->evs[0].a, e.b), "trace event time");
+    stage[i] = e.stage;
+    lane[i] = e.lane;
+    t0[i] = a;
+    t1[i] = b;
+  }
+  fold_events(p);
   return SSHT_OK;
 }
 

@@ -144,6 +144,10 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
 // Packing: data tiles (rows j = (sign, part, b), K-major over 32 l or m')
 // ---------------------------------------------------------------------------------------------
 
+// Each thread loads up to 16 complex values (one (sign, b, k) each) before converting any of
+// them, and writes both parts of each: rows j = sign * NC/2 + 2b (real) and 2b + 1 (imaginary).
+constexpr int XPER = 16;  // NC <= 256: 32 * NC / 2 complex values per tile
+
 // Inverse data tile (m, c): V_m[l, j], l = 32 c + k.
 template <bool BF>
 __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC, const int* __restrict__ xc0,
@@ -155,20 +159,28 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC
   const int nC = (L + TK - 1) / TK;
   if (c >= nC) return;
   const int as = s < 0 ? -s : s, lmin = m > as ? m : as;
-  const int part_bytes = NC * 128;
-  for (int e = threadIdx.x; e < NC * TK; e += blockDim.x) {
-    const int k = e % TK, j = e / TK;
+  const int part_bytes = NC * 128, half = NC / 2, nb = half / 2, total = TK * half;
+  float2 v[XPER];
+#pragma unroll
+  for (int q = 0; q < XPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
     const int l = c * TK + k;
-    float x = 0.f;
-    const int half = NC / 2, sign = j / half, jj = j % half, part = jj & 1, b = jj >> 1;
-    if (b < B && l < L && l >= lmin) {
-      if (!(sign && m == 0)) {
-        const float2 v = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
-        x = part ? v.y : v.x;
-        if (sign && (l & 1)) x = -x;
-      }
+    v[q] = make_float2(0.f, 0.f);
+    if (e < total && b < B && l < L && l >= lmin && !(sign && m == 0)) {
+      v[q] = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
+      if (sign && (l & 1)) v[q] = make_float2(-v[q].x, -v[q].y);
     }
-    put_split<BF>(tile, part_bytes, j, k, x);
+  }
+#pragma unroll
+  for (int q = 0; q < XPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    if (e < total) {
+      const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
+      const int j = sign * half + 2 * b;
+      put_split<BF>(tile, part_bytes, j, k, v[q].x);
+      put_split<BF>(tile, part_bytes, j + 1, k, v[q].y);
+    }
   }
   __syncthreads();
   uint4* dst = (uint4*)(X + (size_t)(xoff[m] + blockIdx.x) * 2 * part_bytes);
@@ -184,20 +196,28 @@ __global__ void __launch_bounds__(256) pack_y_kernel(int L, int B, int NC, const
   const int m = blockIdx.y, c = blockIdx.x;
   const int Lp = L - 1, NT = 2 * L - 1;
   const int nC = (L + TK - 1) / TK;
-  const int part_bytes = NC * 128;
-  for (int e = threadIdx.x; e < NC * TK; e += blockDim.x) {
-    const int k = e % TK, j = e / TK;
+  const int part_bytes = NC * 128, half = NC / 2, nb = half / 2, total = TK * half;
+  float2 v[XPER];
+#pragma unroll
+  for (int q = 0; q < XPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
     const int mp = c * TK + k;
-    float x = 0.f;
-    const int half = NC / 2, sign = j / half, jj = j % half, part = jj & 1, b = jj >> 1;
-    if (b < B && mp < L) {
-      if (!(sign && m == 0)) {
-        const float2 v = H[((size_t)b * NT + (sign ? Lp - m : Lp + m)) * L + mp];
-        x = part ? v.y : v.x;
-        if (sign && (mp & 1)) x = -x;
-      }
+    v[q] = make_float2(0.f, 0.f);
+    if (e < total && b < B && mp < L && !(sign && m == 0)) {
+      v[q] = H[((size_t)b * NT + (sign ? Lp - m : Lp + m)) * L + mp];
+      if (sign && (mp & 1)) v[q] = make_float2(-v[q].x, -v[q].y);
     }
-    put_split<BF>(tile, part_bytes, j, k, x);
+  }
+#pragma unroll
+  for (int q = 0; q < XPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    if (e < total) {
+      const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
+      const int j = sign * half + 2 * b;
+      put_split<BF>(tile, part_bytes, j, k, v[q].x);
+      put_split<BF>(tile, part_bytes, j + 1, k, v[q].y);
+    }
   }
   __syncthreads();
   uint4* dst = (uint4*)(X + ((size_t)m * nC + c) * 2 * part_bytes);
@@ -496,6 +516,13 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
     // Function attributes are process-wide upper bounds: set them for the largest column count
     // (NC = 256) so that plans of other batch sizes can launch with their own amounts.
     const int gemm_max = STAGES * (A_TILE + 2 * 256 * 128) + 1024, xsmem_max = 2 * 256 * 128;
+    if ((e = prefer_shared(tc_gemm_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, true>)) != cudaSuccess ||
+        (e = prefer_shared(tc_gemm_kernel<false, false>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, false>)) != cudaSuccess ||
+        (e = prefer_shared(pack_v_kernel<true>)) != cudaSuccess || (e = prefer_shared(pack_v_kernel<false>)) != cudaSuccess ||
+        (e = prefer_shared(pack_y_kernel<true>)) != cudaSuccess || (e = prefer_shared(pack_y_kernel<false>)) != cudaSuccess ||
+        (e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
+        (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
+      goto fail;
     if (p->bf16) {
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;

@@ -566,6 +566,7 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 std::min(smem_optin - 1024, 200 * 1024))) != cudaSuccess)
     return e;
+  if ((e = prefer_shared(risbo_kernel)) != cudaSuccess || (e = prefer_shared(spin_column_kernel)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;

@@ -127,6 +127,18 @@ cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cuda
   return cudaGetLastError();
 }
 
+cudaError_t real_setup() {
+  cudaError_t e;
+  if ((e = prefer_shared(pack_coeffs_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pack_coeffs_kernel<float>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pack_grid_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pack_grid_kernel<float>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(unpack_grid_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(unpack_grid_kernel<float>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(unpack_coeffs_kernel<double>)) != cudaSuccess) return e;
+  return prefer_shared(unpack_coeffs_kernel<float>);
+}
+
 #define SSHT_REAL_INST(T)                                                                          \
   template cudaError_t real_pack_coeffs<T>(int, int, const void*, void*, cudaStream_t);          \
   template cudaError_t real_pack_grid<T>(int, int, const void*, void*, cudaStream_t);            \

@@ -12,6 +12,15 @@
 
 namespace ssht {
 
+// Every kernel of the library asks for the largest shared-memory carveout of the SM's unified
+// L1 / shared array.  CTAs of different kernels share an SM only under one carveout, and the
+// recursion (one CTA per SM for the whole sweep) is meant to share its SMs with the kernels of
+// the other stream.
+template <class K>
+inline cudaError_t prefer_shared(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // Device status word bits (latched by kernels, read by ssht_plan_check).
 enum : int { kStatusOk = 0, kStatusBarrierTimeout = 1 };
 
@@ -79,6 +88,8 @@ template <typename T> cudaError_t real_pack_coeffs(int L, int nreal, const void*
 template <typename T> cudaError_t real_pack_grid(int L, int nreal, const void* f, void* rg, cudaStream_t st);
 template <typename T> cudaError_t real_unpack_grid(int L, int nreal, const void* rg, void* f, cudaStream_t st);
 template <typename T> cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cudaStream_t st);
+// Kernel attributes of the packing kernels (on the current device).
+cudaError_t real_setup();
 
 // ---------------------------------------------------------------------------
 // Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16, at most 64 fields per plan

@@ -466,7 +466,8 @@ void host_fft(std::vector<std::complex<double>>& a, int sign) {
 
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e != cudaSuccess ? e : prefer_shared(kernel);
 }
 
 }  // namespace

@@ -21,7 +21,7 @@ ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", 
           -5: "SSHT_EUNSUPPORTED"}
 EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspace_bytes", "ssht_inverse",
            "ssht_forward", "ssht_adjoint", "ssht_forward_triangular", "ssht_wigner_delta", "ssht_plan_check", "ssht_plan_profile",
-           "ssht_plan_profile_read", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
+           "ssht_plan_profile_read", "ssht_plan_profile_trace", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
            "ssht_last_error", "ssht_version")
@@ -63,6 +63,8 @@ def _lib():
             "ssht_plan_profile": ([vp, i], i),
             "ssht_plan_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), i,
                                         ctypes.POINTER(ctypes.c_longlong)], i),
+            "ssht_plan_profile_trace": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), i, ctypes.POINTER(i)], i),
             "ssht_wigner_delta_noalloc": ([i, vp, vp], i),
             "ssht_group_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), i, i, i], i),
             "ssht_group_destroy": ([vp], i),
@@ -154,6 +156,19 @@ def ssht_plan_profile_read(h):
     launches = ctypes.c_longlong()
     _check(_lib().ssht_plan_profile_read(h, ms, cnt, n, ctypes.byref(launches)), "ssht_plan_profile_read")
     return {name: (ms[k], cnt[k]) for k, name in enumerate(STAGES)}, launches.value
+
+
+def ssht_plan_profile_trace(h, cap=8192):
+    """Returns the stage brackets since profiling was enabled or last read, in recording order:
+    a list of (stage name, lane, start ms, end ms), lane 0 the caller's stream and 1 the plan's
+    second stream, times after the first bracket's start."""
+    stage = (ctypes.c_int * cap)()
+    lane = (ctypes.c_int * cap)()
+    t0 = (ctypes.c_double * cap)()
+    t1 = (ctypes.c_double * cap)()
+    n = ctypes.c_int()
+    _check(_lib().ssht_plan_profile_trace(h, stage, lane, t0, t1, cap, ctypes.byref(n)), "ssht_plan_profile_trace")
+    return [(STAGES[stage[k]], lane[k], t0[k], t1[k]) for k in range(n.value)]
 
 
 def ssht_plan_workspace_bytes(h):
@@ -282,6 +297,9 @@ class Plan:
 
     def profile_read(self):
         return ssht_plan_profile_read(self._h)
+
+    def profile_trace(self):
+        return ssht_plan_profile_trace(self._h)
 
 
 class InverseFunction(torch.autograd.Function):

@@ -54,4 +54,6 @@ def test_null_arguments_are_rejected():
     assert lib.ssht_forward(None, None, None, None) == -1
     assert lib.ssht_adjoint(None, None, None, None) == -1
     assert lib.ssht_plan_check(None) == -1
+    n = ctypes.c_int()
+    assert lib.ssht_plan_profile_trace(None, None, None, None, None, 0, ctypes.byref(n)) == -1
     assert lib.ssht_plan_destroy(None) == 0

@@ -351,3 +351,37 @@ def test_pipelined_calls_match_synchronised_calls(precision):
         assert torch.equal(b, b_ref)
         assert torch.equal(a, a_ref)
         assert torch.equal(b2, b_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_profile_totals_and_trace(precision):
+    """Stage timing: the trace lists every bracket once, each stream's brackets in order and
+    without overlap, the recursion (and, for the tensor-core path, the A packing) on the plan's
+    second stream; its per-stage sums equal the totals read afterwards."""
+    L, s, B = 96, 2, 4
+    plan = S().Plan(L, s, B, precision=precision)
+    flm = torch.from_numpy(inputs.coeffs(L, s, B, seed=3)).to(plan.dtype).cuda()
+    plan.inverse(flm)
+    plan.profile(True)
+    for _ in range(2):
+        f = plan.inverse(flm)
+        plan.forward(f)
+    trace = plan.profile_trace()
+    assert trace and trace[0][2] == 0.0
+    for name, lane, t0, t1 in trace:
+        assert name in S().STAGES and lane in (0, 1) and 0.0 <= t0 <= t1
+    for lane in (0, 1):
+        spans = [(t0, t1) for _, ln, t0, t1 in trace if ln == lane]
+        assert all(a[1] <= b[0] + 1e-3 for a, b in zip(spans, spans[1:]))
+    aux = {name for name, lane, _, _ in trace if lane == 1}
+    assert aux == ({"delta", "pack"} if precision == "tf32x3" else {"delta"})
+    assert sum(1 for name, _, _, _ in trace if name == "delta") == 4
+    # the trace was folded into the totals
+    totals, launches = plan.profile_read()
+    assert launches > 0
+    for name in S().STAGES:
+        spans = [t1 - t0 for n, _, t0, t1 in trace if n == name]
+        assert totals[name][1] == len(spans)
+        assert totals[name][0] == pytest.approx(sum(spans), rel=1e-3, abs=1e-3)
+    assert plan.profile_trace() == []
+    plan.check()
