@@ -171,10 +171,10 @@ def contraction_macs(L, s):
 
 
 def recursion_updates(L):
-    """Element updates of one octant Risbo sweep: half slabs (l+1)(l+4)/2 and integer slabs
-    (l+2)(l+3)/2 for l = 0 .. L-2."""
+    """Element updates of one octant Risbo sweep: (half-step, integer-step) updates, i.e. half
+    slabs (l+1)(l+4)/2 and integer slabs (l+2)(l+3)/2 summed over l = 0 .. L-2."""
     l = np.arange(0, max(L - 1, 0), dtype=np.float64)
-    return float(np.sum((l + 1) * (l + 4) / 2 + (l + 2) * (l + 3) / 2))
+    return float(np.sum((l + 1) * (l + 4) / 2)), float(np.sum((l + 2) * (l + 3) / 2))
 
 
 def source_hash(*files):
@@ -328,17 +328,19 @@ def run_ssht(args):
         ms_d, n_d = own[dom]
         per_launch_s = ms_d / n_d / 1e3
         if dom == "delta":
-            # 9 flops per octant update: 3 products and 3 fused multiply-adds, i.e. 6 FP64-pipe
-            # instructions; at full pipe this mix reaches 9/12 of the FMA-only peak.
-            flops = 9.0 * recursion_updates(L)
+            # A half-step update is 2 fused multiply-adds, a product and a fused multiply-add
+            # (7 flops, 4 FP64 instructions); an integer-step update adds the row product (8 flops,
+            # 5 instructions).  The FMA-only peak counts 2 flops per instruction.
+            nh, ni = recursion_updates(L)
+            flops = 7.0 * nh + 8.0 * ni
             ach = flops / per_launch_s / 1e12
             peak, src = pk["fp64_tflops"]
             roof = {"bound": "alu", "kernel": "risbo_kernel (FP64)", "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
-                    "fp64_pipe_frac": (6.0 * recursion_updates(L) / per_launch_s) / (peak * 1e12 / 2.0),
+                    "fp64_pipe_frac": ((4.0 * nh + 5.0 * ni) / per_launch_s) / (peak * 1e12 / 2.0),
                     "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
-                    "work_per_launch": "%.3g flops = 9 x %.3g octant updates (6 FP64 instructions each)" % (
-                        flops, recursion_updates(L))}
+                    "work_per_launch": "%.3g flops = 7 x %.3g half-step + 8 x %.3g integer-step updates "
+                                       "(4 and 5 FP64 instructions)" % (flops, nh, ni)}
         elif dom in ("inverse", "project") and prec in ("tf32x3", "bf16x6"):
             # useful flops (4 per complex x real MAC) and the issued split-product tensor flops
             flops = 4.0 * B * contraction_macs(L, s)

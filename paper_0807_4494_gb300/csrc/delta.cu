@@ -44,6 +44,7 @@ namespace {
 #define SSHT_RISBO_MARK(k)  // phase boundary: 1 waited, 2 staged, 3 half step, 4 integer step, 5 table written
 #endif
 constexpr int kThreads = SSHT_RISBO_THREADS;
+static_assert(kThreads >= 64 && kThreads % 32 == 0, "warp 0 polls and publishes while the other warps write the table");
 
 struct RisboParams {
   int L;
@@ -51,6 +52,7 @@ struct RisboParams {
   double* slab0;
   double* slab1;
   const double* sq;         // sqrt(k)
+  const double* rsq;        // 1/sqrt(k), k >= 1
   unsigned int* counter;    // [0] barrier counter, [1] abort flag, [4 + c] degree done by CTA c (reset before launch)
   const int4* part;         // per step l and CTA: r0, r1, o0, o1 (host-made), or null: computed here
   int* status;              // latched status bits
@@ -115,8 +117,9 @@ __host__ __device__ __forceinline__ long long segF(long long n) {
 }
 
 // Work of integer rows [0, m) of a step, half rows included, in 32-column segments: row k has
-// k + 2 half-integer and k + 1 integer columns.
-__host__ __device__ __forceinline__ long long row_cost(long long m) { return segF(m + 1) - 1 + segF(m); }
+// k + 3 half-integer and k + 2 integer columns (each step's update reads one column more than
+// it writes).
+__host__ __device__ __forceinline__ long long row_cost(long long m) { return segF(m + 2) - 2 + segF(m + 1) - 1; }
 
 // Row m0 of the split of rows [0, rows) with cut o of nb: the smallest m with
 // row_cost(m) >= floor(row_cost(rows) * o / nb).
@@ -222,50 +225,62 @@ __host__ __device__ inline void step_partition(int l, int cta, int nb, int* q) {
 }
 
 // Warp 0 waits until every flag of CTAs [o0, o1] has reached `degree` (acquire), one lane per
-// flag so that the polls overlap, one second at most; all threads then learn whether to go on.
+// flag so that the polls overlap, one second at most; returns (to every lane) whether to go on.
+__device__ bool poll_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
+                           int* status) {
+  const int lane = threadIdx.x & 31;
+  int good = 1;
+  const unsigned long long t0 = globaltimer_ns();
+  for (int base = o0; base <= o1 && good; base += 32) {
+    const int o = base + lane;
+    unsigned int spins = 0;
+    while (true) {
+      const bool mine = o > o1 || ld_acquire_u32(done + o) >= degree;
+      if (__all_sync(0xffffffffu, mine)) break;
+      if ((++spins & 63u) == 0u) {
+        int stop = 0;
+        if (lane == 0) {
+          if (*(volatile unsigned int*)abort_flag != 0u) {
+            stop = 1;
+          } else if (globaltimer_ns() - t0 > 1000000000ull) {
+            atomicOr(status, kStatusBarrierTimeout);
+            atomicExch(abort_flag, 1u);
+            stop = 1;
+          }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+          good = 0;
+          break;
+        }
+      }
+    }
+  }
+  return good != 0;
+}
+
+// poll_flags by warp 0, then a barrier; all threads learn whether to go on.
 __device__ bool wait_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
                            int* status) {
   __shared__ int ok;
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int good = 1;
-    const unsigned long long t0 = globaltimer_ns();
-    for (int base = o0; base <= o1 && good; base += 32) {
-      const int o = base + lane;
-      unsigned int spins = 0;
-      while (true) {
-        const bool mine = o > o1 || ld_acquire_u32(done + o) >= degree;
-        if (__all_sync(0xffffffffu, mine)) break;
-        if ((++spins & 63u) == 0u) {
-          int stop = 0;
-          if (lane == 0) {
-            if (*(volatile unsigned int*)abort_flag != 0u) {
-              stop = 1;
-            } else if (globaltimer_ns() - t0 > 1000000000ull) {
-              atomicOr(status, kStatusBarrierTimeout);
-              atomicExch(abort_flag, 1u);
-              stop = 1;
-            }
-          }
-          if (__shfl_sync(0xffffffffu, stop, 0)) {
-            good = 0;
-            break;
-          }
-        }
-      }
-    }
-    if (lane == 0) ok = good;
+    const bool good = poll_flags(done, o0, o1, degree, abort_flag, status);
+    if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
   return ok != 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long long cap) {
+// At most 72 registers a thread (one CTA of 512 threads per SM): the rest of the register file
+// stays free for the kernels that share the SMs from other streams.
+__global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
   extern __shared__ double smem[];
   // Per step l -> l + 1 (slot l & 1): owned rows r0, r1 of degree l + 1, the CTAs o0..o1 that
   // produced the degree-l rows read here, and the step scales p/(2j).
   __shared__ int s_par[2][4];
   __shared__ double s_sc[2][2];
+  // The step whose flags warp 0 already waited for at the end of the previous step (-1: none,
+  // -2: that wait gave up).
+  __shared__ int s_pre;
   const int nb = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -285,6 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
     s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
   };
   const double* __restrict__ sq = P.sq;
+  const double* __restrict__ rsq = P.rsq;
+  if (threadIdx.x == 0) s_pre = -1;
   unsigned int* done = P.counter + 4;
   if (cta == 0 && threadIdx.x < 3) {  // degree 0: row 0 = (Delta_{0,-1}, Delta_00, Delta_01) = (0, 1, 0)
     P.slab0[threadIdx.x] = threadIdx.x == 1 ? 1.0 : 0.0;
@@ -293,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
   if (!grid_barrier(P.counter, nb, P.status, [&] { params(0); })) return;
   for (int l = 0; l + 1 < P.L; ++l) {
     __syncthreads();  // params(l) visible; every thread is done with step l - 1
+    if (s_pre == -2) return;
     const int lp = l + 1;
     const int r0 = s_par[l & 1][0], r1 = s_par[l & 1][1];
     const int o0 = s_par[l & 1][2], o1 = s_par[l & 1][3];
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
       if (threadIdx.x == 0) atomicExch(done + cta, (unsigned)lp);
       continue;
     }
-    if (!wait_flags(done, o0, o1, (unsigned)l, P.counter + 1, P.status)) return;
+    if (s_pre != l && !wait_flags(done, o0, o1, (unsigned)l, P.counter + 1, P.status)) return;
     SSHT_RISBO_MARK(1);
     const double* __restrict__ Yg = (l & 1) ? P.slab1 : P.slab0;
     double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
@@ -341,49 +359,68 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
         for (int i = threadIdx.x; i < l + 4; i += blockDim.x) Ys[po32(l + 1) - ybase + i] = 0.0;
       if (c1 - 1 > l)
         for (int i = threadIdx.x; i < l + 4; i += blockDim.x) Xs[2 + po32(l + 1) - ybase + i] = 0.0;
-      // Row factors: sqrt(j+a) p/(2j), sqrt(j-a) p/(2j) of both steps.
+      // Row factors.  The step factors of half row A are ra = sqrt(j+a) p/(2j) and
+      // rb = sqrt(j-a) p/(2j) (j+a = l+A+1, j-a = l-A), of integer row m ia = sqrt(j+m) p/(2j)
+      // and ib = sqrt(j-m) p/(2j) (j = lp).  Half row A is kept divided by ra(A) (row -1 by
+      // ra(0)), so a half-step update needs kappa = rb/ra only; the integer step multiplies by
+      // alpha = ia(m) ra(m-1) and combines the half rows with kappa = ib ra(m) / (ia ra(m-1)).
       for (int A = Alo + (int)threadIdx.x; A <= Ahi; A += blockDim.x) {
-        Rh[2 * (A - Alo)] = sq[l + A + 1] * sc;  // j + a = l + A + 1
-        Rh[2 * (A - Alo) + 1] = sq[l - A] * sc;  // j - a = l - A
+        Rh[2 * (A - Alo)] = sq[l - A] * rsq[l + A + 1];                     // rb / ra
+        Rh[2 * (A - Alo) + 1] = A > 0 ? sq[l + A + 1] * rsq[l + A] : 1.0;  // ra(A) / ra(A-1)
       }
       for (int m = c0 + (int)threadIdx.x; m < c1; m += blockDim.x) {
-        Ri[2 * (m - c0)] = sq[lp + m] * sc2;
-        Ri[2 * (m - c0) + 1] = sq[lp - m] * sc2;
+        Ri[2 * (m - c0)] = sq[lp + m] * sc2 * ((m > 0 ? sq[l + m] : sq[l + 1]) * sc);
+        Ri[2 * (m - c0) + 1] = m > 0 ? (sq[lp - m] * sq[l + m + 1]) * (rsq[lp + m] * rsq[l + m]) : 1.0;
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
       SSHT_RISBO_MARK(2);
       // Half step l -> l + 1/2 (2j = 2l + 1), half rows A in [Alo, Ahi], columns B in [0, A+1]
-      // (a = A + 1/2, b = B - 1/2): j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.
+      // (a = A + 1/2, b = B - 1/2): j+a = l+A+1, j-a = l-A, j+b = l+B, j-b = l+1-B.  With
+      // P(c) = Y(A, c) + kappa Y(A+1, c) and Q(c) = kappa Y(A+1, c) - Y(A, c),
+      //   X(A, B) / ra(A) = sqrt(j+b) P(B-1) + sqrt(j-b) Q(B):
+      // lane i forms P and Q of column i - 1 and takes P of the column before from its left
+      // neighbour (lane 0 from lane 31 of the warp's previous segment).
       {
-        const SegRange w = warp_segments(Alo, Ahi, 2, warp, nwarps);
+        const SegRange w = warp_segments(Alo, Ahi, 3, warp, nwarps);
         int A = w.x, seg = w.seg;
-        int yo = po32(A) - ybase;  // row A of Ys; half row A of Xs is at 2 + yo
-        double ra = Rh[2 * (A - Alo)], rb = Rh[2 * (A - Alo) + 1];
+        int yo = po32(A) - ybase;  // row A of Ys from column -1; half row A of Xs is at 2 + yo
+        double kap = Rh[2 * (A - Alo)], rat = Rh[2 * (A - Alo) + 1];
+        double carry = 0.0;
+        if (w.count > 0 && seg > 0) {
+          const int i = seg * 32 - 1;
+          carry = fma(kap, Ys[yo + A + 3 + i], Ys[yo + i]);
+        }
         for (int k = 0; k < w.count; ++k) {
-          const int B = seg * 32 + lane;
-          if (B <= A + 1) {
-            const double* y0 = Ys + yo + B;          // Y(A, B-1), Y(A, B)
-            const double* y1 = y0 + (A + 3);         // Y(A+1, B-1), Y(A+1, B)
-            const double sb = sq[l + B], smb = sq[l + 1 - B];
-            const double t1 = fma(-smb, y0[1], sb * y0[0]);
-            const double t2 = fma(smb, y1[1], sb * y1[0]);
-            const double v = fma(ra, t1, rb * t2);
+          const int i = seg * 32 + lane;  // column i - 1
+          double P = 0.0, Q = 0.0;
+          if (i <= A + 2) {
+            const double y0 = Ys[yo + i], y1 = Ys[yo + A + 3 + i];
+            P = fma(kap, y1, y0);
+            Q = fma(kap, y1, -y0);
+          }
+          double Pm = __shfl_up_sync(0xffffffffu, P, 1);
+          const double P31 = __shfl_sync(0xffffffffu, P, 31);
+          if (lane == 0) Pm = carry;
+          carry = P31;
+          if (i >= 1 && i <= A + 2) {
+            const int B = i - 1;
+            const double v = fma(sq[l + 1 - B], Q, sq[l + B] * Pm);
             double* xr = Xs + 2 + yo;
             xr[B] = v;
             if (B == A) {
-              if (A > Alo) xr[-1] = flip(v, true);       // pad of row A-1: X(A-1, A+1) = -X(A, A)
+              if (A > Alo) xr[-1] = -v * rat;            // pad of row A-1, in its scale: X(A-1, A+1) = -X(A, A)
               else if (A == 0) Xs[1] = flip(v, true);    // X(-1/2, 1/2) = -X(1/2, -1/2)
             }
             if (A == 0 && B == 1) Xs[0] = v;             // X(-1/2, -1/2) = X(1/2, 1/2)
           }
-          if (++seg * 32 > A + 1) {
+          if (++seg * 32 > A + 2) {
             yo += A + 3;
             ++A;
             seg = 0;
             if (A <= Ahi) {
-              ra = Rh[2 * (A - Alo)];
-              rb = Rh[2 * (A - Alo) + 1];
+              kap = Rh[2 * (A - Alo)];
+              rat = Rh[2 * (A - Alo) + 1];
             }
           }
         }
@@ -392,23 +429,37 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
       __syncthreads();
       SSHT_RISBO_MARK(3);
       // Integer step l + 1/2 -> lp (2j = 2 lp), rows m in [c0, c1), columns n in [0, m]:
-      // j+m = lp+m, j-m = lp-m, j+n = lp+n, j-n = lp-n; X(m - 1/2, .) is half row m - 1.
+      // j+m = lp+m, j-m = lp-m, j+n = lp+n, j-n = lp-n; X(m - 1/2, .) is half row m - 1.  With
+      // P(c) = X'(m-1, c) + kappa X'(m, c) and Q(c) = kappa X'(m, c) - X'(m-1, c) (X' the stored,
+      // divided half rows), Delta_{mn} = alpha (sqrt(j+n) P(n) + sqrt(j-n) Q(n+1)): lane i forms P
+      // and Q of column i and writes column n = i - 1.
       {
-        const SegRange w = warp_segments(c0, c1 - 1, 1, warp, nwarps);
+        const SegRange w = warp_segments(c0, c1 - 1, 2, warp, nwarps);
         int m = w.x, seg = w.seg;
         int xo = 2 + po32(m) - ybase;  // half row m in Xs (row m - 1 starts m + 2 earlier; row -1 at 0)
         int zo = tri32(m) - z0;
         double* yr = Yn + po32(m);
-        double ia = Ri[2 * (m - c0)], ib = Ri[2 * (m - c0) + 1];
+        double al = Ri[2 * (m - c0)], kap = Ri[2 * (m - c0) + 1];
+        double carry = 0.0;
+        if (w.count > 0 && seg > 0) {
+          const int i = seg * 32 - 1;
+          carry = fma(kap, Xs[xo + i], Xs[(m > 0 ? xo - (m + 2) : 0) + i]);
+        }
         for (int k = 0; k < w.count; ++k) {
-          const int n = seg * 32 + lane;
-          if (n <= m) {
-            const double* x0 = Xs + (m > 0 ? xo - (m + 2) : 0) + n;  // X(m-1, n), X(m-1, n+1)
-            const double* x1 = Xs + xo + n;                          // X(m, n), X(m, n+1)
-            const double sb = sq[lp + n], smb = sq[lp - n];
-            const double t1 = fma(-smb, x0[1], sb * x0[0]);
-            const double t2 = fma(smb, x1[1], sb * x1[0]);
-            const double v = fma(ia, t1, ib * t2);
+          const int i = seg * 32 + lane;
+          double P = 0.0, Q = 0.0;
+          if (i <= m + 1) {
+            const double x0 = Xs[(m > 0 ? xo - (m + 2) : 0) + i], x1 = Xs[xo + i];
+            P = fma(kap, x1, x0);
+            Q = fma(kap, x1, -x0);
+          }
+          double Pm = __shfl_up_sync(0xffffffffu, P, 1);
+          const double P31 = __shfl_sync(0xffffffffu, P, 31);
+          if (lane == 0) Pm = carry;
+          carry = P31;
+          if (i >= 1 && i <= m + 1) {
+            const int n = i - 1;
+            const double v = al * fma(sq[lp - n], Q, sq[lp + n] * Pm);
             yr[n + 1] = v;
             if (n == 1) yr[0] = flip(v, ((lp + m) & 1) != 0);            // Delta_{m,-1} = (-1)^{l+m} Delta_{m,1}
             if (n + 1 == m) {
@@ -418,54 +469,69 @@ __global__ void __launch_bounds__(kThreads, 1) risbo_kernel(RisboParams P, long 
             if (n == m && m == lp) yr[m + 2] = 0.0;                       // Delta_{l,l+1} = 0
             Zs[zo + n] = v;
           }
-          if (++seg * 32 > m) {
+          if (++seg * 32 > m + 1) {
             xo += m + 3;
             zo += m + 1;
             yr += m + 3;
             ++m;
             seg = 0;
             if (m < c1) {
-              ia = Ri[2 * (m - c0)];
-              ib = Ri[2 * (m - c0) + 1];
+              al = Ri[2 * (m - c0)];
+              kap = Ri[2 * (m - c0) + 1];
             }
           }
         }
       }
       __syncthreads();
       SSHT_RISBO_MARK(4);
-      if (c1 == r1 && threadIdx.x == 0) {  // the slab rows of this CTA are complete: publish them
-        __threadfence();
-        atomicExch(done + cta, (unsigned)lp);
-      }
-      // Quadrant table from shared memory: rows T[m][n] = Delta_{mn} (n <= m) ...
-      {
-        const SegRange w = warp_segments(c0, c1 - 1, 1, warp, nwarps);
-        int m = w.x, seg = w.seg;
-        int zo = tri32(m) - z0;
-        double* trow = T + (size_t)m * (lp + 1);
-        for (int k = 0; k < w.count; ++k) {
-          const int n = seg * 32 + lane;
-          if (n <= m) trow[n] = Zs[zo + n];
-          if (++seg * 32 > m) {
-            zo += m + 1;
-            trow += lp + 1;
-            ++m;
-            seg = 0;
+      if (warp == 0) {
+        if (c1 == r1) {
+          // The slab rows of this CTA are complete: publish them, then wait for the flags of the
+          // next step while the other warps write the table.
+          if (lane == 0) {
+            __threadfence();
+            atomicExch(done + cta, (unsigned)lp);
+          }
+          __syncwarp();
+          if (l + 2 < P.L) {
+            const int* q = s_par[(l + 1) & 1];  // made by thread 32 before this step's barriers
+            if (q[0] < q[1]) {
+              const bool good = poll_flags(done, q[2], q[3], (unsigned)lp, P.counter + 1, P.status);
+              if (lane == 0) s_pre = good ? lp : -2;
+            }
           }
         }
-      }
-      // ... and T[n][m] = (-1)^{m-n} Delta_{mn} (n < m): for each table row n, the columns
-      // m in [max(c0, n+1), c1) are contiguous.
-      {
-        const int width = c1 - c0;
-        const int items = (c1 - 1) * width;  // n in [0, c1 - 1)
-        const float inv_w = 1.0f / (float)width;
-        for (int i = threadIdx.x; i < items; i += blockDim.x) {
-          int n = (int)(((float)i + 0.5f) * inv_w);
-          int j = i - n * width;
-          if (j < 0) { --n; j += width; } else if (j >= width) { ++n; j -= width; }
-          const int m = c0 + j;
-          if (m > n) T[(size_t)n * (lp + 1) + m] = flip(Zs[tri32(m) - z0 + n], ((m - n) & 1) != 0);
+      } else {
+        // Quadrant table from shared memory (warps 1 ..): rows T[m][n] = Delta_{mn} (n <= m) ...
+        {
+          const SegRange w = warp_segments(c0, c1 - 1, 1, warp - 1, nwarps - 1);
+          int m = w.x, seg = w.seg;
+          int zo = tri32(m) - z0;
+          double* trow = T + (size_t)m * (lp + 1);
+          for (int k = 0; k < w.count; ++k) {
+            const int n = seg * 32 + lane;
+            if (n <= m) trow[n] = Zs[zo + n];
+            if (++seg * 32 > m) {
+              zo += m + 1;
+              trow += lp + 1;
+              ++m;
+              seg = 0;
+            }
+          }
+        }
+        // ... and T[n][m] = (-1)^{m-n} Delta_{mn} (n < m): for each table row n, the columns
+        // m in [max(c0, n+1), c1) are contiguous.
+        {
+          const int width = c1 - c0;
+          const int items = (c1 - 1) * width;  // n in [0, c1 - 1)
+          const float inv_w = 1.0f / (float)width;
+          for (int i = (int)threadIdx.x - 32; i < items; i += (int)blockDim.x - 32) {
+            int n = (int)(((float)i + 0.5f) * inv_w);
+            int j = i - n * width;
+            if (j < 0) { --n; j += width; } else if (j >= width) { ++n; j -= width; }
+            const int m = c0 + j;
+            if (m > n) T[(size_t)n * (lp + 1) + m] = flip(Zs[tri32(m) - z0 + n], ((m - n) & 1) != 0);
+          }
         }
       }
       SSHT_RISBO_MARK(5);
@@ -508,8 +574,8 @@ static void optimal_cuts(int l, int nb, int* cuts) {
   auto seg = [](long long n) { return (n + 31) / 32; };
   std::vector<long long> pre(rows + 1, 0);
   // (+1 per row: the fixed cost of starting a row, which counts for the many short rows)
-  for (int m = 0; m < rows; ++m) pre[m + 1] = pre[m] + (m <= l ? seg(m + 2) : 0) + seg(m + 1) + 1;
-  auto share = [&](int a, int b) { return pre[b] - pre[a] + (a > 0 ? seg(a + 1) : 0); };
+  for (int m = 0; m < rows; ++m) pre[m + 1] = pre[m] + (m <= l ? seg(m + 3) : 0) + seg(m + 2) + 1;
+  auto share = [&](int a, int b) { return pre[b] - pre[a] + (a > 0 ? seg(a + 2) : 0); };
   auto pack = [&](long long T, int* out) {
     int a = 0, c = 0;
     while (a < rows) {
@@ -572,7 +638,7 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.slab[0], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.slab[1], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.sqrt_tab, (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.barrier, (4 + (size_t)w.blocks) * sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
   {
@@ -599,10 +665,13 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
     w.bytes_part = n * sizeof(int4);
   }
   if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
-  w.bytes = (delta_offset(L) + 2 * slab_doubles(L) + 2 * (size_t)L + 4) * sizeof(double) +
+  w.bytes = (delta_offset(L) + 2 * slab_doubles(L) + 2 * (2 * (size_t)L + 4)) * sizeof(double) +
             (4 + (size_t)w.blocks) * sizeof(unsigned int) + sizeof(int) + w.bytes_part;
-  std::vector<double> sq(2 * (size_t)L + 4);
-  for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
+  // sqrt(k), then 1/sqrt(k) (entry 0 unused), k < 2L + 4
+  const size_t nsq = 2 * (size_t)L + 4;
+  std::vector<double> sq(2 * nsq, 0.0);
+  for (size_t k = 0; k < nsq; ++k) sq[k] = std::sqrt((double)k);
+  for (size_t k = 1; k < nsq; ++k) sq[nsq + k] = 1.0 / std::sqrt((double)k);
   return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
@@ -625,6 +694,7 @@ cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   P.slab0 = w.slab[0];
   P.slab1 = w.slab[1];
   P.sq = w.sqrt_tab;
+  P.rsq = w.sqrt_tab + (2 * (size_t)L + 4);
   P.counter = w.barrier;
   P.status = w.status;
   P.part = w.part;
@@ -649,7 +719,7 @@ cudaError_t delta_spin_column(const double* table, int L, int s, double* U, floa
 // memory for its own pool before loading this library, or the caller may run in a latency-
 // critical loop where an allocation (and the device-wide synchronisation cudaMalloc/cudaFree
 // can cause) is not acceptable.  For them the recursion's scratch -- the two octant slabs, the
-// square-root table, the grid-barrier words and the status word -- lives in the file-scope
+// square-root tables, the grid-barrier words and the status word -- lives in the file-scope
 // array below, sized for band-limits up to kNoAllocMaxL.  Every GPU that loads this library
 // holds the array (about 2.1 MB) until the process exits.
 // ---------------------------------------------------------------------------------------------
@@ -657,20 +727,27 @@ namespace ssht {
 namespace {
 
 constexpr int kNoAllocMaxL = 512;
-// doubles: two padded octant slabs and the sqrt table (2L + 4 entries), then the
+// doubles: two padded octant slabs, the sqrt table and the reciprocal sqrt table (2L + 4
+// entries each), then the
 // synchronisation words: barrier counter, abort flag, status, one spare, and one degree flag
 // per CTA (at most kNoAllocMaxCtas CTAs, one per SM).
 constexpr size_t kNoAllocSlab = slab_doubles(kNoAllocMaxL);
 constexpr size_t kNoAllocSqrt = 2 * (size_t)kNoAllocMaxL + 4;
 constexpr int kNoAllocMaxCtas = 1024;
 constexpr size_t kNoAllocWordDoubles = (4 + kNoAllocMaxCtas) / 2;
-constexpr size_t kNoAllocDoubles = 2 * kNoAllocSlab + kNoAllocSqrt + kNoAllocWordDoubles;
+constexpr size_t kNoAllocDoubles = 2 * kNoAllocSlab + 2 * kNoAllocSqrt + kNoAllocWordDoubles;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
+// sq[k] = sqrt(k) and sq[n + k] = 1/sqrt(k) (0 for k = 0), k < n: the values the host tables
+// of delta_setup hold (both are correctly rounded operations).
 __global__ void noalloc_sqrt_kernel(double* sq, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) sq[k] = sqrt((double)k);
+  if (k < n) {
+    const double r = sqrt((double)k);
+    sq[k] = r;
+    sq[n + k] = k > 0 ? 1.0 / r : 0.0;
+  }
 }
 
 // Marks an incomplete table: a barrier timeout leaves NaN in out[0] (normally Delta^0_00 = 1).
@@ -729,7 +806,7 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
   if (sms > kNoAllocMaxCtas)
     return set_last_error(SSHT_EUNSUPPORTED, "ssht_wigner_delta_noalloc: more SMs than its fixed scratch has flags for");
-  unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + kNoAllocSqrt);  // counter, abort, status, -, flags
+  unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + 2 * kNoAllocSqrt);  // counter, abort, status, -, flags
   // The array keeps the previous call's contents: the synchronisation words start at zero.
   if (cudaMemsetAsync(words, 0, (4 + (size_t)sms) * sizeof(unsigned int), st) != cudaSuccess) return SSHT_ECUDA;
   RisboParams P;
@@ -738,6 +815,7 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   P.slab0 = d.base;
   P.slab1 = d.base + kNoAllocSlab;
   P.sq = d.base + 2 * kNoAllocSlab;
+  P.rsq = P.sq + kNoAllocSqrt;
   P.counter = words;
   P.status = (int*)(words + 2);
   P.part = nullptr;  // no table: the kernel computes each step's partition
