@@ -152,6 +152,10 @@ __device__ __forceinline__ double flip(double v, bool neg) {
   return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
 }
 
+// Shared-memory bytes of the copy of the sqrt table (2L + 4 entries) that follows a CTA's chunk
+// area, rounded to 16.
+__host__ __device__ constexpr size_t sq_smem_bytes(long long L) { return ((2 * L + 4) * 8 + 15) / 16 * 16; }
+
 // Doubles of one padded octant slab for band-limit L (rows 0 .. L, with slack).
 __host__ __device__ constexpr size_t slab_doubles(long long L) { return (size_t)((L + 2) * (L + 7) / 2 + 2); }
 
@@ -299,7 +303,11 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
     s_sc[l & 1][0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
     s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
   };
-  const double* __restrict__ sq = P.sq;
+  // sqrt(k) from shared memory (the column factors of every update): copied after the chunk
+  // area, published by the grid barrier's first __syncthreads.
+  double* sq_s = smem + cap;
+  for (int k = threadIdx.x; k < 2 * P.L + 4; k += blockDim.x) sq_s[k] = P.sq[k];
+  const double* __restrict__ sq = sq_s;
   const double* __restrict__ rsq = P.rsq;
   if (threadIdx.x == 0) s_pre = -1;
   unsigned int* done = P.counter + 4;
@@ -621,9 +629,11 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
         if (r0 < r1) need = std::max(need, chunk_need(l, r0, r1));
       }
     const size_t want = (((size_t)need + 16) * sizeof(double) + 1023) / 1024 * 1024;
-    w.smem = std::min(want, (size_t)std::min(smem_optin - 1024, 200 * 1024));
+    const size_t limit = (size_t)std::min(smem_optin - 1024, 200 * 1024) - sq_smem_bytes(L);
+    const size_t chunk = std::min(want, limit);
+    w.cap = (long long)(chunk / sizeof(double));
+    w.smem = chunk + sq_smem_bytes(L);  // the chunk area, then the sqrt table
   }
-  w.cap = (long long)(w.smem / sizeof(double));
   // Every chunk holds at least one row: the widest single-row chunk (last degree) must fit.
   for (int m = 0; m < L; ++m)
     if (chunk_need(L - 2 > 0 ? L - 2 : 0, m, m + 1) > w.cap) return cudaErrorInvalidValue;
@@ -819,7 +829,7 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   P.counter = words;
   P.status = (int*)(words + 2);
   P.part = nullptr;  // no table: the kernel computes each step's partition
-  long long cap = (long long)(smem / sizeof(double));
+  long long cap = (long long)((smem - sq_smem_bytes(L)) / sizeof(double));  // the chunk area, then the sqrt table
   void* args[] = {&P, &cap};
   if (cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(sms), dim3(kThreads), args, smem, st) != cudaSuccess)
     return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: recursion launch failed");
