@@ -152,9 +152,9 @@ __device__ __forceinline__ double flip(double v, bool neg) {
   return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
 }
 
-// Shared-memory bytes of the copy of the sqrt table (2L + 4 entries) that follows a CTA's chunk
-// area, rounded to 16.
-__host__ __device__ constexpr size_t sq_smem_bytes(long long L) { return ((2 * L + 4) * 8 + 15) / 16 * 16; }
+// Shared-memory bytes of the copies of the sqrt and reciprocal sqrt tables (2L + 4 entries each)
+// that follow a CTA's chunk area, rounded to 16.
+__host__ __device__ constexpr size_t sq_smem_bytes(long long L) { return (2 * (2 * L + 4) * 8 + 15) / 16 * 16; }
 
 // Doubles of one padded octant slab for band-limit L (rows 0 .. L, with slack).
 __host__ __device__ constexpr size_t slab_doubles(long long L) { return (size_t)((L + 2) * (L + 7) / 2 + 2); }
@@ -303,12 +303,15 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
     s_sc[l & 1][0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
     s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
   };
-  // sqrt(k) from shared memory (the column factors of every update): copied after the chunk
-  // area, published by the grid barrier's first __syncthreads.
+  // sqrt(k) and 1/sqrt(k) from shared memory (the column and row factors): copied after the
+  // chunk area, published by the grid barrier's first __syncthreads.
   double* sq_s = smem + cap;
-  for (int k = threadIdx.x; k < 2 * P.L + 4; k += blockDim.x) sq_s[k] = P.sq[k];
+  for (int k = threadIdx.x; k < 2 * P.L + 4; k += blockDim.x) {
+    sq_s[k] = P.sq[k];
+    sq_s[2 * P.L + 4 + k] = P.rsq[k];
+  }
   const double* __restrict__ sq = sq_s;
-  const double* __restrict__ rsq = P.rsq;
+  const double* __restrict__ rsq = sq_s + 2 * P.L + 4;
   if (threadIdx.x == 0) s_pre = -1;
   unsigned int* done = P.counter + 4;
   if (cta == 0 && threadIdx.x < 3) {  // degree 0: row 0 = (Delta_{0,-1}, Delta_00, Delta_01) = (0, 1, 0)
