@@ -29,7 +29,8 @@
 // segments in tensor memory, warps 2-9 (two per 32-lane quarter of tensor memory, one for each
 // sign of m) read the accumulator with tcgen05.ld, apply the phases and write the outputs (the
 // inverse writes half rows m' >= 0 of F; the torus passes apply the extension).  Work items (m, row block)
-// are sorted by decreasing length and dealt round-robin to the CTAs.  Every wait is bounded; a
+// are sorted (inverse: by groups of m; forward: by decreasing length) and dealt round-robin to
+// the CTAs.  Every wait is bounded; a
 // timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
 #include "ssht_internal.h"
 #include "tc_common.cuh"
@@ -486,8 +487,18 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
       }
     }
   }
+  // Inverse: the row blocks of each group of 4 consecutive m run together, so that their data
+  // tiles are read from HBM about once (ncu, L = 1024, B = 64: 7.1 -> 5.8 GB read, 1.19 -> 1.06
+  // ms), dealt round-robin to one CTA fewer than the SMs so that every CTA gets every item length.
+  // Forward: longest first; there the blocks of neighbouring m run together, which lets L2 merge
+  // their scattered output writes (grouping by m raised its writes from 1.0 to 1.6 GB).
+  auto grouped = [](const Item& x, const Item& y) {
+    if (x.m / 4 != y.m / 4) return x.m / 4 < y.m / 4;
+    if (x.i != y.i) return x.i > y.i;
+    return x.m < y.m;
+  };
   auto longest_first = [](const Item& x, const Item& y) { return (x.c1 - x.c0) > (y.c1 - y.c0); };
-  std::stable_sort(inv.begin(), inv.end(), longest_first);
+  std::stable_sort(inv.begin(), inv.end(), grouped);
   std::stable_sort(fwd.begin(), fwd.end(), longest_first);
   p->n_inv = (int)inv.size();
   p->n_fwd = (int)fwd.size();
@@ -597,7 +608,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.ph = (const float2*)ph;
   a.out = (float2*)out;
   a.status = status;
-  const int grid = std::min(p->grid, std::max(a.nitems, 1));
+  const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
   if (forward && p->bf16)
     tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
   else if (forward)
