@@ -186,13 +186,17 @@ struct TorusTables {
   const float2* tw;     // per-pass twiddle tables (Plan16<M>::TW entries)
   const float2* what;   // spectrum of the even sin(theta) weight w_e (zero-padded, length M), / M
   const float2* ph;     // e^{i pi k/N}, |k| < N, at k + N - 1
+  const float2* chirp_ph;  // chirp[k] e^{-i pi m/N}, m = k (k < L) or k - N: the forward DFT's
+                           // output chirp with the phase of eqn dft_spatial, one rounding
 };
 
 // Bluestein DFT of one row: out_k = sum_n in_n e^{SIGN 2 pi i n k/N}.  in through src(n) (n < N),
-// out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.
-template <int M, int SIGN, class Src, class Sink>
+// out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.  PHASE (forward DFTs
+// only): out_k also carries e^{-i pi m/N}, m = k or k - N.
+template <int M, int SIGN, bool PHASE = false, class Src, class Sink>
 __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw, const TorusTables& tb, int N, Src src,
                                           Sink sink) {
+  static_assert(!PHASE || SIGN < 0, "the combined output table is the forward chirp's");
   const float2* khat = SIGN < 0 ? tb.khat_f : tb.khat_i;
   auto in = [&](int n) {
     if (n >= N) return make_float2(0.f, 0.f);
@@ -205,7 +209,7 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
   auto back = [&](int n) { return buf[pidx(n)]; };
   auto out = [&](int k, float2 v) {
     if (k < N) {
-      float2 c = __ldg(&tb.chirp[k]);
+      float2 c = __ldg(PHASE ? &tb.chirp_ph[k] : &tb.chirp[k]);
       if (SIGN > 0) c = conjf2(c);
       sink(k, cmul(v, c));
     }
@@ -312,9 +316,9 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
       auto sink = [&](int k, float2 v) {
         if (!active) return;
         const int m = k <= Lp ? k : k - N;
-        Xb[(size_t)(m + Lp) * L + t] = cscale(cmul(v, tb.ph[-m + N - 1]), scale);  // e^{-i pi m/N}
+        Xb[(size_t)(m + Lp) * L + t] = cscale(v, scale);  // e^{-i pi m/N} in the output chirp
       };
-      bluestein<M, SIGN>(buf, tid, tw, tb, N, src, sink);
+      bluestein<M, SIGN, true>(buf, tid, tw, tb, N, src, sink);
     }
     __syncthreads();
   }
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
       if (k < N) {
         const int mpp = k <= Lp ? k : k - N;
         pos = mpp >= 0 ? mpp : mpp + M;
-        val = cscale(cmul(v, tb.ph[-mpp + N - 1]), invN);
+        val = cscale(v, invN);  // e^{-i pi m''/N} in the output chirp
       } else {
         pos = k - N + L;
         val = make_float2(0.f, 0.f);
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
       auto mid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&tb.khat_f[k])); };
       fft<M, -1>(buf, tid, tw, in, mid);
       auto back = [&](int n) { return buf[pidx(n)]; };
-      auto out = [&](int k, float2 v) { to_conv(k, k < N ? cmul(v, __ldg(&tb.chirp[k])) : v); };
+      auto out = [&](int k, float2 v) { to_conv(k, k < N ? cmul(v, __ldg(&tb.chirp_ph[k])) : v); };
       fft<M, 1>(buf, tid, tw, back, out);
     }
     // circular convolution with the even weight: y = IFFT(FFT(x) * what), what = FFT(w_e)/M
@@ -425,11 +429,8 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
     const float2* x = X + (size_t)(active ? u : 0) * L;
     const int m = active ? (int)(u % N) - Lp : 0;
     auto src = [&](int n) { return (active && n < L) ? x[n] : make_float2(0.f, 0.f); };
-    auto sink = [&](int k, float2 v) {
-      const int mpp = k <= Lp ? k : k - N;
-      buf[pidx(k)] = cmul(v, tb.ph[-mpp + N - 1]);  // H'_{m''} at bin k
-    };
-    bluestein<M, -1>(buf, tid, tw, tb, N, src, sink);
+    auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };  // H'_{m''} at bin k (phase in the chirp)
+    bluestein<M, -1, true>(buf, tid, tw, tb, N, src, sink);
     __syncthreads();
     if (active) {
       const float sig = ((m + s) & 1) ? -1.f : 1.f;
@@ -497,15 +498,20 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
   const int NP = P16 + (REST > 1 ? 1 : 0);
   int TW = 0;
   for (int i = 1, ns = 16; i < NP; ++i, ns *= 16) TW += ((i < P16 ? 16 : REST) - 1) * ns;
-  std::vector<float2> host((size_t)N + 3 * (size_t)M + (size_t)TW);
+  std::vector<float2> host((size_t)N + 3 * (size_t)M + (size_t)TW + (size_t)N);
   float2* chirp = host.data();
   float2* kf = chirp + N;
   float2* ki = kf + M;
   float2* wh = ki + M;
   float2* tw = wh + M;
+  float2* cph = tw + TW;
   for (int n = 0; n < N; ++n) {
     const long long r = ((long long)n * n) % (2LL * N);
     chirp[n] = make_float2((float)std::cos(-pi * r / N), (float)std::sin(-pi * r / N));
+    // e^{-i pi n^2/N} e^{-i pi m/N} = e^{-i pi (n^2 + m)/N}, m = n or n - N, the angle reduced exactly
+    const long long m = n <= L - 1 ? n : n - N;
+    const long long rp = (((long long)n * n + m) % (2LL * N) + 2LL * N) % (2LL * N);
+    cph[n] = make_float2((float)std::cos(-pi * rp / N), (float)std::sin(-pi * rp / N));
   }
   {
     float2* t = tw;
@@ -553,6 +559,7 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
   p->tb.what = p->buf + N + 2 * M;
   p->tb.tw = p->buf + N + 3 * M;
   p->tb.ph = (const float2*)ph;
+  p->tb.chirp_ph = p->buf + N + 3 * M + TW;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   p->grid = sms * 8;
