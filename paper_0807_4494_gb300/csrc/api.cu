@@ -642,8 +642,8 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if ((rc = dalloc(p, (void**)&p->U, tri(L) * sizeof(double), "spin column"))) return bail(rc);
   if ((rc = dalloc(p, (void**)&p->Uf, tri(L) * sizeof(float), "spin column (FP32)"))) return bail(rc);
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
-  // rows of N x L only.
-  const size_t torus = (size_t)B * d.N * (p->f64 ? d.N : d.L) * p->elem;
+  // rows of N x L only, plus one row a field for the column pairs of the phi pass's output.
+  const size_t torus = (size_t)B * (p->f64 ? (size_t)d.N * d.N : (size_t)(d.N + 1) * d.L) * p->elem;
   if (real) {
     if ((rc = dalloc(p, &p->rc, p->pair_coeff_bytes(), "real-field pair coefficients"))) return bail(rc);
     if ((rc = dalloc(p, &p->rg, p->pair_grid_bytes(), "real-field pair samples"))) return bail(rc);

@@ -113,7 +113,8 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
 // Fused torus passes of FP32 plans (torus_pass.cu)
 // ---------------------------------------------------------------------------
 // Odd-length DFTs along theta and phi (Bluestein in shared memory) with the extension, phases, sin(theta) weight convolution and transpositions folded in.  Layouts (float2):
-// F half rows [B][N][L] (m + Lp, m' >= 0), h [B][L][N], f [B][L][N], X [B][N][L], H [B][N][L].
+// F half rows [B][N][L] (m + Lp, m' >= 0), h [B][L][N], f [B][L][N], X [B][(N+1)/2][L][2] (columns
+// m + Lp = 2p + j by pairs), H [B][N][L].
 struct TorusPlan;
 cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device);
 void torus_destroy(TorusPlan* p);

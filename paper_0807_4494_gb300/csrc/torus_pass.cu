@@ -21,7 +21,10 @@
 //   inverse_theta:  F[b][m][m'] (m' in [0,L), eqn fourier_coeff) -> h[b][t][m mod N] (t < L),
 //                   i.e. theta synthesis with the extension eqn Ffourier_sym and both phases of
 //                   eqn idft_spatial; one pair of columns per row group.
-//   rows (phi):     h[b][t][:] -> f[b][t][:] (inverse), f[b][t][:] -> X[b][m][t] (forward/adjoint).
+//   rows (phi):     h[b][t][:] -> f[b][t][:] (inverse), f[b][t][:] -> X (forward/adjoint), stored
+//                   by pairs of columns: X[b][p][t][j], column m + Lp = 2p + j (N + 1 rows a field,
+//                   the last pair half used), so that a store carries two columns of one ring and
+//                   the theta passes read a pair with one 16-byte load.
 //   forward_theta:  X[b][m][t] -> H[b][m][m'] (m' in [0,L)): per-m parity extension, theta DFT,
 //                   then the sin(theta) weight convolution as a zero-padded circular convolution
 //                   of length M in the same shared-memory buffer, and the fold of m' < 0.
@@ -312,11 +315,11 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
       bluestein<M, SIGN>(buf, tid, tw, tb, N, src, sink);
     } else {
       const int b = active ? (int)(u / L) : 0, t = active ? (int)(u % L) : 0;
-      float2* Xb = out + (size_t)b * N * L;
+      float2* Xb = out + (size_t)b * (N + 1) * L + 2 * t;
       auto sink = [&](int k, float2 v) {
         if (!active) return;
-        const int m = k <= Lp ? k : k - N;
-        Xb[(size_t)(m + Lp) * L + t] = cscale(v, scale);  // e^{-i pi m/N} in the output chirp
+        const int mr = (k <= Lp ? k : k - N) + Lp;  // column m + Lp
+        Xb[(size_t)(mr >> 1) * 2 * L + (mr & 1)] = cscale(v, scale);  // e^{-i pi m/N} in the output chirp
       };
       bluestein<M, SIGN, true>(buf, tid, tw, tb, N, src, sink);
     }
@@ -344,14 +347,14 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
     const bool two = p < Lp;
     const bool odd0 = ((m + s) & 1) != 0;
     const float sig = odd0 ? -1.f : 1.f;
-    const float2* X0 = X + ((size_t)b * N + (m + Lp)) * L;
-    const float2* X1 = X0 + L;
+    const float4* Xp = (const float4*)(X + ((size_t)b * (N + 1) + 2 * p) * L);  // pair p: columns m, m + 1
     // extended samples of both columns on theta in [0, 2 pi): the odd one vanishes at theta = pi
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
       const int t = n < L ? n : N - 1 - n;
-      float2 a = X0[t];
-      float2 c = two ? X1[t] : make_float2(0.f, 0.f);
+      const float4 ac = Xp[t];
+      float2 a = make_float2(ac.x, ac.y);
+      float2 c = two ? make_float2(ac.z, ac.w) : make_float2(0.f, 0.f);
       if (t == Lp) {
         if (odd0) a = make_float2(0.f, 0.f);
         else c = make_float2(0.f, 0.f);
@@ -426,9 +429,10 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
   for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += (long long)gridDim.x * Geo<M>::G) {
     const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < nrows;
-    const float2* x = X + (size_t)(active ? u : 0) * L;
-    const int m = active ? (int)(u % N) - Lp : 0;
-    auto src = [&](int n) { return (active && n < L) ? x[n] : make_float2(0.f, 0.f); };
+    const int mr = active ? (int)(u % N) : 0;  // column m + Lp of field u / N
+    const int m = mr - Lp;
+    const float2* x = X + ((size_t)(active ? u / N : 0) * (N + 1) + (mr & ~1)) * L + (mr & 1);
+    auto src = [&](int n) { return (active && n < L) ? x[2 * n] : make_float2(0.f, 0.f); };
     auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };  // H'_{m''} at bin k (phase in the chirp)
     bluestein<M, -1, true>(buf, tid, tw, tb, N, src, sink);
     __syncthreads();
