@@ -480,7 +480,19 @@ int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
   int rc = begin_operands(p, 1, st);
   if (rc) return rc;
   if (p->torus) {
-    if ((rc = run_torus(p, 2, f, p->W2, st)) || (rc = run_torus(p, 4, p->W2, p->W1, st))) return rc;
+    if ((rc = run_torus(p, 2, f, p->W2, st))) return rc;
+    if (p->tc) {
+      // the theta pass writes the projection's data tiles itself (no H, no data packing)
+      const TileOut tiles = tc_forward_tiles(p->tc);
+      {
+        StageScope sc(p, SSHT_STAGE_FFT, st);
+        SSHT_CUDA(torus_pass(p->torus, 4, p->s, p->B, p->W2, nullptr, st, &tiles), "torus pass");
+        p->launches += 1;
+      }
+      if ((rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
+      return mark_free_a(p, 1, st);
+    }
+    if ((rc = run_torus(p, 4, p->W2, p->W1, st))) return rc;
     return project<T>(p, p->W1, flm, st);
   }
   rc = analysis_front<T>(p, f, 0, st);

@@ -593,6 +593,15 @@ cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t s
   return cudaGetLastError();
 }
 
+TileOut tc_forward_tiles(const TcPlan* p) {
+  TileOut o;
+  o.X = p->X;
+  o.NC = p->NC;
+  o.nC = p->nC;
+  o.mode = p->bf16 ? 2 : 1;
+  return o;
+}
+
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches) {
   TcArgs a;
   a.L = p->L;

@@ -108,6 +108,14 @@ cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t s
 // The contraction: forward = 0 writes the half rows F (float2 [B][N][L], m' >= 0) of the inverse;
 // forward = 1 writes flm (float2 [B][L*L]).  Timeouts set bit 2 of *status.
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);
+// Where the forward theta pass writes the projection's data tiles directly (in place of H and
+// tc_pack_data): the tile array, its column count NC, chunks per m nC, and the split form
+// (mode 1: 3xTF32, 2: split-BF16; 0: no tiles, H is written).
+struct TileOut {
+  uint8_t* X = nullptr;
+  int NC = 0, nC = 0, mode = 0;
+};
+TileOut tc_forward_tiles(const TcPlan* p);
 
 // ---------------------------------------------------------------------------
 // Fused torus passes of FP32 plans (torus_pass.cu)
@@ -121,7 +129,9 @@ void torus_destroy(TorusPlan* p);
 size_t torus_bytes(const TorusPlan* p);
 // which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
 // 3 adjoint phi (f -> X), 4 forward theta with the weight convolution (X -> H), 5 adjoint theta (X -> H).
-cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st);
+// which = 4 with tiles (mode != 0): the data tiles of the forward projection instead of H.
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st,
+                       const TileOut* tiles = nullptr);
 
 // ---------------------------------------------------------------------------
 // Torus kernels (torus.cu)

@@ -30,6 +30,7 @@
 //                   of length M in the same shared-memory buffer, and the fold of m' < 0.
 //   adjoint_theta:  X[b][m][t] -> H[b][m][m']: theta DFT of the unextended rings, fold of m' < 0.
 #include "ssht_internal.h"
+#include "tc_common.cuh"
 
 #include <cmath>
 #include <complex>
@@ -327,12 +328,40 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
   }
 }
 
+// Element (b, m, m') of the forward projection's data tiles (the layout of the tensor-core
+// contraction: tile (|m|, m' / 32) of 128-byte swizzled rows j = (m < 0) NC/2 + 2b + part, K = m'
+// mod 32, the negative-m half carrying (-1)^{m'}): both parts of v, split.  The m = 0 tile's
+// negative half and the padding rows b >= B are written as zeros by the passes of m = 0 and of
+// the last field.
+__device__ __forceinline__ void put_tile(const TileOut& to, int b, int B, int mm, int mp, float2 v) {
+  const int am = mm < 0 ? -mm : mm, sign = mm < 0 ? 1 : 0;
+  const int pb = to.NC * 128, half = to.NC / 2, k = mp & 31;
+  uint8_t* tile = to.X + ((size_t)am * to.nC + (mp >> 5)) * 2 * pb;
+  if (sign && (mp & 1)) v = make_float2(-v.x, -v.y);
+  auto put = [&](int row, float x) {
+    if (to.mode == 2) tc::put_split<true>(tile, pb, row, k, x);
+    else tc::put_split<false>(tile, pb, row, k, x);
+  };
+  put(sign * half + 2 * b, v.x);
+  put(sign * half + 2 * b + 1, v.y);
+  if (am == 0) {
+    put(half + 2 * b, 0.f);
+    put(half + 2 * b + 1, 0.f);
+  }
+  if (b == B - 1)
+    for (int r = 2 * B; r < half; ++r) {
+      put(sign * half + r, 0.f);
+      if (am == 0) put(half + r, 0.f);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
-// forward theta analysis with the sin(theta) weight: X[b][m][t] -> H[b][m][m'], pairs of columns
+// forward theta analysis with the sin(theta) weight: X (pairs of columns) -> H[b][m][m'], or the
+// projection's data tiles when to.mode != 0
 // ---------------------------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
-                                                                       float2* __restrict__ H, TorusTables tb) {
+                                                                       float2* __restrict__ H, TorusTables tb, TileOut to) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -396,18 +425,29 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
     fft<M, 1>(buf, tid, tw, cin, cout);
     if (active) {
       // y[m'] = H'_m[m'] + H'_{m+1}[m'], y[-m'] = sig (H'_m[m'] - H'_{m+1}[m']); fold m' < 0:
-      // H = (2 - delta_{m'0}) 2 pi H'
-      float2* H0 = H + ((size_t)b * N + (m + Lp)) * L;
+      // H = (2 - delta_{m'0}) 2 pi H'.  Tiles: the last chunk's columns m' >= L are zeros.
+      float2* H0 = to.mode ? nullptr : H + ((size_t)b * N + (m + Lp)) * L;
       float2* H1 = H0 + L;
       const float c2 = 6.28318530717958648f, c4 = 12.5663706143591730f;
-      for (int mp = tid; mp < L; mp += Geo<M>::T) {
-        const float2 yp = buf[pidx(mp)], ym = buf[pidx((M - mp) & (M - 1))];
-        const float c = mp == 0 ? c2 : c4;
-        if (two) {
-          H0[mp] = cscale(cadd(yp, cscale(ym, sig)), 0.5f * c);
-          H1[mp] = cscale(csub(yp, cscale(ym, sig)), 0.5f * c);
+      const int end = to.mode ? to.nC * 32 : L;
+      for (int mp = tid; mp < end; mp += Geo<M>::T) {
+        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+        if (mp < L) {
+          const float2 yp = buf[pidx(mp)], ym = buf[pidx((M - mp) & (M - 1))];
+          const float c = mp == 0 ? c2 : c4;
+          if (two) {
+            v0 = cscale(cadd(yp, cscale(ym, sig)), 0.5f * c);
+            v1 = cscale(csub(yp, cscale(ym, sig)), 0.5f * c);
+          } else {
+            v0 = cscale(yp, c);
+          }
+        }
+        if (to.mode) {
+          put_tile(to, b, B, m, mp, v0);
+          if (two) put_tile(to, b, B, m + 1, mp, v1);
         } else {
-          H0[mp] = cscale(yp, c);
+          H0[mp] = v0;
+          if (two) H1[mp] = v1;
         }
       }
     }
@@ -600,8 +640,10 @@ size_t torus_bytes(const TorusPlan* p) { return p ? p->bytes : 0; }
 
 // which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
 // 3 adjoint phi (f -> X, no scale), 4 forward theta (X -> H), 5 adjoint theta (X -> H).
-cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st) {
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st,
+                       const TileOut* tiles) {
   const int L = p->L, M = p->M;
+  const TileOut to = (which == 4 && tiles) ? *tiles : TileOut();
   const long long rows = (which == 1 || which == 2 || which == 3) ? (long long)B * L
                          : (which == 5)                            ? (long long)B * p->N
                                                                    : (long long)B * L;  // pairs
@@ -617,7 +659,7 @@ cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* 
       case 1: phi_kernel<MM, 1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;               \
       case 2: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f / (float)p->N, I, O, p->tb); break; \
       case 3: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;              \
-      case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
+      case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to); break;      \
       case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
       default: return cudaErrorInvalidValue;                                                                 \
     }                                                                                                        \
