@@ -330,10 +330,10 @@ int join_operands(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
-int tc_pack(ssht_plan_t p, int forward, const void* src, cudaStream_t st) {
+int tc_pack(ssht_plan_t p, const void* src, cudaStream_t st) {
   int n = 0;
   StageScope sc(p, SSHT_STAGE_PACK, st);
-  SSHT_CUDA(tc_pack_data(p->tc, forward, src, st, &n), "tensor-core data packing");
+  SSHT_CUDA(tc_pack_data(p->tc, src, st, &n), "tensor-core data packing");
   p->launches += n;
   return 0;
 }
@@ -346,14 +346,25 @@ int tc_multiply(ssht_plan_t p, int forward, void* dst, cudaStream_t st) {
   return 0;
 }
 
-// The projection of forward / adjoint from the folded torus sums H (in W), after the join.
+// Tensor-core forward / adjoint after the phi pass (in W2): the theta pass `which` (4 forward, 5
+// adjoint) writes the projection's data tiles itself (no H, no data packing), then the projection.
+int theta_to_tiles(ssht_plan_t p, int which, void* flm, cudaStream_t st) {
+  int rc;
+  const TileOut tiles = tc_forward_tiles(p->tc);
+  {
+    StageScope sc(p, SSHT_STAGE_FFT, st);
+    SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, p->W2, nullptr, st, &tiles), "torus pass");
+    p->launches += 1;
+  }
+  if ((rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
+  return mark_free_a(p, 1, st);
+}
+
+// The SIMT projection of forward / adjoint from the folded torus sums H (in W), after the join
+// (tensor-core plans take theta_to_tiles).
 template <typename T>
 int project(ssht_plan_t p, const void* H, void* flm, cudaStream_t st) {
   int rc;
-  if (p->tc) {
-    if ((rc = tc_pack(p, 1, H, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
-    return mark_free_a(p, 1, st);
-  }
   if ((rc = join_operands(p, st))) return rc;
   {
     StageScope sc(p, SSHT_STAGE_PROJECT, st);
@@ -434,7 +445,7 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   int rc = begin_operands(p, 0, st);
   if (rc) return rc;
   if (p->tc) {
-    if ((rc = tc_pack(p, 0, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)) ||
+    if ((rc = tc_pack(p, flm, st)) || (rc = join_operands(p, st)) || (rc = tc_multiply(p, 0, p->W1, st)) ||
         (rc = mark_free_a(p, 0, st)))
       return rc;
   } else {
@@ -481,17 +492,7 @@ int forward_impl(ssht_plan_t p, const void* f, void* flm, cudaStream_t st) {
   if (rc) return rc;
   if (p->torus) {
     if ((rc = run_torus(p, 2, f, p->W2, st))) return rc;
-    if (p->tc) {
-      // the theta pass writes the projection's data tiles itself (no H, no data packing)
-      const TileOut tiles = tc_forward_tiles(p->tc);
-      {
-        StageScope sc(p, SSHT_STAGE_FFT, st);
-        SSHT_CUDA(torus_pass(p->torus, 4, p->s, p->B, p->W2, nullptr, st, &tiles), "torus pass");
-        p->launches += 1;
-      }
-      if ((rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
-      return mark_free_a(p, 1, st);
-    }
+    if (p->tc) return theta_to_tiles(p, 4, flm, st);
     if ((rc = run_torus(p, 4, p->W2, p->W1, st))) return rc;
     return project<T>(p, p->W1, flm, st);
   }
@@ -523,7 +524,9 @@ int adjoint_impl(ssht_plan_t p, const void* g, void* flm, cudaStream_t st) {
   int rc = begin_operands(p, 1, st);
   if (rc) return rc;
   if (p->torus) {
-    if ((rc = run_torus(p, 3, g, p->W2, st)) || (rc = run_torus(p, 5, p->W2, p->W1, st))) return rc;
+    if ((rc = run_torus(p, 3, g, p->W2, st))) return rc;
+    if (p->tc) return theta_to_tiles(p, 5, flm, st);
+    if ((rc = run_torus(p, 5, p->W2, p->W1, st))) return rc;
     return project<T>(p, p->W1, flm, st);
   }
   rc = analysis_front<T>(p, g, 1, st);

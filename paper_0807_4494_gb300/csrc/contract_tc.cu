@@ -189,43 +189,6 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC
   for (int e = threadIdx.x; e < 2 * part_bytes / 16; e += blockDim.x) dst[e] = src[e];
 }
 
-// Forward data tile (m, c): Y_m[m', j], m' = 32 c + k, from H[b][m + Lp][m'] (m' < L).
-template <bool BF>
-__global__ void __launch_bounds__(256) pack_y_kernel(int L, int B, int NC, const float2* __restrict__ H,
-                                                     uint8_t* __restrict__ X) {
-  extern __shared__ __align__(16) uint8_t tile[];
-  const int m = blockIdx.y, c = blockIdx.x;
-  const int Lp = L - 1, NT = 2 * L - 1;
-  const int nC = (L + TK - 1) / TK;
-  const int part_bytes = NC * 128, half = NC / 2, nb = half / 2, total = TK * half;
-  float2 v[XPER];
-#pragma unroll
-  for (int q = 0; q < XPER; ++q) {
-    const int e = threadIdx.x + q * 256;
-    const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
-    const int mp = c * TK + k;
-    v[q] = make_float2(0.f, 0.f);
-    if (e < total && b < B && mp < L && !(sign && m == 0)) {
-      v[q] = H[((size_t)b * NT + (sign ? Lp - m : Lp + m)) * L + mp];
-      if (sign && (mp & 1)) v[q] = make_float2(-v[q].x, -v[q].y);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < XPER; ++q) {
-    const int e = threadIdx.x + q * 256;
-    if (e < total) {
-      const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
-      const int j = sign * half + 2 * b;
-      put_split<BF>(tile, part_bytes, j, k, v[q].x);
-      put_split<BF>(tile, part_bytes, j + 1, k, v[q].y);
-    }
-  }
-  __syncthreads();
-  uint4* dst = (uint4*)(X + ((size_t)m * nC + c) * 2 * part_bytes);
-  const uint4* src = (const uint4*)tile;
-  for (int e = threadIdx.x; e < 2 * part_bytes / 16; e += blockDim.x) dst[e] = src[e];
-}
-
 // ---------------------------------------------------------------------------------------------
 // The tensor-core GEMM
 // ---------------------------------------------------------------------------------------------
@@ -530,7 +493,6 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
     if ((e = prefer_shared(tc_gemm_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, true>)) != cudaSuccess ||
         (e = prefer_shared(tc_gemm_kernel<false, false>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, false>)) != cudaSuccess ||
         (e = prefer_shared(pack_v_kernel<true>)) != cudaSuccess || (e = prefer_shared(pack_v_kernel<false>)) != cudaSuccess ||
-        (e = prefer_shared(pack_y_kernel<true>)) != cudaSuccess || (e = prefer_shared(pack_y_kernel<false>)) != cudaSuccess ||
         (e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
         (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
       goto fail;
@@ -538,12 +500,10 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
       if ((e = cudaFuncSetAttribute(pack_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_y_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
     } else {
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
       if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
       if ((e = cudaFuncSetAttribute(pack_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_y_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
     }
   }
   *out = p;
@@ -578,14 +538,10 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches) {
+cudaError_t tc_pack_data(TcPlan* p, const void* src, cudaStream_t st, int* launches) {
   const int xsmem = 2 * p->NC * 128;
   const dim3 g(p->nC, p->L);
-  if (forward && p->bf16)
-    pack_y_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
-  else if (forward)
-    pack_y_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->B, p->NC, (const float2*)src, p->X);
-  else if (p->bf16)
+  if (p->bf16)
     pack_v_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);
   else
     pack_v_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);

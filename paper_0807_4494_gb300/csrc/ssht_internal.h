@@ -102,9 +102,9 @@ size_t tc_bytes(const TcPlan* p);
 // Pack the A operand (U_l[m'] Delta^l_{m'm} in FP32, then split) of one direction from the FP64
 // table and the FP32 copy of U.
 cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* U, cudaStream_t st, int* launches);
-// Pack the data operand: forward = 0: V from flm (float2 [B][L*L]); forward = 1: Y from the
-// folded torus sums H (float2 [B][N][L]).
-cudaError_t tc_pack_data(TcPlan* p, int forward, const void* src, cudaStream_t st, int* launches);
+// Pack the inverse's data operand V from flm (float2 [B][L*L]); the forward's and the adjoint's
+// data tiles come from their theta passes (TileOut).
+cudaError_t tc_pack_data(TcPlan* p, const void* src, cudaStream_t st, int* launches);
 // The contraction: forward = 0 writes the half rows F (float2 [B][N][L], m' >= 0) of the inverse;
 // forward = 1 writes flm (float2 [B][L*L]).  Timeouts set bit 2 of *status.
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);

@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
 // ---------------------------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
-                                                                       float2* __restrict__ H, TorusTables tb) {
+                                                                       float2* __restrict__ H, TorusTables tb, TileOut to) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -478,10 +478,23 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
     __syncthreads();
     if (active) {
       const float sig = ((m + s) & 1) ? -1.f : 1.f;
-      float2* Hr = H + (size_t)u * L;
-      for (int mp = tid; mp < L; mp += Geo<M>::T) {
-        const float2 a = buf[pidx(mp)];
-        Hr[mp] = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
+      if (to.mode) {
+        // the projection's data tiles (the last chunk's columns m' >= L are zeros)
+        const int b = (int)(u / N);
+        for (int mp = tid; mp < to.nC * 32; mp += Geo<M>::T) {
+          float2 v = make_float2(0.f, 0.f);
+          if (mp < L) {
+            const float2 a = buf[pidx(mp)];
+            v = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
+          }
+          put_tile(to, b, B, m, mp, v);
+        }
+      } else {
+        float2* Hr = H + (size_t)u * L;
+        for (int mp = tid; mp < L; mp += Geo<M>::T) {
+          const float2 a = buf[pidx(mp)];
+          Hr[mp] = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
+        }
       }
     }
     __syncthreads();
@@ -643,7 +656,7 @@ size_t torus_bytes(const TorusPlan* p) { return p ? p->bytes : 0; }
 cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st,
                        const TileOut* tiles) {
   const int L = p->L, M = p->M;
-  const TileOut to = (which == 4 && tiles) ? *tiles : TileOut();
+  const TileOut to = ((which == 4 || which == 5) && tiles) ? *tiles : TileOut();
   const long long rows = (which == 1 || which == 2 || which == 3) ? (long long)B * L
                          : (which == 5)                            ? (long long)B * p->N
                                                                    : (long long)B * L;  // pairs
@@ -660,7 +673,7 @@ cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* 
       case 2: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f / (float)p->N, I, O, p->tb); break; \
       case 3: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;              \
       case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to); break;      \
-      case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
+      case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to); break;      \
       default: return cudaErrorInvalidValue;                                                                 \
     }                                                                                                        \
     return cudaGetLastError();                                                                               \
