@@ -310,6 +310,11 @@ int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
     // still be running while this call's recursion starts
     if (p->free_valid) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free, 0), "operands-free wait");
     if (p->tc && p->afree_valid[forward]) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free_a[forward], 0), "A-free wait");
+    // ... and the other direction's contraction: it cannot share an SM with the recursion, so
+    // queued behind a running recursion it would wait for the whole sweep, while run first
+    // (about 1 ms) it lets the torus passes that follow it overlap the recursion
+    if (p->tc && p->afree_valid[1 - forward] && p->afree_capture[1 - forward] == cap)
+      SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free_a[1 - forward], 0), "other contraction wait");
   } else {
     SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");
     SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
