@@ -260,6 +260,32 @@ def run_ssht(args):
     value = throughput(world, B, args.steps, ms)
     ms_step = ms / args.steps
 
+    # end to end through the C ABI with host buffers: H2D of the coefficients, D2H of the result
+    # (measured before the oracle check below keeps the host cores busy)
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
+        h_in.copy_(flm.cpu())
+        h_out = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
+
+        def step_host():
+            plan.inverse(h_in, out=grid)        # host -> device inside the call
+            plan.forward(grid, out=h_out)       # device -> host inside the call
+        for _ in range(max(1, args.warmup)):
+            step_host()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        nrep = max(5, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            step_host()
+        torch.cuda.synchronize()
+        barrier(world, device)
+        el = max_over_ranks(time.perf_counter() - t0, world, device)
+        nbytes = B * L * L * h_in.element_size()
+        e2e = {"value": world * B * nrep / el, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": nrep}
+
     # roundtrip error over the whole batch, and the oracle check on sampled fields
     rt = float((back - flm).abs().max() / flm.abs().max())
     check = None
@@ -367,31 +393,6 @@ def run_ssht(args):
             roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": pk["hbm_gbs"][0], "unit": "GB/s",
                     "frac": None, "traffic": None}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1] > 0}
-
-    # end to end through the C ABI with host buffers: H2D of the coefficients, D2H of the result
-    e2e = None
-    if not args.no_e2e:
-        h_in = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
-        h_in.copy_(flm.cpu())
-        h_out = torch.empty(plan.coeff_shape(), dtype=cdt, pin_memory=True)
-
-        def step_host():
-            plan.inverse(h_in, out=grid)        # host -> device inside the call
-            plan.forward(grid, out=h_out)       # device -> host inside the call
-        for _ in range(max(1, args.warmup)):
-            step_host()
-        torch.cuda.synchronize()
-        barrier(world, device)
-        nrep = max(5, args.steps // 2)
-        t0 = time.perf_counter()
-        for _ in range(nrep):
-            step_host()
-        torch.cuda.synchronize()
-        barrier(world, device)
-        el = max_over_ranks(time.perf_counter() - t0, world, device)
-        nbytes = B * L * L * h_in.element_size()
-        e2e = {"value": world * B * nrep / el, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": nrep}
 
     # the plan-time Delta cache (the paper's timing protocol: precomputed Delta in memory)
     cache_line = None
