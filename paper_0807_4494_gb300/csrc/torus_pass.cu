@@ -2,7 +2,7 @@
 // (eqns dft_spatial / idft_spatial, Sec. 3.4.1) with the extension, phase, weight convolution and
 // transposition steps folded into their loads and stores.
 //
-// DFT core.  A row of length N = 2L-1 is transformed by Bluestein's algorithm (see dft.cu): the
+// DFT core.  A row of length N = 2L-1 is transformed by Bluestein's algorithm: the
 // chirped row goes through a forward FFT of size M = 2^p >= 2N-1, a product with the chirp
 // kernel's spectrum and an inverse FFT.  The FFTs are Stockham autosort passes (radix 16, last
 // pass radix 2/4/8) executed by T = M/16 threads per row; the first pass reads its inputs through a
@@ -25,10 +25,13 @@
 //                   by pairs of columns: X[b][p][t][j], column m + Lp = 2p + j (N + 1 rows a field,
 //                   the last pair half used), so that a store carries two columns of one ring and
 //                   the theta passes read a pair with one 16-byte load.
-//   forward_theta:  X[b][m][t] -> H[b][m][m'] (m' in [0,L)): per-m parity extension, theta DFT,
-//                   then the sin(theta) weight convolution as a zero-padded circular convolution
-//                   of length M in the same shared-memory buffer, and the fold of m' < 0.
-//   adjoint_theta:  X[b][m][t] -> H[b][m][m']: theta DFT of the unextended rings, fold of m' < 0.
+//   forward_theta:  X (a pair of columns) -> H[b][m][m'] (m' in [0,L)): per-m parity extension,
+//                   theta DFT, then the sin(theta) weight convolution as a zero-padded circular
+//                   convolution of length M in the same shared-memory buffer, and the fold of
+//                   m' < 0.  Tensor-core plans: the projection's split data tiles in place of H
+//                   (put_tile), so that the forward transform needs no separate data packing.
+//   adjoint_theta:  X (one column) -> H[b][m][m'] or the data tiles: theta DFT of the unextended
+//                   rings, fold of m' < 0.
 #include "ssht_internal.h"
 #include "tc_common.cuh"
 
