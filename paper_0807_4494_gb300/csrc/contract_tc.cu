@@ -86,19 +86,18 @@ __device__ __forceinline__ float2 ipow_signed(int s, int k) {
 // ---------------------------------------------------------------------------------------------
 
 // FP64 -> FP32, round to nearest even, by integer operations on the bit pattern (IEEE 754
-// rounding; the FP64 pipe is the scarce one on this part).  |x| below the FP32 normal range
-// becomes a signed zero; |x| must stay below 2^128 (entries here are at most ~13 in magnitude).
+// rounding; the FP64 pipe is the scarce one on this part): adding 2^28 - 1 plus the lowest kept
+// bit to the pattern rounds the 29 dropped fraction bits to nearest even, a carry moving into the
+// exponent as rounding requires; the exponent is then rebiased from 1023 to 127.  |x| below the
+// FP32 normal range becomes a signed zero; |x| must stay below 2^128 (entries here are at most ~13
+// in magnitude).
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-  if (e <= 0) return __uint_as_float(sign);
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
-  unsigned m23 = (unsigned)(mant >> 29);
-  const unsigned long long rest = mant & ((1ull << 29) - 1), half = 1ull << 28;
-  if (rest > half || (rest == half && (m23 & 1u))) ++m23;
-  // a carry out of the 23 fraction bits moves into the exponent field, as rounding requires
-  return __uint_as_float((sign | ((unsigned)e << 23)) + m23);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned long long t = b + 0x0FFFFFFFull + ((lo >> 29) & 1u);
+  const unsigned mag = ((unsigned)(t >> 29) - (896u << 23)) & 0x7FFFFFFFu;
+  const unsigned sign = hi & 0x80000000u;
+  return __uint_as_float(((hi >> 20) & 0x7FFu) <= 896u ? sign : (sign | mag));
 }
 
 // Inverse A tile (m, i, c): rows m' = 128 i + r, columns l = 32 c + k (K-major).
