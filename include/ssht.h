@@ -229,7 +229,8 @@ SSHT_API int ssht_group_adjoint(ssht_group_t group, const void* f, void* flm, vo
 
 /* Capture inverse (flm -> f) followed by forward (f -> flm_out) of the whole group into one
  * CUDA graph (replacing a previous capture); ssht_group_replay launches it on `stream`.  The
- * buffers are bound at capture time. */
+ * buffers are bound at capture time.  Capturing launches nothing: it records on a private stream
+ * and does not use its `stream` argument. */
 SSHT_API int ssht_group_capture(ssht_group_t group, const void* flm, void* f, void* flm_out, void* stream);
 SSHT_API int ssht_group_replay(ssht_group_t group, void* stream);
 

@@ -1255,7 +1255,8 @@ int ssht_group_capture(ssht_group_t g, const void* flm, void* f, void* flm_out, 
   if (!g || !flm || !f || !flm_out) return fail(SSHT_EINVAL, "null argument");
   if (!is_device_pointer(flm) || !is_device_pointer(f) || !is_device_pointer(flm_out))
     return fail(SSHT_EINVAL, "group buffers must be device memory");
-  cudaStream_t st = (cudaStream_t)stream;
+  (void)stream;  // capturing launches nothing: it records on a private stream (the legacy default
+                 // stream cannot be captured)
   cudaStream_t cap = nullptr;
   SSHT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
   if (g->exec) {
