@@ -1276,7 +1276,6 @@ int ssht_group_capture(ssht_group_t g, const void* flm, void* f, void* flm_out, 
   cudaStreamDestroy(cap);
   if (rc) return rc;
   if (ce != cudaSuccess) return fail(SSHT_ECUDA, std::string("group graph capture: ") + cudaGetErrorString(ce));
-  (void)st;
   return SSHT_OK;
 }
 
