@@ -7,6 +7,7 @@
 * adjoint: dot-product test and the conjugate transpose of the dense synthesis matrix;
 * the weight w(p) against numerical integration;
 * the torus symmetry eqn Ffourier_sym;
+* Parseval: the sphere integral of |f|^2 of the direct synthesis equals sum |sf_lm|^2;
 * the paper's triangular forward: its printed L = 5 sparsity pattern, machine precision at small
   band-limits and error growth with the band-limit (Sec. 4.2).
 """
@@ -111,6 +112,22 @@ def test_gauss_legendre_quadrature_recovers_coefficients(L, s):
     flm = inputs.coeffs(L, s, 1, seed=9)[0]
     got = brute.gauss_legendre_analysis(lambda th, ph: brute.synthesis_direct(flm, L, s, th, ph), L, s)
     assert rel(got, flm) < 1e-13
+
+
+@pytest.mark.parametrize("L,s", [(5, 0), (8, 2), (9, -1), (12, 3)])
+def test_parseval_of_direct_synthesis(L, s):
+    """Orthonormal spin harmonics: the integral of |f|^2 over the sphere is sum |sf_lm|^2.
+    |f|^2 is a polynomial of degree <= 2L - 2 in cos(theta) (the half-angle powers of d^l_{m,-s}
+    pair up for equal m and s) with phi frequencies |k| <= 2L - 2, so Gauss-Legendre with L nodes
+    and 4L uniform phi points integrate it exactly."""
+    flm = inputs.coeffs(L, s, 1, seed=11)[0]
+    x, w = np.polynomial.legendre.leggauss(L)
+    nphi = 4 * L
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    f = brute.synthesis_direct(flm, L, s, np.arccos(x), phi)
+    integral = float(np.sum(w[:, None] * np.abs(f) ** 2) * 2 * np.pi / nphi)
+    norm2 = float(np.sum(np.abs(flm) ** 2))
+    assert abs(integral - norm2) < 1e-12 * norm2
 
 
 @pytest.mark.parametrize("L,s", [(1, 0), (2, 1), (5, 0), (10, 2), (17, -3), (24, 0)])
