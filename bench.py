@@ -260,6 +260,24 @@ def run_ssht(args):
     value = throughput(world, B, args.steps, ms)
     ms_step = ms / args.steps
 
+    # the recursion alone, nothing beside it (in the step the forward call's sweep shares its SMs
+    # with the torus passes): a few sweeps through ssht_wigner_delta, timed by the same stage events
+    delta_alone_ms = None
+    if rank == 0 and args.delta_mode == "recompute":
+        tab = torch.empty(L * (L + 1) * (2 * L + 1) // 6, dtype=torch.float64, device=device)
+        plan.wigner_delta(out=tab)
+        torch.cuda.synchronize()
+        plan.profile(True)
+        for _ in range(3):
+            plan.wigner_delta(out=tab)
+            torch.cuda.synchronize()
+        dst, _ = plan.profile_read()
+        plan.profile(False)
+        plan.check()
+        if dst["delta"][1] > 0:
+            delta_alone_ms = dst["delta"][0] / dst["delta"][1]
+        del tab
+
     # end to end through the C ABI with host buffers: H2D of the coefficients, D2H of the result
     # (measured before the oracle check below keeps the host cores busy)
     e2e = None
@@ -367,6 +385,11 @@ def run_ssht(args):
                     "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
                     "work_per_launch": "%.3g flops = 7 x %.3g half-step + 8 x %.3g integer-step updates "
                                        "(4 and 5 FP64 instructions)" % (flops, nh, ni)}
+            if delta_alone_ms:
+                a1 = flops / (delta_alone_ms / 1e3) / 1e12
+                roof["alone"] = {"ms": delta_alone_ms, "achieved": a1, "frac": a1 / peak,
+                                 "note": "the same sweep timed by itself (in the step the forward call's "
+                                         "sweep shares its SMs with the torus passes)"}
         elif dom in ("inverse", "project") and prec in ("tf32x3", "bf16x6"):
             # useful flops (4 per complex x real MAC) and the issued split-product tensor flops
             flops = 4.0 * B * contraction_macs(L, s)
