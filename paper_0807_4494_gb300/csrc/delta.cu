@@ -207,14 +207,6 @@ __device__ __forceinline__ SegRange warp_segments(int lo, int hi, int add, int w
   return r;
 }
 
-// 1/k to FP64 accuracy without an FP64 division: FP32 reciprocal, then two Newton steps.
-__device__ __forceinline__ double recip(double k) {
-  double r = (double)(1.0f / (float)k);
-  r = r * fma(-k, r, 2.0);
-  r = r * fma(-k, r, 2.0);
-  return r;
-}
-
 // Step l -> l + 1 of CTA cta: owned rows q[0], q[1] of degree l + 1, and the CTAs q[2] .. q[3]
 // that produced the degree-l rows [r0 - 2, r1 + 1]: the rows staged here, and the rows whose
 // producers also read (one step earlier) the slab rows this CTA overwrites, pad slots included.
@@ -288,21 +280,6 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
   const int nb = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  auto params = [&](int l) {
-    int* q = s_par[l & 1];
-    const int lp = l + 1;
-    if (P.part) {
-      const int4 v = __ldg(&P.part[(size_t)l * nb + cta]);
-      q[0] = v.x;
-      q[1] = v.y;
-      q[2] = v.z;
-      q[3] = v.w;
-    } else {
-      step_partition(l, cta, nb, q);
-    }
-    s_sc[l & 1][0] = 0.70710678118654752440 * recip((double)(2 * l + 1));
-    s_sc[l & 1][1] = 0.70710678118654752440 * recip((double)(2 * lp));
-  };
   // sqrt(k) and 1/sqrt(k) from shared memory (the column and row factors): copied after the
   // chunk area, published by the grid barrier's first __syncthreads.
   double* sq_s = smem + cap;
@@ -312,13 +289,38 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
   }
   const double* __restrict__ sq = sq_s;
   const double* __restrict__ rsq = sq_s + 2 * P.L + 4;
+  // Thread 32 makes the next step's parameters while the step runs; the partition entry comes
+  // from a register loaded a step earlier, so that no global load or FP64 division sits in a
+  // step (1/(2j) = (1/sqrt(2j))^2 from the shared table).
+  int4 part_next = make_int4(0, 0, 0, 0);
+  auto load_part = [&](int l) { return P.part ? __ldg(&P.part[(size_t)l * nb + cta]) : make_int4(0, 0, 0, 0); };
+  auto params = [&](int l, int4 v) {
+    int* q = s_par[l & 1];
+    const int lp = l + 1;
+    if (P.part) {
+      q[0] = v.x;
+      q[1] = v.y;
+      q[2] = v.z;
+      q[3] = v.w;
+    } else {
+      step_partition(l, cta, nb, q);
+    }
+    const double r1 = rsq[2 * l + 1], r2 = rsq[2 * lp];
+    s_sc[l & 1][0] = 0.70710678118654752440 * (r1 * r1);
+    s_sc[l & 1][1] = 0.70710678118654752440 * (r2 * r2);
+  };
+
   if (threadIdx.x == 0) s_pre = -1;
   unsigned int* done = P.counter + 4;
   if (cta == 0 && threadIdx.x < 3) {  // degree 0: row 0 = (Delta_{0,-1}, Delta_00, Delta_01) = (0, 1, 0)
     P.slab0[threadIdx.x] = threadIdx.x == 1 ? 1.0 : 0.0;
     if (threadIdx.x == 0) P.table[0] = 1.0;
   }
-  if (!grid_barrier(P.counter, nb, P.status, [&] { params(0); })) return;
+  if (!grid_barrier(P.counter, nb, P.status, [&] {
+        params(0, load_part(0));
+        if (P.L > 2) part_next = load_part(1);
+      }))
+    return;
   for (int l = 0; l + 1 < P.L; ++l) {
     __syncthreads();  // params(l) visible; every thread is done with step l - 1
     if (s_pre == -2) return;
@@ -326,7 +328,10 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
     const int r0 = s_par[l & 1][0], r1 = s_par[l & 1][1];
     const int o0 = s_par[l & 1][2], o1 = s_par[l & 1][3];
     const double sc = s_sc[l & 1][0], sc2 = s_sc[l & 1][1];
-    if (threadIdx.x == 32 && l + 2 < P.L) params(l + 1);
+    if (threadIdx.x == 32 && l + 2 < P.L) {
+      params(l + 1, part_next);
+      if (l + 3 < P.L) part_next = load_part(l + 2);
+    }
     if (r0 >= r1) {  // nothing owned at this degree: nothing to wait for or to publish but progress
       if (threadIdx.x == 0) atomicExch(done + cta, (unsigned)lp);
       continue;
