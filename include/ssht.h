@@ -186,7 +186,7 @@ SSHT_API int ssht_plan_profile_read(ssht_plan_t plan, double* ms, long long* cou
  * has no counterpart), in recording order, at most cap of them: *n receives the number written.
  * stage[i] is an SSHT_STAGE_* id, lane[i] 0 for the caller's stream and 1 for the plan's second
  * stream (the recursion and the A-operand packing), t0[i] / t1[i] the bracket's start and end
- * in milliseconds after the first bracket's start.  A bracket starts when its stream reaches it,
+ * in milliseconds after the earliest bracket's start.  A bracket starts when its stream reaches it,
  * which can precede the first kernel's start when that kernel waits for room on the GPU.  The
  * brackets are then folded into the totals of ssht_plan_profile_read.  Synchronises the device.
  * At most the last 8192 brackets are kept between reads. */

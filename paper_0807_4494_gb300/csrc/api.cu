@@ -937,6 +937,7 @@ int ssht_plan_profile_trace(ssht_plan_t p, int* stage, int* lane, double* t0, do
   if (rc) return rc;
   SSHT_CUDA(cudaDeviceSynchronize(), "device synchronize");
   *n = (int)std::min(p->evs.size(), (size_t)cap);
+  double first = 0.0;  // brackets of the two streams need not start in recording order
   for (int i = 0; i < *n; ++i) {
     const auto& e = p->evs[i];
     float a = 0.f, b = 0.f;
@@ -946,6 +947,11 @@ int ssht_plan_profile_trace(ssht_plan_t p, int* stage, int* lane, double* t0, do
     lane[i] = e.lane;
     t0[i] = a;
     t1[i] = b;
+    first = std::min(first, (double)a);
+  }
+  for (int i = 0; i < *n; ++i) {
+    t0[i] -= first;
+    t1[i] -= first;
   }
   fold_events(p);
   return SSHT_OK;

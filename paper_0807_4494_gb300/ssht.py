@@ -161,7 +161,7 @@ def ssht_plan_profile_read(h):
 def ssht_plan_profile_trace(h, cap=8192):
     """Returns the stage brackets since profiling was enabled or last read, in recording order:
     a list of (stage name, lane, start ms, end ms), lane 0 the caller's stream and 1 the plan's
-    second stream, times after the first bracket's start."""
+    second stream, times after the earliest bracket's start."""
     stage = (ctypes.c_int * cap)()
     lane = (ctypes.c_int * cap)()
     t0 = (ctypes.c_double * cap)()
