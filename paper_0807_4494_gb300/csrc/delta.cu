@@ -16,17 +16,18 @@
 // out the same way in shared memory.
 //
 // Parallel layout.  One cooperative persistent grid walks l.  For the step l -> l+1 the rows
-// of the new integer slab are split over the CTAs in equal numbers of 32-column segments (a
-// warp computes one segment per instruction stream).  A CTA that owns integer rows [r0, r1)
-// works through them in chunks [c0, c1) sized to its shared memory: it copies the padded rows
-// [c0-1, c1] of degree l from global memory into shared memory, computes the half-integer rows
-// [c0-1, c1-1], then the integer rows [c0, c1), which go to the next slab (global) and to
-// shared memory.  It then publishes "degree l+1 done" in its flag word and writes the rows to the
-// quadrant table from shared memory, both orientations coalesced, while its neighbours already
-// proceed.  Before step l -> l+1 a CTA waits only for the CTAs that produced the rows of degree l
-// it reads (which are also all the readers of the slab rows it overwrites): no grid-wide barrier
-// per degree.  Every wait spins at most one second, then latches a status bit, raises the abort
-// flag and leaves the kernel; the other CTAs leave at their next wait.
+// of the new integer slab are split over the CTAs by a partition made on the host that minimises
+// the largest share of 32-column segments (a warp computes one segment per instruction stream),
+// or, without a host table, by equal shares made in the kernel.  A CTA that owns integer rows
+// [r0, r1) works through them in chunks [c0, c1) sized to its shared memory: it copies the padded
+// rows [c0-1, c1] of degree l from global memory into shared memory, computes the half-integer
+// rows [c0-1, c1-1], then the integer rows [c0, c1), which go to the next slab (global) and to
+// shared memory.  Warp 0 then publishes "degree l+1 done" in the CTA's flag word and waits for the
+// flags of the next step while the other warps write the rows to the quadrant table from shared
+// memory, both orientations coalesced.  A CTA waits only for the CTAs that produced the rows of
+// degree l it reads (which are also all the readers of the slab rows it overwrites): no grid-wide
+// barrier per degree.  Every wait spins at most one second, then latches a status bit, raises the
+// abort flag and leaves the kernel; the other CTAs leave at their next wait.
 #include "ssht_internal.h"
 
 #include <algorithm>
