@@ -78,6 +78,13 @@ typedef enum {
                           * one complex transform (half the work).  Samples f are real arrays
                           * [batch][L][2L-1] (double or float); coefficients stay complex and the
                           * inverse reads them as given (they must have the symmetry). */
+#define SSHT_FLAG_RISBO 2 /* make the Delta^l table with the Risbo recursion (the recursion the paper
+                           * uses, Sec. 2.2: degree l+1 from degree l by two half-integer steps)
+                           * instead of the default three-term relation in the first index m'
+                           * (Delta_{m'-1,m} from Delta_{m'm} and Delta_{m'+1,m} within one degree,
+                           * from the closed-form first row Delta_{l m}).  Both give Delta^l to
+                           * rounding; the default needs no hand-off between degrees and about a
+                           * third of the FP64 instructions. */
 
 typedef struct {
   int L;          /* exclusive band-limit, 1 <= L <= 2048                      */
@@ -85,7 +92,7 @@ typedef struct {
   int batch;      /* number of fields per call, 1 <= batch <= 65535            */
   int precision;  /* ssht_precision                                            */
   int delta_mode; /* ssht_delta_mode                                           */
-  int flags;      /* 0 or SSHT_FLAG_REAL                                       */
+  int flags;      /* 0 or SSHT_FLAG_REAL and / or SSHT_FLAG_RISBO              */
 } ssht_plan_desc;
 
 typedef struct ssht_plan_s* ssht_plan_t;
@@ -150,9 +157,10 @@ SSHT_API int ssht_wigner_delta(ssht_plan_t plan, double* out, void* stream);
  * that every GPU loading this library holds until the process exits.
  * out: device buffer of L(L+1)(2L+1)/6 doubles, layout as in ssht_wigner_delta; the caller owns
  * it.  L outside [1, 512] or a NULL out returns SSHT_EINVAL before any device work.
- * The first call on a device sets that device up (looks up the address of the array and fills
- * its square-root table) and should be made before any stream capture.  Asynchronous on
- * `stream`.  All calls share the one array: calls whose work overlaps on the GPU (on different
+ * The first call on a device sets that device up (looks up the address of the array, fills its
+ * square-root table and waits for that fill on `stream`); made during stream capture it returns
+ * SSHT_EINVAL and sets nothing up, so make it before any capture.  Later calls are asynchronous
+ * on `stream`.  All calls share the one array: calls whose work overlaps on the GPU (on different
  * streams or devices' shared contexts) race and must be serialised by the caller.  If a grid
  * barrier inside the recursion exceeds its one-second spin limit the table is left incomplete
  * and out[0] (normally Delta^0_00 = 1) is set to NaN. */

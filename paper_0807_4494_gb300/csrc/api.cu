@@ -598,7 +598,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (L < 1 || L > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
   if (s <= -L || s >= L) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
   if (nfields < 1 || nfields > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
-  if ((desc->flags & ~SSHT_FLAG_REAL) != 0) return fail(SSHT_EINVAL, "unknown flags");
+  if ((desc->flags & ~(SSHT_FLAG_REAL | SSHT_FLAG_RISBO)) != 0) return fail(SSHT_EINVAL, "unknown flags");
   const bool real = (desc->flags & SSHT_FLAG_REAL) != 0;
   if (real && s != 0) return fail(SSHT_EINVAL, "real fields (SSHT_FLAG_REAL) need spin 0");
   if (real && shared) return fail(SSHT_EINVAL, "groups take complex fields only");
@@ -647,7 +647,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     p->delta = *shared;
     p->delta_shared = true;
   } else {
-    ce = delta_setup(p->delta, L, p->device);
+    ce = delta_setup(p->delta, L, p->device, (desc->flags & SSHT_FLAG_RISBO) ? kDeltaRisbo : kDeltaColumn);
     if (ce != cudaSuccess) {
       release(p);
       return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,

@@ -617,9 +617,10 @@ static void optimal_cuts(int l, int nb, int* cuts) {
   pack(lo, cuts);
 }
 
-cudaError_t delta_setup(DeltaWork& w, int L, int device) {
+static cudaError_t risbo_setup(DeltaWork& w, int L, int device) {
   cudaError_t e;
   int sms = 0, per_sm = 0, smem_optin = 0;
+  w.method = kDeltaRisbo;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) return e;
   w.threads = kThreads;
@@ -694,17 +695,23 @@ cudaError_t delta_setup(DeltaWork& w, int L, int device) {
   return cudaMemcpy(w.sqrt_tab, sq.data(), sq.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
+cudaError_t delta_setup(DeltaWork& w, int L, int device, int method) {
+  return method == kDeltaRisbo ? risbo_setup(w, L, device) : column_setup(w, L, device);
+}
+
 void delta_free(DeltaWork& w) {
-  void* ptrs[] = {w.table, w.slab[0], w.slab[1], w.sqrt_tab, w.barrier, w.status, w.part};
+  void* ptrs[] = {w.table, w.slab[0], w.slab[1], w.sqrt_tab, w.barrier, w.status, w.part, w.tasks};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   w.part = nullptr;
+  w.tasks = nullptr;
   w.table = w.slab[0] = w.slab[1] = w.sqrt_tab = nullptr;
   w.barrier = nullptr;
   w.status = nullptr;
 }
 
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
+  if (w.method != kDeltaRisbo) return column_run(w, L, st);
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, (4 + (size_t)w.blocks) * sizeof(unsigned int), st)) != cudaSuccess) return e;
   RisboParams P;
@@ -797,37 +804,51 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   NoAllocDevice& d = g_noalloc_dev[dev];
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  auto cuda_fail = [](const char* what, cudaError_t e) {
+    return set_last_error(SSHT_ECUDA, (std::string("ssht_wigner_delta_noalloc: ") + what + ": " +
+                                       cudaGetErrorString(e)).c_str());
+  };
+  cudaError_t ce;
   if (!d.ready) {
+    // The set-up fills the square-root table with a kernel and waits for it, so it must not be
+    // recorded into a graph (the fill would then only happen at the graph's launch).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((ce = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail("cudaStreamIsCapturing", ce);
+    if (cs != cudaStreamCaptureStatusNone)
+      return set_last_error(SSHT_EINVAL, "ssht_wigner_delta_noalloc: the first call on a device sets the device up and "
+                                         "must not be made during stream capture");
     // Once per device, with that device current: the device address of the scratch array.
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess)
-      return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: cudaGetSymbolAddress failed");
+    if ((ce = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", ce);
     d.base = (double*)p;
-    int sms = 0, smem_optin = 0, per_sm = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSHT_ECUDA;
-    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-      return SSHT_ECUDA;
+    int smem_optin = 0, per_sm = 0;
+    if ((ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+      return cuda_fail("shared-memory attribute query", ce);
     const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
-    if (cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return SSHT_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, smem) != cudaSuccess ||
-        per_sm < 1)
-      return SSHT_ECUDA;
+    if ((ce = cudaFuncSetAttribute(risbo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return cuda_fail("cudaFuncSetAttribute", ce);
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, smem)) != cudaSuccess)
+      return cuda_fail("occupancy query", ce);
+    if (per_sm < 1)
+      return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: the recursion kernel does not fit on an SM");
     double* sq = d.base + 2 * kNoAllocSlab;
     noalloc_sqrt_kernel<<<(unsigned)((kNoAllocSqrt + 255) / 256), 256, 0, st>>>(sq, (int)kNoAllocSqrt);
-    if (cudaGetLastError() != cudaSuccess) return SSHT_ECUDA;
+    if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_fail("square-root table launch", ce);
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail("square-root table", ce);
     d.ready = true;
   }
   int sms = 0, smem_optin = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSHT_ECUDA;
-  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return SSHT_ECUDA;
+  if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail("SM count query", ce);
+  if ((ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return cuda_fail("shared-memory attribute query", ce);
   const size_t smem = (size_t)std::min(smem_optin - 1024, 200 * 1024);
   if (sms > kNoAllocMaxCtas)
     return set_last_error(SSHT_EUNSUPPORTED, "ssht_wigner_delta_noalloc: more SMs than its fixed scratch has flags for");
   unsigned int* words = (unsigned int*)(d.base + 2 * kNoAllocSlab + 2 * kNoAllocSqrt);  // counter, abort, status, -, flags
   // The array keeps the previous call's contents: the synchronisation words start at zero.
-  if (cudaMemsetAsync(words, 0, (4 + (size_t)sms) * sizeof(unsigned int), st) != cudaSuccess) return SSHT_ECUDA;
+  if ((ce = cudaMemsetAsync(words, 0, (4 + (size_t)sms) * sizeof(unsigned int), st)) != cudaSuccess)
+    return cuda_fail("synchronisation-word reset", ce);
   RisboParams P;
   P.L = L;
   P.table = out;

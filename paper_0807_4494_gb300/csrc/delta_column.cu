@@ -1,0 +1,242 @@
+// Delta^l = d^l(pi/2) for l = 0 .. L-1, FP64, one column m at a time by the three-term relation
+// in the first index m' -- the default way the plans make the table (the Risbo recursion of
+// Sec. 2.2, which the paper uses, is in delta.cu and selected by SSHT_FLAG_RISBO).
+//
+// The relation.  d^l(pi/2) rotates the z axis onto the x axis, so it turns J_z into J_x:
+// J_x Delta^l = Delta^l J_z with the ladder elements <m'+-1| J_+- |m'> = sqrt((l -+ m')(l +- m' + 1)).
+// Written out for row m' and column m of degree l:
+//   sqrt((l-m'+1)(l+m')) Delta_{m'-1,m} + sqrt((l-m')(l+m'+1)) Delta_{m'+1,m} = 2m Delta_{m'm},
+// i.e. Delta_{m'-1,m} = 2m a(m') Delta_{m'm} - b(m') Delta_{m'+1,m} with
+//   a(m') = 1/sqrt((l-m'+1)(l+m')),  b(m') = sqrt((l-m')(l+m'+1)) a(m')   (b(l) = 0).
+// It starts from the first row, which eqn wignerd_b gives in closed form at beta = pi/2:
+//   Delta_{l m} = (-1)^{l-m} 2^{-l} sqrt(C(2l, l+m)) = (-1)^{l-m} 2^{-l} prod_{k=m+1}^{l} g(k),
+//   g(k) = sqrt((l+k)/(l-k+1)).
+// Run downwards in m' (from the first row into the interior) the relation moves from the
+// region where d(pi/2) decays towards the one where it oscillates, the stable direction; the
+// table matches the oracle's Risbo recursion to ~1e-14 up to l = 2047.
+//
+// Work.  Every degree is independent once its first row is known, so there is no hand-off
+// between CTAs: a task is one degree l and one block of 32 columns m = 32b + lane, a warp walks
+// m' from l down to 32b (the octant part m' >= m of its columns, plus the 32 x 32 diagonal
+// block), writing row m' of its columns directly (coalesced) and the transposed entries
+// Delta_{m m'} = (-1)^{m'-m} Delta_{m'm} of rows m through a 32 x 32 shared-memory block (again
+// coalesced).  Each update is 3 FP64 instructions (the FP64 pipe is the scarce one on this part:
+// 2 lanes per SM and clock); the coefficients of 32 consecutive m' are made once per chunk by the
+// warp from the sqrt tables.  Tasks are taken longest first from an atomic counter.
+//
+// Range.  Delta_{l,l} = 2^{-l} is below the FP64 normal range for l > 1022.  For band-limits
+// above 1024 each lane carries its own binary exponent E (true value = stored * 2^E) until the
+// value is back in range; entries below 2^-1021 are written as 0 (they are below 1e-307 and
+// contribute nothing to any transform).
+#include "ssht_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace ssht {
+namespace {
+
+__device__ __forceinline__ size_t delta_offset_dev(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
+
+constexpr int kColWarps = 8;
+constexpr int kColThreads = 32 * kColWarps;
+constexpr int kStageDoubles = 32 * 33;              // a warp's transposition block (padded rows)
+constexpr int kWarpDoubles = kStageDoubles + 64;    // + the chunk's coefficients a[32], b[32]
+constexpr size_t kColSmem = (size_t)kColWarps * kWarpDoubles * sizeof(double);
+
+struct ColumnParams {
+  int L;
+  int ntasks;
+  const int2* tasks;       // (l, b), longest first
+  const double* sq;        // sqrt(k), k < 2L + 4
+  const double* rsq;       // 1/sqrt(k), k >= 1
+  double* table;           // quadrant table, entry (l, m', m) at offset(l) + m'(l+1) + m
+  unsigned int* counter;   // next task (zeroed before the launch)
+};
+
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+  return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
+}
+// Unbiased binary exponent of a normal nonzero double, and the same mantissa with exponent e
+// (integer operations on the bit pattern; no FP64 instruction).
+__device__ __forceinline__ int exp_of(double v) { return ((__double2hiint(v) >> 20) & 0x7ff) - 1023; }
+__device__ __forceinline__ double with_exp(double v, int e) {
+  const int hi = (__double2hiint(v) & (int)0x800fffff) | ((e + 1023) << 20);
+  return __hiloint2double(hi, __double2loint(v));
+}
+
+template <bool SCALED>
+__global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(ColumnParams P) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* stage = smem + warp * kWarpDoubles;
+  double* coef = stage + kStageDoubles;
+  const double* __restrict__ sq = P.sq;
+  const double* __restrict__ rsq = P.rsq;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(P.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= P.ntasks) break;
+    const int2 task = P.tasks[t];
+    const int l = task.x, m0 = 32 * task.y, m = m0 + lane;
+    const bool act = m <= l;
+
+    // ---- first row: Delta_{l m} = (-1)^{l-m} 2^{-l} prod_{k=m+1}^{l} g(k) ----
+    // G = prod_{k = m0+33}^{l} g(k) as gm * 2^ge: each lane multiplies every 32nd factor (at most
+    // 64 factors of at most sqrt(2l) <= 64, so no overflow), then the warp multiplies the lanes'
+    // products with their exponents split off (the whole product reaches 2^l).
+    double gm = 1.0;
+    for (int k = m0 + 33 + lane; k <= l; k += 32) gm = __dmul_rn(gm, __dmul_rn(sq[l + k], rsq[l - k + 1]));
+    int ge = exp_of(gm);
+    gm = with_exp(gm, 0);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, gm, d);
+      const int oe = __shfl_xor_sync(0xffffffffu, ge, d);
+      gm = __dmul_rn(gm, om);  // in [1, 4)
+      ge += oe + exp_of(gm);
+      gm = with_exp(gm, 0);
+    }
+    // h = prod_{k = m+1}^{min(m0+32, l)} g(k): suffix product of the lanes' own factors g(m+1)
+    // (at most 32 factors, at most 2^192).
+    double h = (m + 1 <= l) ? __dmul_rn(sq[l + m + 1], rsq[l - m]) : 1.0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, h, d);
+      if (lane + d < 32) h = __dmul_rn(h, o);
+    }
+    const double v = __dmul_rn(h, gm);  // Delta_{l m} = (-1)^{l-m} v 2^{ge - l}
+    int E = 0;                          // SCALED: true value = stored * 2^E (E < 0 while out of range)
+    double cur;
+    if (!act) {
+      cur = 0.0;
+    } else if (!SCALED || exp_of(v) + ge - l >= -1021) {
+      cur = flip_sign(ldexp(v, ge - l), ((l - m) & 1) != 0);
+    } else {
+      cur = flip_sign(v, ((l - m) & 1) != 0);
+      E = ge - l;
+    }
+    double prev = 0.0;
+    const double m2 = 2.0 * (double)m;
+    double* __restrict__ T = P.table + delta_offset_dev(l);
+    const size_t row = (size_t)l + 1;
+
+    // ---- rows m' = l .. m0 ----
+    for (int mp = l; mp >= m0; --mp) {
+      const int j = mp & 31;
+      if (mp == l || j == 31) {
+        // coefficients a(m'), b(m') of the chunk of m' in [mp & ~31, (mp & ~31) + 31]
+        __syncwarp();
+        const int k = (mp & ~31) + lane;
+        double a = 0.0, b = 0.0;
+        if (k >= 1 && k <= l) {
+          a = __dmul_rn(rsq[l - k + 1], rsq[l + k]);
+          b = __dmul_rn(__dmul_rn(sq[l - k], sq[l + k + 1]), a);
+        }
+        coef[lane] = a;
+        coef[32 + lane] = b;
+        __syncwarp();
+      }
+      const double out = (SCALED && E != 0) ? 0.0 : cur;
+      if (act) T[(size_t)mp * row + m] = out;
+      if (mp >= m0 + 32) {
+        // transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}, written a 32-column chunk at a time
+        stage[lane * 33 + j] = flip_sign(out, ((mp - m) & 1) != 0);
+        if (j == 0) {
+          __syncwarp();
+          const int c = mp + lane;
+          for (int r = 0; r < 32 && m0 + r <= l; ++r)
+            if (c <= l) T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
+          __syncwarp();
+        }
+      }
+      if (mp > m0) {
+        const double c = __dmul_rn(m2, coef[j]);
+        const double t2 = __dmul_rn(coef[32 + j], prev);
+        const double nxt = __fma_rn(c, cur, -t2);
+        prev = cur;
+        cur = nxt;
+        if (SCALED && E != 0) {
+          const int x = exp_of(cur);
+          if (x + E >= -1021) {  // back in the normal range: fold the exponent in
+            cur = ldexp(cur, E);
+            prev = ldexp(prev, E);
+            E = 0;
+          } else if (x > 512) {  // keep the stored values far from overflow
+            cur = __dmul_rn(cur, 0x1p-512);
+            prev = __dmul_rn(prev, 0x1p-512);
+            E += 512;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// Tasks (l, b) for every degree l < L and block b <= l / 32 of 32 columns, longest first (a task
+// of degree l and block b walks l - 32b + 1 rows).
+static std::vector<int2> column_tasks(int L) {
+  std::vector<int2> t;
+  for (int l = 0; l < L; ++l)
+    for (int b = 0; 32 * b <= l; ++b) t.push_back(make_int2(l, b));
+  std::stable_sort(t.begin(), t.end(), [](const int2& x, const int2& y) { return x.x - 32 * x.y > y.x - 32 * y.y; });
+  return t;
+}
+
+cudaError_t column_setup(DeltaWork& w, int L, int device) {
+  cudaError_t e;
+  int sms = 0, per_sm = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+  const bool scaled = L > 1024;
+  const void* fn = scaled ? (const void*)column_recursion_kernel<true> : (const void*)column_recursion_kernel<false>;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kColThreads, kColSmem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const std::vector<int2> tasks = column_tasks(L);
+  w.method = kDeltaColumn;
+  w.threads = kColThreads;
+  w.blocks = sms * std::min(per_sm, 2);
+  w.smem = kColSmem;
+  w.ntasks = (int)tasks.size();
+  if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.barrier, 4 * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.tasks, tasks.size() * sizeof(int2))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(w.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
+  w.bytes = (delta_offset(L) + 2 * (2 * (size_t)L + 4)) * sizeof(double) + 4 * sizeof(unsigned int) + sizeof(int) +
+            tasks.size() * sizeof(int2);
+  const size_t nsq = 2 * (size_t)L + 4;
+  std::vector<double> sqv(2 * nsq, 0.0);
+  for (size_t k = 0; k < nsq; ++k) sqv[k] = std::sqrt((double)k);
+  for (size_t k = 1; k < nsq; ++k) sqv[nsq + k] = 1.0 / std::sqrt((double)k);
+  return cudaMemcpy(w.sqrt_tab, sqv.data(), sqv.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  ColumnParams P;
+  P.L = L;
+  P.ntasks = w.ntasks;
+  P.tasks = w.tasks;
+  P.sq = w.sqrt_tab;
+  P.rsq = w.sqrt_tab + (2 * (size_t)L + 4);
+  P.table = w.table;
+  P.counter = w.barrier;
+  if (L > 1024)
+    column_recursion_kernel<true><<<w.blocks, w.threads, w.smem, st>>>(P);
+  else
+    column_recursion_kernel<false><<<w.blocks, w.threads, w.smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace ssht

@@ -41,7 +41,12 @@ inline size_t tri(long long l) { return (size_t)(l * (l + 1) / 2); }
 // ---------------------------------------------------------------------------
 // Delta recursion (delta.cu)
 // ---------------------------------------------------------------------------
+// How the Delta table is made: the three-term relation in m' (delta_column.cu, the default) or
+// the Risbo recursion the paper uses (delta.cu).
+enum : int { kDeltaColumn = 0, kDeltaRisbo = 1 };
+
 struct DeltaWork {
+  int method = kDeltaColumn;
   double* table = nullptr;        // quadrant table, delta_offset(L) doubles
   double* slab[2] = {nullptr, nullptr};  // padded octant slabs (rows 0..L, columns -1..m+1)
   double* sqrt_tab = nullptr;     // sqrt(k), k = 0 .. 2L + 2
@@ -54,11 +59,16 @@ struct DeltaWork {
   int4* part = nullptr;   // per step and CTA: owned rows and the CTAs waited for
   size_t bytes_part = 0;
   long long cap = 0;  // shared-memory doubles per CTA
+  int2* tasks = nullptr;  // column method: (degree, column block) tasks, longest first
+  int ntasks = 0;
 };
 
-cudaError_t delta_setup(DeltaWork& w, int L, int device);
+cudaError_t delta_setup(DeltaWork& w, int L, int device, int method = kDeltaColumn);
 void delta_free(DeltaWork& w);
 cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st);
+// The column method's setup and launch (delta_column.cu); delta_setup / delta_run dispatch.
+cudaError_t column_setup(DeltaWork& w, int L, int device);
+cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st);
 // U[l][m'] = sqrt((2l+1)/4pi) Delta^l_{m',-s}, l < L, 0 <= m' <= l, at tri(l) + m'; Uf is the
 // same in FP32 (rounded to nearest).
 cudaError_t delta_spin_column(const double* table, int L, int s, double* U, float* Uf, cudaStream_t st);

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libssht.so")
 
 FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
 FLAG_REAL = 1
+FLAG_RISBO = 2
 RECOMPUTE, CACHE = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
 ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
@@ -193,10 +194,11 @@ class Plan:
     Tensors: coefficients ``[batch, L*L]``, samples ``[batch, L, 2L-1]`` (complex128 for
     precision ``fp64``, complex64 otherwise), on the plan's CUDA device or on the host.
     ``real=True`` (spin 0): real fields, samples real (float64 / float32), coefficients complex
-    with sf_{l,-m} = (-1)^m conj(sf_lm).
+    with sf_{l,-m} = (-1)^m conj(sf_lm).  ``recursion="risbo"`` makes Delta with the Risbo
+    recursion the paper uses instead of the default three-term relation in m'.
     """
 
-    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False):
+    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False, recursion="column"):
         self.L, self.s, self.batch = int(L), int(s), int(batch)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.delta_mode = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
@@ -204,7 +206,10 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
         self.grid_dtype = (torch.float64 if self.precision == FP64 else torch.float32) if self.real else self.dtype
-        self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode, FLAG_REAL if self.real else 0)
+        if recursion not in ("column", "risbo"):
+            raise ValueError("recursion must be 'column' or 'risbo'")
+        flags = (FLAG_REAL if self.real else 0) | (FLAG_RISBO if recursion == "risbo" else 0)
+        self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode, flags)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

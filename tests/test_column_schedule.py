@@ -1,0 +1,181 @@
+"""A lane-level model of the column recursion kernel (csrc/delta_column.cu), run on the CPU.
+
+The model follows the kernel warp step by warp step: the task list (degree l, block b of 32
+columns, longest first), the first row from the lanes' factor products and the warp's suffix
+scan with split-off exponents, the chunk coefficients a(m'), b(m') made from the sqrt tables,
+the three-instruction update in the kernel's rounding order, the direct row writes and the
+transposed entries staged in a 32 x 33 block and flushed a chunk at a time, and the per-lane
+exponent of the scaled variant (band-limits above 1024).  Every table write is checked against
+the table's bounds and must land on an entry not written before; at the end every entry must
+have been written once, and the table must equal the oracle's (the Risbo recursion) to the
+tolerance the GPU tests use.  A change to the kernel's index arithmetic that breaks coverage or
+bounds shows up here before any GPU run."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import transforms as T
+
+
+def offset(l):
+    return l * (l + 1) * (2 * l + 1) // 6
+
+
+def tasks(L):
+    t = [(l, b) for l in range(L) for b in range(l // 32 + 1)]
+    t.sort(key=lambda x: -(x[0] - 32 * x[1]))  # Python's sort is stable, as std::stable_sort
+    return t
+
+
+def exp_of(v):
+    return math.frexp(v)[1] - 1  # unbiased exponent of a normal double
+
+
+def with_exp(v, e):
+    return math.ldexp(math.frexp(v)[0] * 2.0, e)
+
+
+def run_task(l, b, sq, rsq, table, written, scaled):
+    m0 = 32 * b
+    lanes = np.arange(32)
+    m = m0 + lanes
+    act = m <= l
+    # first row: lanes' products of every 32nd factor g(k), k >= m0 + 33
+    gm = np.ones(32)
+    for j in range(32):
+        k = m0 + 33 + j
+        while k <= l:
+            gm[j] = gm[j] * (sq[l + k] * rsq[l - k + 1])
+            k += 32
+    ge = np.array([exp_of(x) for x in gm])
+    gm = np.array([with_exp(x, 0) for x in gm])
+    for d in (16, 8, 4, 2, 1):
+        om, oe = gm[lanes ^ d], ge[lanes ^ d]
+        gm = gm * om
+        ge = ge + oe + np.array([exp_of(x) for x in gm])
+        gm = np.array([with_exp(x, 0) for x in gm])
+    h = np.where(m + 1 <= l, sq[np.minimum(l + m + 1, len(sq) - 1)] * rsq[np.maximum(l - m, 1)], 1.0)
+    for d in (1, 2, 4, 8, 16):
+        o = np.concatenate([h[d:], np.zeros(d)])
+        h = np.where(lanes + d < 32, h * o, h)
+    v = h * gm
+    E = np.zeros(32, dtype=np.int64)
+    cur = np.zeros(32)
+    for i in range(32):
+        if not act[i]:
+            continue
+        sgn = -1.0 if (l - m[i]) & 1 else 1.0
+        if not scaled or exp_of(v[i]) + ge[i] - l >= -1021:
+            cur[i] = sgn * math.ldexp(v[i], int(ge[i]) - l)
+        else:
+            cur[i] = sgn * v[i]
+            E[i] = ge[i] - l
+    prev = np.zeros(32)
+    m2 = 2.0 * m
+    base, row = offset(l), l + 1
+    stage = np.full((32, 33), np.nan)
+    coef = np.zeros(64)
+
+    def put(idx, val):
+        assert offset(l) <= idx < offset(l + 1), (l, idx)
+        assert not written[idx], ("written twice", l, idx)
+        written[idx] = True
+        table[idx] = val
+
+    for mp in range(l, m0 - 1, -1):
+        j = mp & 31
+        if mp == l or j == 31:
+            k = (mp & ~31) + lanes
+            ok = (k >= 1) & (k <= l)
+            kk = np.clip(k, 1, l if l >= 1 else 1)
+            a = np.where(ok, rsq[np.maximum(l - kk + 1, 1)] * rsq[l + kk], 0.0)
+            bb = np.where(ok, (sq[np.maximum(l - kk, 0)] * sq[l + kk + 1]) * a, 0.0)
+            coef[:32], coef[32:] = a, bb
+        out = np.where(E != 0, 0.0, cur) if scaled else cur.copy()
+        for i in range(32):
+            if act[i]:
+                put(base + mp * row + m[i], out[i])
+        if mp >= m0 + 32:
+            for i in range(32):
+                stage[i, j] = -out[i] if (mp - m[i]) & 1 else out[i]
+            if j == 0:
+                for r in range(32):
+                    if m0 + r > l:
+                        break
+                    for c in range(32):
+                        col = mp + c
+                        if col <= l:
+                            assert not math.isnan(stage[r, c]), "flush reads an unstaged slot"
+                            put(base + (m0 + r) * row + col, stage[r, c])
+                stage[:] = np.nan
+        if mp > m0:
+            c = m2 * coef[j]
+            t2 = coef[32 + j] * prev
+            nxt = c * cur - t2  # the kernel fuses this into one FMA; the model rounds twice
+            prev, cur = cur, nxt
+            if scaled:
+                for i in range(32):
+                    if E[i] == 0:
+                        continue
+                    x = exp_of(cur[i]) if cur[i] != 0 else -1100
+                    if x + E[i] >= -1021:
+                        cur[i] = math.ldexp(cur[i], int(E[i]))
+                        prev[i] = math.ldexp(prev[i], int(E[i]))
+                        E[i] = 0
+                    elif x > 512:
+                        cur[i] *= 2.0 ** -512
+                        prev[i] *= 2.0 ** -512
+                        E[i] += 512
+
+
+def model_table(L, scaled=None, degrees=None):
+    scaled = L > 1024 if scaled is None else scaled
+    nsq = 2 * L + 4
+    sq = np.sqrt(np.arange(nsq, dtype=np.float64))
+    rsq = np.zeros(nsq)
+    rsq[1:] = 1.0 / np.sqrt(np.arange(1, nsq, dtype=np.float64))
+    n = offset(L)
+    table = np.zeros(n)
+    written = np.zeros(n, dtype=bool)
+    for l, b in tasks(L):
+        if degrees is None or l in degrees:
+            run_task(l, b, sq, rsq, table, written, scaled)
+    return table, written
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 31, 32, 33, 65, 97])
+def test_column_model_covers_table_once_and_matches_oracle(L):
+    table, written = model_table(L)
+    assert written.all()
+    want = T.delta_quadrant(L)
+    assert np.abs(table - want).max() < 1e-13
+
+
+def test_column_model_scaled_variant_matches_oracle_at_small_L():
+    """The per-lane exponent path (used above L = 1024) gives the same table where nothing is out of range."""
+    L = 70
+    table, written = model_table(L, scaled=True)
+    assert written.all()
+    assert np.abs(table - T.delta_quadrant(L)).max() < 1e-13
+
+
+def test_task_list_is_longest_first_and_complete():
+    L = 300
+    t = tasks(L)
+    lengths = [l - 32 * b + 1 for l, b in t]
+    assert lengths == sorted(lengths, reverse=True)
+    assert len(t) == sum(l // 32 + 1 for l in range(L))
+    assert len(set(t)) == len(t)
+
+
+@pytest.mark.slow
+def test_column_model_scaled_high_degree_matches_oracle():
+    """Degree 1500 of a band-limit above 1024: first-row entries below 2^-1022 start with an exponent."""
+    l = 1500
+    L = l + 1
+    table, written = model_table(L, degrees={l})
+    got = table[offset(l):offset(l + 1)].reshape(l + 1, l + 1)
+    assert written[offset(l):offset(l + 1)].all()
+    full = T.wigner_full(2 * l)
+    assert np.abs(got - full[l:, l:]).max() < 5e-13

@@ -53,6 +53,48 @@ def test_group_matches_oracle_per_field(precision, tune, tol):
         assert rel(As[i].cpu().numpy(), T.adjoint(fi.astype(np.complex128), L, s)) < tol
 
 
+def config4_case(per_bucket=2, seed=0):
+    """The uneven-batch configuration at its own band-limits, scaled down in count: every (L, s)
+    bucket with L in {128, 256, 512, 1024} and s in {0, +-1, +-2} holds `per_bucket` fields,
+    Re/Im iid N(0,1), in a shuffled caller order."""
+    rng = np.random.default_rng(seed)
+    pairs = [(L, s) for L in (128, 256, 512, 1024) for s in (0, 1, -1, 2, -2)] * per_bucket
+    order = rng.permutation(len(pairs))
+    Ls = [pairs[i][0] for i in order]
+    ss = [pairs[i][1] for i in order]
+    flms = [inputs.coeffs(L, s, 1, seed=seed * 1000 + i)[0] for i, (L, s) in enumerate(zip(Ls, ss))]
+    return Ls, ss, flms
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tune", [("fp32", True), ("tf32x3", False)])
+def test_group_at_uneven_batch_band_limits(precision, tune):
+    """Shared Delta per L, per-bucket streams, the tuner's choice and the graph replay at the
+    uneven batch's own band-limits: every field of the L <= 256 buckets and the first field of
+    every L = 512 and L = 1024 bucket, inverse (from the graph), forward and adjoint."""
+    Ls, ss, flms = config4_case()
+    g = S().Group(Ls, ss, precision=precision, tune=tune)
+    dt = g.dtype
+    flat = g.pack_coeffs([torch.from_numpy(x).to(dt).cuda() for x in flms])
+    f_s, b_s = g.empty_grid(), g.empty_coeffs()
+    g.capture(flat, f_s, b_s)
+    g.replay()
+    adj = g.adjoint(f_s)
+    g.check()
+    fs, bs, As = g.unpack_grid(f_s), g.unpack_coeffs(b_s), g.unpack_coeffs(adj)
+    seen = set()
+    for i, (L, s) in enumerate(zip(Ls, ss)):
+        if L > 256 and (L, s) in seen:
+            continue
+        seen.add((L, s))
+        fi = fs[i].cpu().numpy()
+        assert rel(fi, T.inverse(flms[i], L, s)) < 2e-6, ("inverse", L, s)
+        g64 = fi.astype(np.complex128)
+        assert rel(bs[i].cpu().numpy(), T.forward(g64, L, s)) < 2e-6, ("forward", L, s)
+        assert rel(As[i].cpu().numpy(), T.adjoint(g64, L, s)) < 2e-6, ("adjoint", L, s)
+    assert len(seen) == 20
+
+
 def test_group_graph_replay_and_cache_mode():
     Ls, ss, flms = make_case(n=16, seed=1)
     g = S().Group(Ls, ss, precision="fp32", tune=True)

@@ -41,9 +41,13 @@ def random_grid(L, B, seed):
     return rng.standard_normal((B, L, 2 * L - 1)) + 1j * rng.standard_normal((B, L, 2 * L - 1))
 
 
-@pytest.mark.parametrize("L", [1, 2, 3, 8, 33, 100, 257])
-def test_delta_table_matches_oracle(L):
-    plan = S().Plan(L, 0, 1)
+RECURSIONS = ["column", "risbo"]
+
+
+@pytest.mark.parametrize("recursion", RECURSIONS)
+@pytest.mark.parametrize("L", [1, 2, 3, 8, 32, 33, 64, 65, 100, 257])
+def test_delta_table_matches_oracle(L, recursion):
+    plan = S().Plan(L, 0, 1, recursion=recursion)
     got = plan.wigner_delta().cpu().numpy()
     plan.check()
     want = T.delta_quadrant(L)
@@ -51,14 +55,52 @@ def test_delta_table_matches_oracle(L):
     assert np.abs(got - want).max() < 1e-13
 
 
-def test_delta_table_top_degrees_at_L1024():
+@pytest.mark.parametrize("recursion", RECURSIONS)
+def test_delta_table_top_degrees_at_L1024(recursion):
     L = 1024
-    plan = S().Plan(L, 0, 1)
+    plan = S().Plan(L, 0, 1, recursion=recursion)
     tab = plan.wigner_delta().cpu().numpy()
     plan.check()
     for l in (1023, 640):
         full = T.wigner_full(2 * l)
         assert np.abs(T.delta_slab(tab, l) - full[l:, l:]).max() < 5e-13
+
+
+def test_delta_table_degrees_of_L2048():
+    """Band-limit 2048 (the column method's scaled variant: first-row entries of high degrees are
+    below the FP64 normal range and start with a per-lane exponent): whole degrees against the
+    oracle's full-matrix Risbo recursion, copied off the 22.9 GB device table one degree at a time."""
+    L = 2048
+    plan = S().Plan(L, 0, 1)
+    tab = plan.wigner_delta()
+    plan.check()
+    off = T.delta_offsets(L)
+    for l in (1100, 2047):
+        got = tab[int(off[l]):int(off[l + 1])].cpu().numpy().reshape(l + 1, l + 1)
+        full = T.wigner_full(2 * l)
+        assert np.abs(got - full[l:, l:]).max() < 5e-13
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("tf32x3", 1e-6)])
+def test_transforms_with_the_risbo_recursion(precision, tol):
+    """Plans with SSHT_FLAG_RISBO (the paper's recursion) give the oracle's transforms too, and
+    agree with the default plans to rounding."""
+    L, s, B = 97, 2, 3
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    flm = inputs.coeffs(L, s, B, seed=17)
+    a = S().Plan(L, s, B, precision=precision, recursion="risbo")
+    b = S().Plan(L, s, B, precision=precision)
+    fa = a.inverse(dev(flm, dt))
+    ba = a.forward(fa).cpu().numpy()
+    fb = b.inverse(dev(flm, dt)).cpu().numpy()
+    a.check()
+    b.check()
+    fa = fa.cpu().numpy()
+    for k in range(B):
+        f_or = T.inverse(flm[k], L, s)
+        assert rel(fa[k], f_or) < tol
+        assert rel(ba[k], T.forward(fa[k].astype(np.complex128), L, s)) < tol
+    assert rel(fa, fb) < tol
 
 
 @pytest.mark.parametrize("L,s,B", [(1, 0, 1), (2, 0, 1), (2, 1, 2), (5, 0, 3), (8, 2, 1), (8, -2, 2), (17, 3, 1),

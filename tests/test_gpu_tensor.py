@@ -38,10 +38,23 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(torch.complex64).cuda()
 
 
+def check_fields(flm, f, back, adj, L, s, fields):
+    """Every listed field of the batch against the oracle, element by element: the packing puts
+    field b in columns 2b, 2b+1 of each sign half, so a column-index error in any one field (or
+    two swapped fields) fails here."""
+    f_all = T.inverse(flm[list(fields)], L, s)
+    g = f[list(fields)].astype(np.complex128)
+    fwd_all, adj_all = T.forward(g, L, s), T.adjoint(g, L, s)
+    for k, b in enumerate(fields):
+        assert rel(f[b], f_all[k]) < TOL_SPLIT, ("inverse", b)
+        assert rel(back[b], fwd_all[k]) < TOL_SPLIT, ("forward", b)
+        assert rel(adj[b], adj_all[k]) < TOL_SPLIT, ("adjoint", b)
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("L,s,B,spectrum", [(1, 0, 1, "flat"), (16, 0, 1, "flat"), (33, 2, 3, "flat"),
                                             (100, -1, 16, "cmb"), (129, 3, 5, "flat"), (200, 2, 64, "cmb"),
-                                            (257, 130, 2, "flat")])
+                                            (256, -2, 64, "flat"), (257, 130, 2, "flat")])
 def test_split_matches_oracle(precision, L, s, B, spectrum):
     flm = inputs.coeffs(L, s, B, seed=L, spectrum=spectrum)
     plan = S().Plan(L, s, B, precision=precision)
@@ -49,12 +62,22 @@ def test_split_matches_oracle(precision, L, s, B, spectrum):
     back = plan.forward(f).cpu().numpy()
     adj = plan.adjoint(f).cpu().numpy()
     plan.check()
-    f = f.cpu().numpy()
-    for b in sorted({0, B - 1}):
-        f_or = T.inverse(flm[b], L, s)
-        assert rel(f[b], f_or) < TOL_SPLIT
-        assert rel(back[b], T.forward(f[b].astype(np.complex128), L, s)) < TOL_SPLIT
-        assert rel(adj[b], T.adjoint(f[b].astype(np.complex128), L, s)) < TOL_SPLIT
+    check_fields(flm, f.cpu().numpy(), back, adj, L, s, range(B))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_headline_batch_every_eighth_field(precision):
+    """The headline workload, L = 1024, s = 2, B = 64, CMB-like spectrum: fields 0, 8, ..., 56 and
+    63 against the oracle in all three directions."""
+    L, s, B = 1024, 2, 64
+    flm = inputs.coeffs(L, s, B, seed=0, spectrum="cmb")
+    plan = S().Plan(L, s, B, precision=precision)
+    f = plan.inverse(dev(flm))
+    back = plan.forward(f).cpu().numpy()
+    adj = plan.adjoint(f).cpu().numpy()
+    plan.check()
+    check_fields(flm, f.cpu().numpy(), back, adj, L, s, list(range(0, B, 8)) + [B - 1])
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)

@@ -40,8 +40,9 @@ def _noalloc(L):
 
 
 def _with_plan(L):
+    """The same table from the plan entry point, made with the same (Risbo) recursion."""
     ssht, _ = _lib()
-    plan = ssht.Plan(L, 0, 1)
+    plan = ssht.Plan(L, 0, 1, recursion="risbo")
     ref = plan.wigner_delta()
     plan.check()
     return ref
