@@ -102,6 +102,7 @@ struct ssht_plan_s {
   void* stage_out = nullptr;
   size_t stage_out_bytes = 0;
   bool delta_ready = false;
+  bool u_fixed = false;  // U / Uf made once at creation (3xTF32 plans with the recursion writing the A tiles)
   size_t bytes = 0;
   TcPlan* tc = nullptr;    // tensor-core contraction (precisions SSHT_TF32X3, SSHT_BF16X6)
   TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
@@ -243,15 +244,38 @@ int set_streams(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
+int pack_a(ssht_plan_t p, int forward, cudaStream_t st);
+
 int run_delta(ssht_plan_t p, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_DELTA, st);
   if (!p->delta_shared) {
     SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
     p->launches += 1;
   }
-  SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, p->Uf, st), "spin column launch");
-  p->launches += 1;
+  if (!p->u_fixed) {
+    SSHT_CUDA(delta_spin_column(p->delta.table, p->d.L, p->s, p->U, p->Uf, st), "spin column launch");
+    p->launches += 1;
+  }
   return 0;
+}
+
+// 3xTF32 plans that run their own column recursion make the A tiles in the recursion itself
+// (no FP64 table, no packing); U, the spin column, is then made once at plan creation.
+bool tiles_direct(const ssht_plan_s* p) {
+  return p->tc && tc_a_tiles(p->tc).A && !p->delta_shared && p->delta.method == kDeltaColumn;
+}
+
+// Delta and the contraction's A operand of one direction, on st.
+int make_operands(ssht_plan_t p, int forward, cudaStream_t st) {
+  if (tiles_direct(p)) {
+    StageScope sc(p, SSHT_STAGE_DELTA, st);
+    SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
+    p->launches += 1;
+    return 0;
+  }
+  int rc = run_delta(p, st);
+  if (rc) return rc;
+  return p->tc ? pack_a(p, forward, st) : 0;
 }
 
 int pack_a(ssht_plan_t p, int forward, cudaStream_t st) {
@@ -320,9 +344,8 @@ int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
     SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork wait");
   }
   if (p->delta_shared && p->delta_event) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->delta_event, 0), "shared Delta wait");
-  int rc = run_delta(p, p->aux);
+  int rc = make_operands(p, forward, p->aux);
   if (rc) return rc;
-  if (p->tc && (rc = pack_a(p, forward, p->aux))) return rc;
   SSHT_CUDA(cudaEventRecord(p->ev_join, p->aux), "join event");
   p->join_pending = true;
   return 0;
@@ -736,9 +759,24 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     }
     p->bytes += tc_bytes(p->tc);
   }
-  if (p->delta_mode == SSHT_DELTA_CACHE) {
+  if (tiles_direct(p)) {
+    // the spin column once: the table of one sweep, then U from it
     if ((rc = run_delta(p, 0))) return bail(rc);
-    if (p->tc && ((rc = pack_a(p, 0, 0)) || (rc = pack_a(p, 1, 0)))) return bail(rc);
+    p->u_fixed = true;
+    // the calls' recursions run on the plan's non-blocking stream: U must be complete first
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) {
+      release(p);
+      return fail(SSHT_ECUDA, std::string("spin column: ") + cudaGetErrorString(ce));
+    }
+  }
+  if (p->delta_mode == SSHT_DELTA_CACHE) {
+    if (tiles_direct(p)) {
+      if ((rc = make_operands(p, 1, 0))) return bail(rc);
+    } else {
+      if ((rc = run_delta(p, 0))) return bail(rc);
+      if (p->tc && ((rc = pack_a(p, 0, 0)) || (rc = pack_a(p, 1, 0)))) return bail(rc);
+    }
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) {
       release(p);

@@ -33,6 +33,7 @@
 // the CTAs.  Every wait is bounded; a
 // timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
 #include "ssht_internal.h"
+#include "f32_round.h"
 #include "tc_common.cuh"
 
 #include <algorithm>
@@ -43,10 +44,10 @@ namespace {
 
 using namespace tc;
 
-constexpr int TM = 128;                    // rows per tile
-constexpr int TK = 32;                     // K per chunk (one 128-byte TF32 row)
-constexpr int A_PART = TM * TK * 4;        // 16 KB: one split part of an A tile
-constexpr int A_TILE = 2 * A_PART;         // hi then lo
+constexpr int TM = kTileRows;              // rows per tile
+constexpr int TK = kTileK;                 // K per chunk (one 128-byte TF32 row)
+constexpr int A_PART = kAPart;             // 16 KB: one split part of an A tile
+constexpr int A_TILE = kATile;             // hi then lo
 constexpr int STAGES = 2;
 constexpr int EPI_WARPS = 8;                       // two per tensor-memory lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer warp, MMA warp, epilogue warps
@@ -65,6 +66,7 @@ struct TcArgs {
   int nitems;
   const Item* items;
   const uint8_t* A;       // packed A tiles
+  const long long* abase; // MN inverse: per m, the index of the forward tile (m, m / 128, 0)
   const uint8_t* X;       // packed data tiles
   const long long* xoff;  // per m: data tile index of chunk xc0(m)
   const int* xc0;         // per m: first chunk stored for m
@@ -84,21 +86,6 @@ __device__ __forceinline__ float2 ipow_signed(int s, int k) {
 // ---------------------------------------------------------------------------------------------
 // Packing: A tiles from the FP64 Delta table
 // ---------------------------------------------------------------------------------------------
-
-// FP64 -> FP32, round to nearest even, by integer operations on the bit pattern (IEEE 754
-// rounding; the FP64 pipe is the scarce one on this part): adding 2^28 - 1 plus the lowest kept
-// bit to the pattern rounds the 29 dropped fraction bits to nearest even, a carry moving into the
-// exponent as rounding requires; the exponent is then rebiased from 1023 to 127.  |x| below the
-// FP32 normal range becomes a signed zero; |x| must stay below 2^128 (entries here are at most ~13
-// in magnitude).
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned long long t = b + 0x0FFFFFFFull + ((lo >> 29) & 1u);
-  const unsigned mag = ((unsigned)(t >> 29) - (896u << 23)) & 0x7FFFFFFFu;
-  const unsigned sign = hi & 0x80000000u;
-  return __uint_as_float(((hi >> 20) & 0x7FFu) <= 896u ? sign : (sign | mag));
-}
 
 // Inverse A tile (m, i, c): rows m' = 128 i + r, columns l = 32 c + k (K-major).
 // Forward A tile (m, i, c): rows l = 128 i + r, columns m' = 32 c + k.
@@ -208,8 +195,13 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
   for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-template <bool FWD, bool BF>
+// MN (inverse, 3xTF32 only): the A operand is read from the forward tiles (rows l, K = m') as an
+// MN-major operand -- for the chunk of l in [32 kc, 32 kc + 32) of item (m, row block i'), the
+// 32-row slices (rows l mod 128) of the forward tiles (m, kc / 4, 4 i' + c'), c' < 4, each four
+// 1 KB swizzle atoms of 8 rows (K) x 128 bytes (32 m'), laid side by side along M.
+template <bool FWD, bool BF, bool MN>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
+  static_assert(!MN || (!FWD && !BF), "the MN-major A operand serves the 3xTF32 inverse");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int b_part = a.NC * 128;
@@ -255,7 +247,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
           }
           uint8_t* st = smem + s * stage_bytes;
           mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-          bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
+          if constexpr (MN) {
+            const int il = c >> 2, im = itm.m / TM;
+            const long long t0 = a.abase[itm.m] + 2ll * il * (il + 1) - 2ll * im * (im + 1) + 4ll * itm.i;
+            for (int cc = 0; cc < 4; ++cc)
+              for (int part = 0; part < 2; ++part)
+                bulk_g2s(st + part * A_PART + cc * 4096,
+                         a.A + (size_t)(t0 + cc) * A_TILE + part * A_PART + (size_t)(c & 3) * 4096, 4096, &full[s]);
+          } else {
+            bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
+          }
           const long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
           bulk_g2s(st + A_TILE, a.X + (size_t)xt * 2 * b_part, (uint32_t)(2 * b_part), &full[s]);
           last_use[s] = u;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer: one tensor-memory segment per chunk, corrections first ----
-      const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : idesc_tf32(TM, a.NC);
+      const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : (idesc_tf32(TM, a.NC) | (MN ? kTransposeA : 0u));
       int it = 0;
       for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
         const Item itm = a.items[w];
@@ -298,16 +299,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
                 mma_bf16(dt, desc_sw128(sa + oa[pa[q]] + kk * 32), desc_sw128(sb + ob[pb[q]] + kk * 32), idesc,
                          (q == 0 && kk == 0) ? 0u : 1u);
           } else {
+            // A: K-major (K step kk at byte 32 kk of each row) or MN-major (K step kk = atom kk)
+            auto ad = [&](uint32_t base, int kk) {
+              return MN ? desc_mn_sw128(base + kk * 1024, 4096, 1024) : desc_sw128(base + kk * 32);
+            };
 #pragma unroll
             for (int kk = 0; kk < TK / 8; ++kk) {
               const uint32_t ko = kk * 32;
-              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
-              mma_tf32(dt, desc_sw128(sa + A_PART + ko), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
+              mma_tf32(dt, ad(sa, kk), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
+              mma_tf32(dt, ad(sa + A_PART, kk), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
             }
 #pragma unroll
             for (int kk = 0; kk < TK / 8; ++kk) {
               const uint32_t ko = kk * 32;
-              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
+              mma_tf32(dt, ad(sa, kk), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
             }
           }
           mma_commit(&empty[s]);
@@ -396,9 +401,15 @@ struct TcPlan {
   Item* items_inv = nullptr;
   Item* items_fwd = nullptr;
   int n_inv = 0, n_fwd = 0;
-  long long tiles_inv = 0, tiles_fwd = 0, xtiles_inv = 0, xtiles_fwd = 0;
+  long long tiles_A = 0, tiles_inv = 0, xtiles_inv = 0, xtiles_fwd = 0;
+  // Forward A tiles (m, i, c): rows l = 128 i + r, K = m' = 32 c + k, tile index abase[m] +
+  // 2i(i+1) - 2 i_m(i_m+1) + c with i_m = m / 128 (each (m, i), i >= i_m, holds 4i + 4 slots, so
+  // that the four 32-wide m' chunks of every 128-row m' block of the inverse exist; slots and
+  // entries nothing writes stay zero).  3xTF32: both directions read these (the inverse as an
+  // MN-major operand).  Split-BF16: the inverse has its own K-major tiles A_inv.
+  uint8_t* A = nullptr;
   uint8_t* A_inv = nullptr;
-  uint8_t* A_fwd = nullptr;
+  long long* abase = nullptr;
   uint8_t* X = nullptr;  // data tiles (shared by both directions; sized for the larger)
   long long* xoff = nullptr;
   int* xc0 = nullptr;
@@ -411,6 +422,12 @@ static cudaError_t tc_alloc(void** p, size_t bytes, size_t* total) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e == cudaSuccess) *total += bytes;
   return e;
+}
+
+template <class K>
+static cudaError_t gemm_attrs(K kernel, int bytes) {
+  cudaError_t e = prefer_shared(kernel);
+  return e != cudaSuccess ? e : cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
@@ -426,26 +443,26 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   p->nI = (L + TM - 1) / TM;
   const int as = s < 0 ? -s : s;
   std::vector<Item> inv, fwd;
-  std::vector<long long> xoff(L);
+  std::vector<long long> xoff(L), abase(L);
   std::vector<int> xc0(L);
   long long at = 0, ft = 0, xt = 0;
   for (int m = 0; m < L; ++m) {
-    const int lmin = std::max(m, as);
+    const int lmin = std::max(m, as), im = m / TM;
     xc0[m] = lmin / TK;
     xoff[m] = xt;
     xt += p->nC - xc0[m];
+    abase[m] = ft;
+    for (int i = im; i < p->nI; ++i) {
+      // forward: rows l in block i with l >= m (rows l < |s| come out as zeros), K = m' <= l
+      fwd.push_back({m, i, 0, std::min(p->nC, 4 * i + 4), ft});
+      ft += 4 * i + 4;
+    }
     for (int i = 0; i < p->nI; ++i) {
       // inverse: rows m' in block i, K = l >= max(m, m', |s|)
       const int c0 = std::max(lmin / TK, (i * TM) / TK);
-      if (i * TM <= L - 1 && c0 < p->nC) {
+      if (c0 < p->nC) {
         inv.push_back({m, i, c0, p->nC, at});
         at += p->nC - c0;
-      }
-      // forward: rows l in block i with l >= m (rows l < |s| come out as zeros), K = m' <= l
-      if ((i + 1) * TM > m && i * TM <= L - 1) {
-        const int c1 = std::min(p->nC, ((i + 1) * TM + TK - 1) / TK);
-        fwd.push_back({m, i, 0, c1, ft});
-        ft += c1;
       }
     }
   }
@@ -464,21 +481,24 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   std::stable_sort(fwd.begin(), fwd.end(), longest_first);
   p->n_inv = (int)inv.size();
   p->n_fwd = (int)fwd.size();
+  p->tiles_A = ft;
   p->tiles_inv = at;
-  p->tiles_fwd = ft;
   p->xtiles_inv = xt;
   p->xtiles_fwd = (long long)L * p->nC;
   cudaError_t e;
   const size_t xbytes = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * 2 * p->NC * 128;
   if ((e = tc_alloc((void**)&p->items_inv, inv.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = tc_alloc((void**)&p->A_fwd, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->A, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = cudaMemset(p->A, 0, (size_t)ft * A_TILE)) != cudaSuccess) goto fail;
+  if (p->bf16 && (e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->abase, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xoff, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xc0, L * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->items_inv, inv.data(), inv.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->items_fwd, fwd.data(), fwd.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->abase, abase.data(), L * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->xoff, xoff.data(), L * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->xc0, xc0.data(), L * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   {
@@ -489,20 +509,17 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
     // Function attributes are process-wide upper bounds: set them for the largest column count
     // (NC = 256) so that plans of other batch sizes can launch with their own amounts.
     const int gemm_max = STAGES * (A_TILE + 2 * 256 * 128) + 1024, xsmem_max = 2 * 256 * 128;
-    if ((e = prefer_shared(tc_gemm_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, true>)) != cudaSuccess ||
-        (e = prefer_shared(tc_gemm_kernel<false, false>)) != cudaSuccess || (e = prefer_shared(tc_gemm_kernel<true, false>)) != cudaSuccess ||
-        (e = prefer_shared(pack_v_kernel<true>)) != cudaSuccess || (e = prefer_shared(pack_v_kernel<false>)) != cudaSuccess ||
-        (e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
+    if ((e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
         (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
       goto fail;
     if (p->bf16) {
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_v_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, true, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, true, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(pack_v_kernel<true>, xsmem_max)) != cudaSuccess) goto fail;
     } else {
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = cudaFuncSetAttribute(pack_v_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, false, true>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, false, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(pack_v_kernel<false>, xsmem_max)) != cudaSuccess) goto fail;
     }
   }
   *out = p;
@@ -514,7 +531,7 @@ fail:
 
 void tc_destroy(TcPlan* p) {
   if (!p) return;
-  void* ptrs[] = {p->items_inv, p->items_fwd, p->A_inv, p->A_fwd, p->X, p->xoff, p->xc0};
+  void* ptrs[] = {p->items_inv, p->items_fwd, p->A, p->A_inv, p->abase, p->X, p->xoff, p->xc0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -522,17 +539,26 @@ void tc_destroy(TcPlan* p) {
 
 size_t tc_bytes(const TcPlan* p) { return p ? p->bytes : 0; }
 
+ATiles tc_a_tiles(const TcPlan* p) {
+  ATiles t;
+  if (p && !p->bf16) {
+    t.A = p->A;
+    t.abase = p->abase;
+  }
+  return t;
+}
+
 cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* U, cudaStream_t st, int* launches) {
+  // 3xTF32: one set of tiles serves both directions, the forward layout
+  if (!p->bf16) forward = 1;
   // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
   const dim3 gf(p->nC, p->n_fwd), gi(p->nC, p->n_inv);
   if (forward && p->bf16)
-    pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
+    pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
   else if (forward)
-    pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A_fwd);
-  else if (p->bf16)
-    pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+    pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
   else
-    pack_a_kernel<false, false><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+    pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -565,7 +591,8 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.NC = p->NC;
   a.nitems = forward ? p->n_fwd : p->n_inv;
   a.items = forward ? p->items_fwd : p->items_inv;
-  a.A = forward ? p->A_fwd : p->A_inv;
+  a.A = (forward || !p->bf16) ? p->A : p->A_inv;
+  a.abase = p->abase;
   a.X = p->X;
   a.xoff = p->xoff;
   a.xc0 = p->xc0;
@@ -574,13 +601,13 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.status = status;
   const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
   if (forward && p->bf16)
-    tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<true, true, false><<<grid, THREADS, p->smem, st>>>(a);
   else if (forward)
-    tc_gemm_kernel<true, false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<true, false, false><<<grid, THREADS, p->smem, st>>>(a);
   else if (p->bf16)
-    tc_gemm_kernel<false, true><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<false, true, false><<<grid, THREADS, p->smem, st>>>(a);
   else
-    tc_gemm_kernel<false, false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<false, false, true><<<grid, THREADS, p->smem, st>>>(a);
   *launches += 1;
   return cudaGetLastError();
 }

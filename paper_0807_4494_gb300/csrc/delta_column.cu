@@ -29,6 +29,8 @@
 // value is back in range; entries below 2^-1021 are written as 0 (they are below 1e-307 and
 // contribute nothing to any transform).
 #include "ssht_internal.h"
+#include "f32_round.h"
+#include "tc_common.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -53,7 +55,20 @@ struct ColumnParams {
   const double* rsq;       // 1/sqrt(k), k >= 1
   double* table;           // quadrant table, entry (l, m', m) at offset(l) + m'(l+1) + m
   unsigned int* counter;   // next task (zeroed before the launch)
+  // tile output (3xTF32 plans): A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} into the forward tile layout
+  const float* Uf;         // U_l[m'] in FP32 at l(l+1)/2 + m'
+  uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m', hi then lo
+  const long long* abase;  // per m: index of the tile (m, m / 128, 0)
 };
+
+// Writes A_M[l][K] = x (already in FP32) split hi + lo into row l mod 128 of tile (M, l / 128, K / 32).
+__device__ __forceinline__ void put_a(uint8_t* A, long long tile, int row, int k, float x) {
+  float hi, lo;
+  tc::split_tf32(x, &hi, &lo);
+  uint8_t* t = A + (size_t)tile * tc::kATile;
+  *(float*)(t + tc::sw128(row, 4 * k)) = hi;
+  *(float*)(t + tc::kAPart + tc::sw128(row, 4 * k)) = lo;
+}
 
 __device__ __forceinline__ double flip_sign(double v, bool neg) {
   return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
@@ -66,7 +81,12 @@ __device__ __forceinline__ double with_exp(double v, int e) {
   return __hiloint2double(hi, __double2loint(v));
 }
 
-template <bool SCALED>
+// TILES: write the A tiles of a 3xTF32 plan instead of the table.  With x = Delta_{m'm} in lane m
+// at step m' (row), the entry serves two tiles: A_{m'}[l][m] = U_l[m] (-1)^{m'-m} x, a row of 32
+// consecutive K values across the warp (written at once), for every row m' >= 32b; and A_m[l][m']
+// = U_l[m'] x, which goes through the transposition block like the table's transposed entries,
+// for m' >= 32b + 32 -- together every (M, K) pair of the degree once.
+template <bool SCALED, bool TILES>
 __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(ColumnParams P) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -120,8 +140,19 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
     }
     double prev = 0.0;
     const double m2 = 2.0 * (double)m;
-    double* __restrict__ T = P.table + delta_offset_dev(l);
+    double* __restrict__ T = TILES ? nullptr : P.table + delta_offset_dev(l);
     const size_t row = (size_t)l + 1;
+    // tile output: row l mod 128 of the tiles of row block il; U_l[m] of this lane's column and
+    // the tile base of its row M = m (for the transposed writes)
+    const int il = l >> 7, trow = l & 127;
+    const long long ilpre = 2ll * il * (il + 1);
+    float u_lane = 0.f;
+    long long base_lane = 0;
+    if (TILES && act) {
+      u_lane = __ldg(&P.Uf[(size_t)l * (l + 1) / 2 + m]);
+      const int im = m >> 7;
+      base_lane = __ldg(&P.abase[m]) + ilpre - 2ll * im * (im + 1);
+    }
 
     // ---- rows m' = l .. m0 ----
     for (int mp = l; mp >= m0; --mp) {
@@ -140,15 +171,32 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
         __syncwarp();
       }
       const double out = (SCALED && E != 0) ? 0.0 : cur;
-      if (act) T[(size_t)mp * row + m] = out;
+      if constexpr (TILES) {
+        if (act) {
+          const int im = mp >> 7;
+          const long long tile = __ldg(&P.abase[mp]) + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
+          put_a(P.A, tile, trow, lane, u_lane * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
+        }
+      } else {
+        if (act) T[(size_t)mp * row + m] = out;
+      }
       if (mp >= m0 + 32) {
-        // transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}, written a 32-column chunk at a time
-        stage[lane * 33 + j] = flip_sign(out, ((mp - m) & 1) != 0);
+        // table: transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}; tiles: A_m[l][m'] =
+        // U_l[m'] Delta_{m'm}; either way written a 32-column chunk at a time
+        stage[lane * 33 + j] = TILES ? out : flip_sign(out, ((mp - m) & 1) != 0);
         if (j == 0) {
           __syncwarp();
           const int c = mp + lane;
-          for (int r = 0; r < 32 && m0 + r <= l; ++r)
-            if (c <= l) T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
+          if constexpr (TILES) {
+            const float uc = c <= l ? __ldg(&P.Uf[(size_t)l * (l + 1) / 2 + c]) : 0.f;
+            for (int r = 0; r < 32 && m0 + r <= l; ++r) {
+              const long long tile = __shfl_sync(0xffffffffu, base_lane, r) + (mp >> 5);
+              if (c <= l) put_a(P.A, tile, trow, lane, uc * f64_to_f32_rn(stage[r * 33 + lane]));
+            }
+          } else {
+            for (int r = 0; r < 32 && m0 + r <= l; ++r)
+              if (c <= l) T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
+          }
           __syncwarp();
         }
       }
@@ -192,12 +240,15 @@ cudaError_t column_setup(DeltaWork& w, int L, int device) {
   int sms = 0, per_sm = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
   const bool scaled = L > 1024;
-  const void* fn = scaled ? (const void*)column_recursion_kernel<true> : (const void*)column_recursion_kernel<false>;
-  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kColThreads, kColSmem)) != cudaSuccess) return e;
+  const void* fns[2] = {scaled ? (const void*)column_recursion_kernel<true, false> : (const void*)column_recursion_kernel<false, false>,
+                        scaled ? (const void*)column_recursion_kernel<true, true> : (const void*)column_recursion_kernel<false, true>};
+  for (const void* fn : fns) {
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)) !=
+        cudaSuccess)
+      return e;
+  }
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[1], kColThreads, kColSmem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const std::vector<int2> tasks = column_tasks(L);
   w.method = kDeltaColumn;
@@ -221,7 +272,7 @@ cudaError_t column_setup(DeltaWork& w, int L, int device) {
   return cudaMemcpy(w.sqrt_tab, sqv.data(), sqv.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
-cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) {
+static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   ColumnParams P;
@@ -232,11 +283,26 @@ cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) {
   P.rsq = w.sqrt_tab + (2 * (size_t)L + 4);
   P.table = w.table;
   P.counter = w.barrier;
-  if (L > 1024)
-    column_recursion_kernel<true><<<w.blocks, w.threads, w.smem, st>>>(P);
+  P.Uf = Uf;
+  P.A = t.A;
+  P.abase = t.abase;
+  const bool tiles = t.A != nullptr;
+  if (L > 1024 && tiles)
+    column_recursion_kernel<true, true><<<w.blocks, w.threads, w.smem, st>>>(P);
+  else if (L > 1024)
+    column_recursion_kernel<true, false><<<w.blocks, w.threads, w.smem, st>>>(P);
+  else if (tiles)
+    column_recursion_kernel<false, true><<<w.blocks, w.threads, w.smem, st>>>(P);
   else
-    column_recursion_kernel<false><<<w.blocks, w.threads, w.smem, st>>>(P);
+    column_recursion_kernel<false, false><<<w.blocks, w.threads, w.smem, st>>>(P);
   return cudaGetLastError();
+}
+
+cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) { return column_launch(w, L, nullptr, ATiles(), st); }
+
+cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st) {
+  if (!t.A || !t.abase || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;
+  return column_launch(w, L, Uf, t, st);
 }
 
 }  // namespace ssht

@@ -126,6 +126,16 @@ struct TileOut {
   int NC = 0, nC = 0, mode = 0;
 };
 TileOut tc_forward_tiles(const TcPlan* p);
+// Where the recursion can write the A operand itself (3xTF32 plans): the forward tile array and
+// its per-m tile index base; A is null for split-BF16 plans (their A comes from tc_pack_a).
+struct ATiles {
+  uint8_t* A = nullptr;
+  const long long* abase = nullptr;
+};
+ATiles tc_a_tiles(const TcPlan* p);
+// The column recursion writing the A tiles of a 3xTF32 plan directly (no FP64 table):
+// A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, split hi + lo (delta_column.cu).
+cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Fused torus passes of FP32 plans (torus_pass.cu)

@@ -11,6 +11,11 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// A-operand tiles of the contraction: 128 rows x 32 K values, two split parts of 16 KB each.
+constexpr int kTileRows = 128, kTileK = 32;
+constexpr int kAPart = kTileRows * kTileK * 4;
+constexpr int kATile = 2 * kAPart;
+
 // Byte offset of element (row, kbyte) in a K-major tile with 128-byte rows in the SWIZZLE_128B
 // layout: 8-row x 128-byte atoms stacked along rows, the 16-byte chunk c of row r stored at
 // chunk c ^ (r mod 8).  Tiles start on 1024-byte boundaries.
@@ -29,6 +34,22 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
+
+// Shared-memory descriptor of an MN-major operand in the SWIZZLE_128B layout: swizzle atoms of
+// 8 rows along K x 128 bytes along M (or N), `lbo` bytes from one atom to the next along M,
+// `sbo` bytes from one group of 8 K rows to the next.
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction-descriptor bit that marks the A operand MN-major ("transpose A").
+constexpr uint32_t kTransposeA = 1u << 15;
 
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
 __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {

@@ -179,3 +179,101 @@ def test_column_model_scaled_high_degree_matches_oracle():
     assert written[offset(l):offset(l + 1)].all()
     full = T.wigner_full(2 * l)
     assert np.abs(got - full[l:, l:]).max() < 5e-13
+
+
+# ---- the tile output of 3xTF32 plans ---------------------------------------------------------
+
+def a_layout(L):
+    """The forward A-tile layout of the tensor-core plans (contract_tc.cu tc_setup): per m the
+    index of tile (m, m // 128, 0), and the forward items (m, i, c1, first tile)."""
+    nC, nI = (L + 31) // 32, (L + 127) // 128
+    abase, items, ft = [], [], 0
+    for m in range(L):
+        abase.append(ft)
+        for i in range(m // 128, nI):
+            items.append((m, i, min(nC, 4 * i + 4), ft))
+            ft += 4 * i + 4
+    return abase, items, ft
+
+
+def tile_index(abase, M, il, c):
+    im = M // 128
+    assert il >= im and 0 <= c < 4 * il + 4
+    return abase[M] + 2 * il * (il + 1) - 2 * im * (im + 1) + c
+
+
+def test_tile_index_matches_the_plan_layout():
+    for L in (1, 64, 129, 300, 1024):
+        abase, items, total = a_layout(L)
+        seen = set()
+        for m, i, c1, first in items:
+            assert tile_index(abase, m, i, 0) == first
+            for c in range(4 * i + 4):
+                t = tile_index(abase, m, i, c)
+                assert 0 <= t < total and t not in seen
+                seen.add(t)
+        assert len(seen) == total
+
+
+def model_tiles(L, s):
+    """Every A entry the tile-mode kernel writes: (tile, row, k) -> value, following its two
+    write paths (the row of 32 K values across the warp, and the flushed transposition block)."""
+    tab = T.delta_quadrant(L)
+    off = T.delta_offsets(L)
+    abase, _, _ = a_layout(L)
+    U = {}
+    for l in range(L):
+        D = tab[off[l]:off[l + 1]].reshape(l + 1, l + 1)
+        for mp in range(l + 1):
+            d = 0.0 if l < abs(s) else D[mp, abs(s)] * (-1.0 if (s > 0 and (l + mp) & 1) else 1.0)
+            U[l, mp] = np.float32(np.sqrt((2 * l + 1) / (4 * np.pi)) * d)
+    out = {}
+
+    def put(key, val):
+        assert key not in out, ("written twice", key)
+        out[key] = val
+
+    for l, b in tasks(L):
+        D = tab[off[l]:off[l + 1]].reshape(l + 1, l + 1)
+        m0, il, row = 32 * b, l // 128, l % 128
+        for mp in range(l, m0 - 1, -1):
+            for lane in range(32):
+                m = m0 + lane
+                if m > l:
+                    continue
+                x = D[mp, m]  # Delta_{m' m}, lane m at step m'
+                sgn = -1.0 if (mp - m) & 1 else 1.0
+                put((tile_index(abase, mp, il, m0 // 32), row, lane), U[l, m] * np.float32(sgn * x))
+            if mp >= m0 + 32 and (mp & 31) == 0:
+                for r in range(32):
+                    M = m0 + r
+                    if M > l:
+                        break
+                    for lane in range(32):
+                        c = mp + lane
+                        if c <= l:
+                            put((tile_index(abase, M, il, mp // 32), row, lane), U[l, c] * np.float32(D[c, M]))
+    return out, U
+
+
+@pytest.mark.parametrize("L,s", [(40, 2), (97, -1), (150, 0)])
+def test_tile_mode_writes_every_entry_of_A_once(L, s):
+    """A_m[l][m'] = U_l[m'] Delta^l_{m'm} for every 0 <= m, m' <= l < L lands exactly once at
+    row l mod 128, K = m' mod 32 of tile (m, l // 128, m' // 32); nothing else is written."""
+    out, U = model_tiles(L, s)
+    tab = T.delta_quadrant(L)
+    off = T.delta_offsets(L)
+    abase, _, _ = a_layout(L)
+    want = {}
+    for l in range(L):
+        D = tab[off[l]:off[l + 1]].reshape(l + 1, l + 1)
+        for m in range(l + 1):
+            for mp in range(l + 1):
+                key = (tile_index(abase, m, l // 128, mp // 32), l % 128, mp % 32)
+                want[key] = U[l, mp] * np.float32(D[mp, m])
+    assert set(out) == set(want)
+    # the oracle's full-matrix table is symmetric only to rounding: compare to FP32 rounding
+    keys = sorted(want)
+    a = np.array([out[k] for k in keys], dtype=np.float64)
+    b = np.array([want[k] for k in keys], dtype=np.float64)
+    assert np.abs(a - b).max() <= 2e-7 * np.abs(b).max()
