@@ -1105,12 +1105,12 @@ int time_plan(ssht_plan_t p, float* ms) {
     return rc;
   }
   p->bytes -= cb + gb + cb;
-  cudaMemset(a, 0, cb);
   cudaEvent_t e0, e1;
   cudaStream_t st = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  cudaMemsetAsync(a, 0, cb, st);
   for (int it = 0; it < 6 && !rc; ++it) {
     if (it == 2) cudaEventRecord(e0, st);
     rc = p->f64 ? inverse_impl<double>(p, a, b, st) : inverse_impl<float>(p, a, b, st);

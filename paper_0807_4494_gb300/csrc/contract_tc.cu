@@ -490,7 +490,10 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   if ((e = tc_alloc((void**)&p->items_inv, inv.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->A, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  // zero once (entries no call writes stay zero); cudaMemset is asynchronous on the legacy
+  // stream, and the plans' packing and recursions run on non-blocking streams: wait for it
   if ((e = cudaMemset(p->A, 0, (size_t)ft * A_TILE)) != cudaSuccess) goto fail;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) goto fail;
   if (p->bf16 && (e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->abase, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
