@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-alt", action="store_true", help="skip the other split precision's line")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (captured graph) line")
     ap.add_argument("--no-real", action="store_true", help="skip the real spin-0 fields line")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 transform line")
     ap.add_argument("--error-sweep", action="store_true",
                     help="print errors vs the FP64 oracle for L = 32 .. 2048 and every precision, then exit")
     return ap.parse_args()
@@ -229,6 +230,110 @@ def fft_flops(M):
     return 5.0 * M * np.log2(M)
 
 
+KERNEL_SOURCES = {
+    "column_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu"],
+    "risbo_kernel": ["paper_0807_4494_gb300/csrc/delta.cu"],
+    "tc_gemm_kernel<inverse>": ["paper_0807_4494_gb300/csrc/contract_tc.cu"],
+    "tc_gemm_kernel<forward>": ["paper_0807_4494_gb300/csrc/contract_tc.cu"],
+    "pack_v_kernel": ["paper_0807_4494_gb300/csrc/contract_tc.cu"],
+    "inverse_theta_kernel": ["paper_0807_4494_gb300/csrc/torus_pass.cu"],
+    "phi_kernel<+1>": ["paper_0807_4494_gb300/csrc/torus_pass.cu"],
+    "phi_kernel<-1>": ["paper_0807_4494_gb300/csrc/torus_pass.cu"],
+    "forward_theta_kernel": ["paper_0807_4494_gb300/csrc/torus_pass.cu"],
+    "inverse_kernel (SIMT)": ["paper_0807_4494_gb300/csrc/contract_simt.cu"],
+    "project_kernel (SIMT)": ["paper_0807_4494_gb300/csrc/contract_simt.cu"],
+}
+
+
+def split_trace(trace, steps):
+    """Per-kernel live launch times (ms) from the stage trace of `steps` inverse + forward steps of
+    one plan: the torus passes are the caller-stream FFT brackets in call order (inverse theta,
+    inverse phi, forward phi, forward theta), the recursion the Delta brackets, the packing of the
+    inverse's data operand the caller-stream pack brackets."""
+    out = {}
+    fft = [t1 - t0 for name, lane, t0, t1 in trace if name == "fft" and lane == 0]
+    names = ["theta_inverse", "phi_inverse", "phi_forward", "theta_forward"]
+    for k, d in enumerate(fft):
+        out.setdefault(names[k % 4], []).append(d)
+    for name, lane, t0, t1 in trace:
+        key = {("delta", 1): "recursion", ("delta", 0): "recursion", ("inverse", 0): "contraction_inverse",
+               ("project", 0): "contraction_forward", ("pack", 0): "pack_data", ("pack", 1): "pack_a",
+               ("torus", 0): "torus_glue"}.get((name, lane))
+        if key:
+            out.setdefault(key, []).append(t1 - t0)
+    return {k: {"ms": float(np.mean(v)), "launches": len(v)} for k, v in out.items()}
+
+
+def kernel_rooflines(times, L, s, B, prec, recursion, pk):
+    """Achieved fraction of each kernel's bound: algorithmic work of one launch over its live
+    average duration.  Algorithmic bytes count each operand once (a lower bound on DRAM traffic)."""
+    N, M = 2 * L - 1, torus_M(L)
+    macs = B * contraction_macs(L, s)
+    quad = quadrant_entries(L)
+    res = {}
+
+    def entry(kernel, ms, flops=None, fpeak=None, fsrc=None, nbytes=None, extra=None):
+        t = ms / 1e3
+        e = {"kernel": kernel, "ms": ms}
+        fr = {}
+        if flops is not None:
+            e["tflops"] = flops / t / 1e12
+            e["flop_frac"] = e["tflops"] / fpeak[0]
+            e["flop_peak"] = fpeak[0]
+            e["flop_peak_source"] = fpeak[1]
+            fr["flop"] = e["flop_frac"]
+        if nbytes is not None:
+            e["gbs"] = nbytes / t / 1e9
+            e["hbm_frac"] = e["gbs"] / pk["hbm_gbs"][0]
+            e["algorithmic_bytes"] = nbytes
+            fr["hbm"] = e["hbm_frac"]
+        e["bound"] = max(fr, key=fr.get) if fr else None
+        if extra:
+            e.update(extra)
+        e["traffic"] = traffic_for(kernel, KERNEL_SOURCES.get(kernel, []))
+        return e
+
+    tc = prec in ("tf32x3", "bf16x6")
+    for key, v in times.items():
+        ms = v["ms"]
+        if key == "recursion":
+            if recursion == "risbo":
+                nh, ni = recursion_updates(L)
+                res[key] = entry("risbo_kernel", ms, 7.0 * nh + 8.0 * ni, pk["fp64_tflops"], None, quad * 8.0,
+                                 {"fp64_instr_frac": ((4.0 * nh + 5.0 * ni) / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0)})
+            else:
+                u = column_updates(L)
+                res[key] = entry("column_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * 8.0,
+                                 {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
+                                  "work": "%.3g updates x 3 FP64 instructions (4 flops); writes %s" % (
+                                      u, "the A tiles (8 B an entry)" if tc else "the FP64 table"),
+                                  "fp64_probe_tflops": FP64_PROBE_TFLOPS})
+        elif key in ("contraction_inverse", "contraction_forward") and tc:
+            nprod, pkey = (3, "tf32_tflops") if prec == "tf32x3" else (6, "bf16_tflops_sustained")
+            fwd = key.endswith("forward")
+            data = B * (N * L if fwd else L * L) * 16.0
+            outb = B * (L * L if fwd else N * L) * 8.0
+            res[key] = entry("tc_gemm_kernel<%s>" % ("forward" if fwd else "inverse"), ms, nprod * 4.0 * macs,
+                             pk[pkey], None, quad * 8.0 + data + outb,
+                             {"useful_tflops": 4.0 * macs / (ms / 1e3) / 1e12, "issued_products": nprod})
+        elif key in ("contraction_inverse", "contraction_forward"):
+            fwd = key.endswith("forward")
+            pkey = "fp64_tflops" if prec == "fp64" else "fp32_tflops"
+            res[key] = entry(("project_kernel" if fwd else "inverse_kernel") + " (SIMT)", ms, 4.0 * macs, pk[pkey], None,
+                             quad * 8.0 + B * (L * L + N * L) * (16.0 if prec == "fp64" else 8.0))
+        elif key == "pack_data":
+            res[key] = entry("pack_v_kernel", ms, None, None, None, B * L * L * 24.0)
+        elif key in ("theta_inverse", "phi_inverse", "phi_forward", "theta_forward") and prec != "fp64":
+            rows = B * L
+            nfft = 4 if key == "theta_forward" else 2
+            outb = B * L * (N + 1) * (16.0 if (key == "theta_forward" and tc) else 8.0)
+            kern = {"theta_inverse": "inverse_theta_kernel", "phi_inverse": "phi_kernel<+1>",
+                    "phi_forward": "phi_kernel<-1>", "theta_forward": "forward_theta_kernel"}[key]
+            res[key] = entry(kern, ms, rows * nfft * fft_flops(M), pk["fp32_tflops"], None, B * L * N * 8.0 + outb,
+                             {"work": "%d rows x %d FFTs of %d points (5 M log2 M flops each)" % (rows, nfft, M)})
+    return res
+
+
 def source_hash(*files):
     h = hashlib.sha256()
     for f in files:
@@ -305,6 +410,7 @@ def run_ssht(args):
     barrier(world, device)
     ms_local = e0.elapsed_time(e1)
     clocks = sampler.stop() if sampler else None
+    trace = plan.profile_trace()
     stages, launches1 = plan.profile_read()
     plan.profile(False)
     plan.check()
@@ -359,7 +465,7 @@ def run_ssht(args):
     # roundtrip error over the whole batch, and the oracle check on sampled fields
     rt = float((back - flm).abs().max() / flm.abs().max())
     check = None
-    fields = sorted({0, B - 1})
+    fields = sorted(set(range(0, B, 8)) | {B - 1})
     inv_oracle = {}
 
     def oracle_errors(g_dev, b_dev):
@@ -415,59 +521,33 @@ def run_ssht(args):
         aplan.close()
         del grid2, back2
 
-    # roofline of the dominant kernel of this library (cuFFT is excluded: library code)
-    pk = peaks()
-    own = {k: v for k, v in stages.items() if k != "fft" and v[1] > 0}
-    dom = max(own, key=lambda k: own[k][0]) if own else None
+    # every kernel of the step, timed live (stage brackets on their own streams), against its
+    # bound; the top-level line is the kernel that takes the most time
+    sms, clk = device_units()
+    pk = peaks(sms, clk)
+    kern = kernel_rooflines(split_trace(trace, args.steps), L, s, B, prec, "column", pk)
     roof = None
-    if dom:
-        ms_d, n_d = own[dom]
-        per_launch_s = ms_d / n_d / 1e3
-        if dom == "delta":
-            # A half-step update is 2 fused multiply-adds, a product and a fused multiply-add
-            # (7 flops, 4 FP64 instructions); an integer-step update adds the row product (8 flops,
-            # 5 instructions).  The FMA-only peak counts 2 flops per instruction.
-            nh, ni = recursion_updates(L)
-            flops = 7.0 * nh + 8.0 * ni
-            ach = flops / per_launch_s / 1e12
-            peak, src = pk["fp64_tflops"]
-            roof = {"bound": "alu", "kernel": "risbo_kernel (FP64)", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
-                    "fp64_pipe_frac": ((4.0 * nh + 5.0 * ni) / per_launch_s) / (peak * 1e12 / 2.0),
-                    "traffic": traffic_for("risbo_kernel", ["paper_0807_4494_gb300/csrc/delta.cu"]),
-                    "work_per_launch": "%.3g flops = 7 x %.3g half-step + 8 x %.3g integer-step updates "
-                                       "(4 and 5 FP64 instructions)" % (flops, nh, ni)}
-            if delta_alone_ms:
-                a1 = flops / (delta_alone_ms / 1e3) / 1e12
-                roof["alone"] = {"ms": delta_alone_ms, "achieved": a1, "frac": a1 / peak,
-                                 "note": "the same sweep timed by itself (in the step the forward call's "
-                                         "sweep shares its SMs with the torus passes)"}
-        elif dom in ("inverse", "project") and prec in ("tf32x3", "bf16x6"):
-            # useful flops (4 per complex x real MAC) and the issued split-product tensor flops
-            flops = 4.0 * B * contraction_macs(L, s)
-            nprod, kind, pkey = (3, "tf32", "tf32_tflops") if prec == "tf32x3" else (6, "f16 (bf16)", "bf16_tflops")
-            ach = nprod * flops / per_launch_s / 1e12
-            peak, src = pk[pkey]
-            roof = {"bound": "tensor", "kernel": "tc_gemm_kernel<%s> (tcgen05 kind::%s, %d products)" % (
-                        "forward" if dom == "project" else "inverse", kind, nprod),
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
-                    "useful_tflops": flops / per_launch_s / 1e12,
-                    "traffic": traffic_for("tc_gemm_kernel", ["paper_0807_4494_gb300/csrc/contract_tc.cu"]),
-                    "work_per_launch": "%.3g useful flops = 4 x B x %.3g MACs; x%d issued" % (
-                        flops, contraction_macs(L, s), nprod)}
-        elif dom in ("inverse", "project"):
-            flops = 4.0 * B * contraction_macs(L, s)
-            ach = flops / per_launch_s / 1e12
-            key = "fp64_tflops" if prec == "fp64" else "fp32_tflops"
-            peak, src = pk[key]
-            roof = {"bound": "alu", "kernel": dom + " contraction (SIMT " + prec + ")", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
-                    "traffic": None,
-                    "work_per_launch": "%.3g flops = 4 x B x %.3g MACs" % (flops, contraction_macs(L, s))}
+    if kern:
+        dom = max(kern, key=lambda k: kern[k]["ms"])
+        e = kern[dom]
+        if e["bound"] == "hbm":
+            roof = {"bound": "hbm", "achieved": e["gbs"], "peak": pk["hbm_gbs"][0], "unit": "GB/s",
+                    "frac": e["hbm_frac"], "peak_source": pk["hbm_gbs"][1]}
         else:
-            roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": pk["hbm_gbs"][0], "unit": "GB/s",
-                    "frac": None, "traffic": None}
+            roof = {"bound": "tensor" if e["kernel"].startswith("tc_gemm") else "alu", "achieved": e["tflops"],
+                    "peak": e["flop_peak"], "unit": "TFLOP/s", "frac": e["flop_frac"],
+                    "peak_source": e["flop_peak_source"]}
+        roof.update({"kernel": e["kernel"], "stage": dom, "ms_per_launch": e["ms"], "traffic": e["traffic"]})
+        if delta_alone_ms and dom == "recursion":
+            u = column_updates(L)
+            roof["alone"] = {"ms": delta_alone_ms, "achieved": 4.0 * u / (delta_alone_ms / 1e3) / 1e12,
+                             "note": "the table-writing sweep timed by itself (ssht_wigner_delta)"}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1] > 0}
+
+    # the plain FP64 GPU transform of the same workload (the mixed-precision form must beat it)
+    fp64_line = None
+    if not args.no_fp64 and prec != "fp64":
+        fp64_line = run_fp64(args, torch, inputs, ssht, world, device, stream, rank, pk, inv_oracle, flm_np)
 
     # the plan-time Delta cache (the paper's timing protocol: precomputed Delta in memory)
     cache_line = None
@@ -525,10 +605,12 @@ def run_ssht(args):
             "rel_err": check,
             "alt_precision": alt,
             "roofline": roof,
+            "kernels": kern,
             "stage_ms_per_step": stage_ms,
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": int(launches1 - launches0),
+            "fp64": fp64_line,
             "delta_cache": cache_line,
             "uneven_batch": uneven,
             "real_fields": real_line,
@@ -539,6 +621,55 @@ def run_ssht(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_fp64(args, torch, inputs, ssht, world, device, stream, rank, pk, inv_oracle, flm_np):
+    """The plain FP64 GPU transform on the same band-limit and spin: B fields (the headline batch)
+    and one field, with the FP64 contractions' live rooflines and the errors of field 0."""
+    L, s = args.L, args.s
+    res = {}
+    for B in sorted({args.batch, 1}, reverse=True):
+        plan = ssht.Plan(L, s, B, precision="fp64")
+        flm = torch.from_numpy(flm_np[:B]).to(torch.complex128).to(device)
+        grid = torch.empty(plan.grid_shape(), dtype=torch.complex128, device=device)
+        back = torch.empty(plan.coeff_shape(), dtype=torch.complex128, device=device)
+
+        def step():
+            plan.inverse(flm, out=grid)
+            plan.forward(grid, out=back)
+        step()
+        torch.cuda.synchronize()
+        nrep = 3 if B > 1 else 5
+        plan.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nrep):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        trace = plan.profile_trace()
+        plan.profile(False)
+        plan.check()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+        times = {k: v for k, v in split_trace(trace, nrep).items()
+                 if k in ("recursion", "contraction_inverse", "contraction_forward")}
+        line = {"batch": B, "value": throughput(world, B, nrep, ms), "unit": "transforms/s", "ms_per_step": ms / nrep,
+                "steps": nrep, "kernels": kernel_rooflines(times, L, s, B, "fp64", "column", pk)}
+        if rank == 0 and not args.no_check:
+            from oracle import transforms as T
+            if 0 not in inv_oracle:
+                inv_oracle[0] = T.inverse(flm_np[0], L, s)
+            f_or = inv_oracle[0]
+            g0 = grid[0].cpu().numpy()
+            fw = T.forward(g0, L, s)
+            line["inverse"] = float(np.abs(g0 - f_or).max() / np.abs(f_or).max())
+            line["forward"] = float(np.abs(back[0].cpu().numpy() - fw).max() / np.abs(fw).max())
+        res["B%d" % B] = line
+        plan.close()
+        del flm, grid, back
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_real(args, torch, inputs, ssht, world, device, stream, rank, prec):
@@ -610,14 +741,21 @@ def run_uneven(args, torch, inputs, ssht, world, device, stream, rank):
                        for (L, s_, c, p) in g.buckets()],
            "roundtrip": float((back - flat).abs().max() / flat.abs().max())}
     if rank == 0 and not args.no_check:
+        # the first field of every (L, s) bucket against the oracle, inverse and forward
         from oracle import transforms as T
-        fs = g.unpack_grid(f)
-        errs = []
-        for Lq in (128, 256, 512, 1024):
-            i = next(k for k, L in enumerate(Ls) if L == Lq)
-            f_or = T.inverse(flms[i], Lq, ss[i])
-            errs.append(float(np.abs(fs[i].cpu().numpy() - f_or).max() / np.abs(f_or).max()))
-        res["inverse_max_err_one_field_per_L"] = max(errs)
+        fs, bs = g.unpack_grid(f), g.unpack_coeffs(back)
+        e_inv, e_fwd, seen = 0.0, 0.0, set()
+        for i, (Lq, sq_) in enumerate(zip(Ls, ss)):
+            if (Lq, sq_) in seen:
+                continue
+            seen.add((Lq, sq_))
+            f_or = T.inverse(flms[i], Lq, sq_)
+            fi = fs[i].cpu().numpy()
+            e_inv = max(e_inv, float(np.abs(fi - f_or).max() / np.abs(f_or).max()))
+            fw = T.forward(fi.astype(np.complex128), Lq, sq_)
+            e_fwd = max(e_fwd, float(np.abs(bs[i].cpu().numpy() - fw).max() / np.abs(fw).max()))
+        res["rel_err"] = {"inverse": e_inv, "forward": e_fwd, "buckets_checked": len(seen),
+                          "fields_checked": "the first field of every (L, s) bucket"}
     g.close()
     return res
 
@@ -680,6 +818,23 @@ def error_sweep(args):
     __graft_entry__.build()
     from oracle import transforms as T
     from paper_0807_4494_gb300 import inputs, ssht
+    # the single-field FP64 configuration: Re/Im iid N(0,1), spins 0 and 2 separately, L = 32 .. 512
+    for s in (0, 2):
+        for L in (32, 64, 128, 256, 512):
+            flm = inputs.coeffs(L, s, 1, seed=0)
+            f_or = T.inverse(flm[0], L, s)
+            plan = ssht.Plan(L, s, 1, precision="fp64")
+            x = torch.from_numpy(flm).cuda()
+            f = plan.inverse(x)
+            back = plan.forward(f)
+            plan.check()
+            f0 = f[0].cpu().numpy()
+            fw = T.forward(f_or, L, s)
+            print(json.dumps({"L": L, "s": s, "spectrum": "flat N(0,1)", "precision": "fp64",
+                              "inverse": float(np.abs(f0 - f_or).max() / np.abs(f_or).max()),
+                              "forward_of_oracle_grid": float(np.abs(plan.forward(torch.from_numpy(f_or[None]).cuda())[0].cpu().numpy() - fw).max() / np.abs(fw).max()),
+                              "roundtrip": float((back - x).abs().max() / x.abs().max())}), flush=True)
+            plan.close()
     s = args.s
     for L in (32, 64, 128, 256, 512, 1024, 2048):
         flm = inputs.coeffs(L, s, 1, seed=0, spectrum="cmb")
@@ -692,7 +847,7 @@ def error_sweep(args):
             plan.check()
             f0 = f[0].cpu().numpy()
             fw = T.forward(f0.astype(np.complex128), L, s)
-            line = {"L": L, "s": s, "precision": prec,
+            line = {"L": L, "s": s, "spectrum": "cmb CN(0, 1/(l+1)^2)", "precision": prec,
                     "inverse": float(np.abs(f0 - f_or).max() / np.abs(f_or).max()),
                     "forward": float(np.abs(back[0].cpu().numpy() - fw).max() / np.abs(fw).max()),
                     "roundtrip": float((back - x).abs().max() / x.abs().max())}

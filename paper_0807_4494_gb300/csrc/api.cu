@@ -259,15 +259,16 @@ int run_delta(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
-// 3xTF32 plans that run their own column recursion make the A tiles in the recursion itself
-// (no FP64 table, no packing); U, the spin column, is then made once at plan creation.
+// 3xTF32 plans that run their own column recursion make the forward transform's A tiles in the
+// recursion itself (no FP64 table, no packing); U, the spin column, is then made once at plan
+// creation.  The inverse's tiles are the transpose (rows m', K = l) and are packed from the table.
 bool tiles_direct(const ssht_plan_s* p) {
   return p->tc && tc_a_tiles(p->tc).A && !p->delta_shared && p->delta.method == kDeltaColumn;
 }
 
 // Delta and the contraction's A operand of one direction, on st.
 int make_operands(ssht_plan_t p, int forward, cudaStream_t st) {
-  if (tiles_direct(p)) {
+  if (forward && tiles_direct(p)) {
     StageScope sc(p, SSHT_STAGE_DELTA, st);
     SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
     p->launches += 1;
@@ -772,7 +773,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   }
   if (p->delta_mode == SSHT_DELTA_CACHE) {
     if (tiles_direct(p)) {
-      if ((rc = make_operands(p, 1, 0))) return bail(rc);
+      if ((rc = make_operands(p, 0, 0)) || (rc = make_operands(p, 1, 0))) return bail(rc);
     } else {
       if ((rc = run_delta(p, 0))) return bail(rc);
       if (p->tc && ((rc = pack_a(p, 0, 0)) || (rc = pack_a(p, 1, 0)))) return bail(rc);

@@ -66,7 +66,6 @@ struct TcArgs {
   int nitems;
   const Item* items;
   const uint8_t* A;       // packed A tiles
-  const long long* abase; // MN inverse: per m, the index of the forward tile (m, m / 128, 0)
   const uint8_t* X;       // packed data tiles
   const long long* xoff;  // per m: data tile index of chunk xc0(m)
   const int* xc0;         // per m: first chunk stored for m
@@ -195,13 +194,8 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
   for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// MN (inverse, 3xTF32 only): the A operand is read from the forward tiles (rows l, K = m') as an
-// MN-major operand -- for the chunk of l in [32 kc, 32 kc + 32) of item (m, row block i'), the
-// 32-row slices (rows l mod 128) of the forward tiles (m, kc / 4, 4 i' + c'), c' < 4, each four
-// 1 KB swizzle atoms of 8 rows (K) x 128 bytes (32 m'), laid side by side along M.
-template <bool FWD, bool BF, bool MN>
+template <bool FWD, bool BF>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
-  static_assert(!MN || (!FWD && !BF), "the MN-major A operand serves the 3xTF32 inverse");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int b_part = a.NC * 128;
@@ -247,16 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
           }
           uint8_t* st = smem + s * stage_bytes;
           mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-          if constexpr (MN) {
-            const int il = c >> 2, im = itm.m / TM;
-            const long long t0 = a.abase[itm.m] + 2ll * il * (il + 1) - 2ll * im * (im + 1) + 4ll * itm.i;
-            for (int cc = 0; cc < 4; ++cc)
-              for (int part = 0; part < 2; ++part)
-                bulk_g2s(st + part * A_PART + cc * 4096,
-                         a.A + (size_t)(t0 + cc) * A_TILE + part * A_PART + (size_t)(c & 3) * 4096, 4096, &full[s]);
-          } else {
-            bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
-          }
+          bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
           const long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
           bulk_g2s(st + A_TILE, a.X + (size_t)xt * 2 * b_part, (uint32_t)(2 * b_part), &full[s]);
           last_use[s] = u;
@@ -269,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer: one tensor-memory segment per chunk, corrections first ----
-      const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : (idesc_tf32(TM, a.NC) | (MN ? kTransposeA : 0u));
+      const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : idesc_tf32(TM, a.NC);
       int it = 0;
       for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
         const Item itm = a.items[w];
@@ -299,20 +284,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
                 mma_bf16(dt, desc_sw128(sa + oa[pa[q]] + kk * 32), desc_sw128(sb + ob[pb[q]] + kk * 32), idesc,
                          (q == 0 && kk == 0) ? 0u : 1u);
           } else {
-            // A: K-major (K step kk at byte 32 kk of each row) or MN-major (K step kk = atom kk)
-            auto ad = [&](uint32_t base, int kk) {
-              return MN ? desc_mn_sw128(base + kk * 1024, 4096, 1024) : desc_sw128(base + kk * 32);
-            };
 #pragma unroll
             for (int kk = 0; kk < TK / 8; ++kk) {
               const uint32_t ko = kk * 32;
-              mma_tf32(dt, ad(sa, kk), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
-              mma_tf32(dt, ad(sa + A_PART, kk), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
+              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + b_part + ko), idesc, kk == 0 ? 0u : 1u);  // hi * lo
+              mma_tf32(dt, desc_sw128(sa + A_PART + ko), desc_sw128(sb + ko), idesc, 1u);                 // lo * hi
             }
 #pragma unroll
             for (int kk = 0; kk < TK / 8; ++kk) {
               const uint32_t ko = kk * 32;
-              mma_tf32(dt, ad(sa, kk), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
+              mma_tf32(dt, desc_sw128(sa + ko), desc_sw128(sb + ko), idesc, 1u);                          // hi * hi
             }
           }
           mma_commit(&empty[s]);
@@ -403,10 +384,9 @@ struct TcPlan {
   int n_inv = 0, n_fwd = 0;
   long long tiles_A = 0, tiles_inv = 0, xtiles_inv = 0, xtiles_fwd = 0;
   // Forward A tiles (m, i, c): rows l = 128 i + r, K = m' = 32 c + k, tile index abase[m] +
-  // 2i(i+1) - 2 i_m(i_m+1) + c with i_m = m / 128 (each (m, i), i >= i_m, holds 4i + 4 slots, so
-  // that the four 32-wide m' chunks of every 128-row m' block of the inverse exist; slots and
-  // entries nothing writes stay zero).  3xTF32: both directions read these (the inverse as an
-  // MN-major operand).  Split-BF16: the inverse has its own K-major tiles A_inv.
+  // 2i(i+1) - 2 i_m(i_m+1) + c with i_m = m / 128 (each (m, i), i >= i_m, holds 4i + 4 slots;
+  // entries nothing writes stay zero).  Inverse A tiles A_inv (m, i, c): rows m' = 128 i + r,
+  // K = l = 32 c + k, at the item's tile index.
   uint8_t* A = nullptr;
   uint8_t* A_inv = nullptr;
   long long* abase = nullptr;
@@ -494,7 +474,7 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   // stream, and the plans' packing and recursions run on non-blocking streams: wait for it
   if ((e = cudaMemset(p->A, 0, (size_t)ft * A_TILE)) != cudaSuccess) goto fail;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) goto fail;
-  if (p->bf16 && (e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->abase, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xoff, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
@@ -516,12 +496,12 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
         (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
       goto fail;
     if (p->bf16) {
-      if ((e = gemm_attrs(tc_gemm_kernel<false, true, false>, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(tc_gemm_kernel<true, true, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, true>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, true>, gemm_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(pack_v_kernel<true>, xsmem_max)) != cudaSuccess) goto fail;
     } else {
-      if ((e = gemm_attrs(tc_gemm_kernel<false, false, true>, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(tc_gemm_kernel<true, false, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, false>, gemm_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(pack_v_kernel<false>, xsmem_max)) != cudaSuccess) goto fail;
     }
   }
@@ -552,16 +532,16 @@ ATiles tc_a_tiles(const TcPlan* p) {
 }
 
 cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* U, cudaStream_t st, int* launches) {
-  // 3xTF32: one set of tiles serves both directions, the forward layout
-  if (!p->bf16) forward = 1;
   // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
   const dim3 gf(p->nC, p->n_fwd), gi(p->nC, p->n_inv);
   if (forward && p->bf16)
     pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
   else if (forward)
     pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
-  else
+  else if (p->bf16)
     pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+  else
+    pack_a_kernel<false, false><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -594,8 +574,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.NC = p->NC;
   a.nitems = forward ? p->n_fwd : p->n_inv;
   a.items = forward ? p->items_fwd : p->items_inv;
-  a.A = (forward || !p->bf16) ? p->A : p->A_inv;
-  a.abase = p->abase;
+  a.A = forward ? p->A : p->A_inv;
   a.X = p->X;
   a.xoff = p->xoff;
   a.xc0 = p->xc0;
@@ -604,13 +583,13 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.status = status;
   const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
   if (forward && p->bf16)
-    tc_gemm_kernel<true, true, false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
   else if (forward)
-    tc_gemm_kernel<true, false, false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<true, false><<<grid, THREADS, p->smem, st>>>(a);
   else if (p->bf16)
-    tc_gemm_kernel<false, true, false><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<false, true><<<grid, THREADS, p->smem, st>>>(a);
   else
-    tc_gemm_kernel<false, false, true><<<grid, THREADS, p->smem, st>>>(a);
+    tc_gemm_kernel<false, false><<<grid, THREADS, p->smem, st>>>(a);
   *launches += 1;
   return cudaGetLastError();
 }

@@ -35,22 +35,6 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Shared-memory descriptor of an MN-major operand in the SWIZZLE_128B layout: swizzle atoms of
-// 8 rows along K x 128 bytes along M (or N), `lbo` bytes from one atom to the next along M,
-// `sbo` bytes from one group of 8 K rows to the next.
-__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction-descriptor bit that marks the A operand MN-major ("transpose A").
-constexpr uint32_t kTransposeA = 1u << 15;
-
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
 __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
