@@ -245,6 +245,21 @@ SSHT_API int ssht_group_replay(ssht_group_t group, void* stream);
 /* Wait for the group's work and report a latched kernel-side timeout (SSHT_ETIMEOUT). */
 SSHT_API int ssht_group_check(ssht_group_t group);
 
+/* Test hook (the paper has no counterpart): the n-th device allocation this library makes from
+ * now on, in any call on any thread, fails as if the device were out of memory (cudaMalloc
+ * returning cudaErrorMemoryAllocation); n = 0 disables it.  Plan and group creation then return
+ * SSHT_ENOMEM after releasing what they had allocated.  n < 0 returns SSHT_EINVAL. */
+SSHT_API int ssht_debug_fail_allocation(int n);
+
+/* Spin limit of the plan's device-side waits, in nanoseconds of the device clock (default 10^9, one
+ * second): the Risbo recursion's hand-offs between CTAs (SSHT_FLAG_RISBO plans) and the
+ * tensor-core contraction's pipeline waits.  A wait that exceeds it latches SSHT_ETIMEOUT in the
+ * plan (read by ssht_plan_check), makes the kernel's other CTAs leave at their next wait, and leaves
+ * the outputs of that call incomplete; copies and tensor-core operations already issued are waited
+ * for before a CTA leaves, with the default limit.  A tiny limit makes the waits give up at once
+ * (how the tests exercise this path).  ns <= 0 restores the default. */
+SSHT_API int ssht_plan_set_wait_limit(ssht_plan_t plan, long long ns);
+
 /* Message describing the last error on the calling host thread ("" if none). */
 SSHT_API const char* ssht_last_error(void);
 

@@ -3,6 +3,7 @@
 #include "ssht_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -23,6 +24,21 @@ int fail(int code, const std::string& msg) {
 
 namespace ssht {
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
+
+namespace {
+std::atomic<long long> g_alloc_countdown{0};
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  long long n = g_alloc_countdown.load();
+  while (n > 0 && !g_alloc_countdown.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {  // this is the chosen allocation: fail it like an exhausted device
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
 }  // namespace ssht
 
 namespace {
@@ -103,6 +119,7 @@ struct ssht_plan_s {
   size_t stage_out_bytes = 0;
   bool delta_ready = false;
   bool u_fixed = false;  // U / Uf made once at creation (3xTF32 plans with the recursion writing the A tiles)
+  long long wait_ns = kDefaultWaitNs;  // spin limit of the device-side waits
   size_t bytes = 0;
   TcPlan* tc = nullptr;    // tensor-core contraction (precisions SSHT_TF32X3, SSHT_BF16X6)
   TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
@@ -194,7 +211,7 @@ struct StageScope {
 };
 
 int dalloc(ssht_plan_t p, void** ptr, size_t bytes, const char* what) {
-  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  cudaError_t e = dev_malloc(ptr, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     cudaGetLastError();
@@ -249,7 +266,7 @@ int pack_a(ssht_plan_t p, int forward, cudaStream_t st);
 int run_delta(ssht_plan_t p, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_DELTA, st);
   if (!p->delta_shared) {
-    SSHT_CUDA(delta_run(p->delta, p->d.L, st), "Delta recursion launch");
+    SSHT_CUDA(delta_run(p->delta, p->d.L, st, p->wait_ns), "Delta recursion launch");
     p->launches += 1;
   }
   if (!p->u_fixed) {
@@ -370,7 +387,7 @@ int tc_pack(ssht_plan_t p, const void* src, cudaStream_t st) {
 int tc_multiply(ssht_plan_t p, int forward, void* dst, cudaStream_t st) {
   int n = 0;
   StageScope sc(p, forward ? SSHT_STAGE_PROJECT : SSHT_STAGE_INVERSE, st);
-  SSHT_CUDA(tc_gemm(p->tc, forward, dst, p->ph, p->delta.status, st, &n), "tensor-core contraction");
+  SSHT_CUDA(tc_gemm(p->tc, forward, dst, p->ph, p->delta.status, p->wait_ns, st, &n), "tensor-core contraction");
   p->launches += n;
   return 0;
 }
@@ -930,8 +947,17 @@ int ssht_plan_check(ssht_plan_t p) {
   if (st != 0) {
     cudaMemset(p->delta.status, 0, sizeof(int));
     if (p->delta_mode == SSHT_DELTA_CACHE) p->delta_ready = false;
-    return fail(SSHT_ETIMEOUT, "a Delta recursion grid barrier exceeded its spin limit");
+    return fail(SSHT_ETIMEOUT, std::string("a device-side wait exceeded its spin limit (") +
+                                   ((st & kStatusBarrierTimeout) ? "recursion hand-off" : "") +
+                                   ((st & kStatusBarrierTimeout) && (st & 2) ? ", " : "") +
+                                   ((st & 2) ? "tensor-core pipeline" : "") + ")");
   }
+  return SSHT_OK;
+}
+
+int ssht_plan_set_wait_limit(ssht_plan_t p, long long ns) {
+  if (!p) return fail(SSHT_EINVAL, "null plan");
+  p->wait_ns = ns > 0 ? ns : kDefaultWaitNs;
   return SSHT_OK;
 }
 
@@ -997,6 +1023,12 @@ int ssht_plan_profile_trace(ssht_plan_t p, int* stage, int* lane, double* t0, do
 }
 
 const char* ssht_last_error(void) { return g_last_error.c_str(); }
+
+int ssht_debug_fail_allocation(int n) {
+  if (n < 0) return fail(SSHT_EINVAL, "ssht_debug_fail_allocation: n must be >= 0");
+  g_alloc_countdown.store(n);
+  return SSHT_OK;
+}
 
 int ssht_version(void) { return 100; }
 

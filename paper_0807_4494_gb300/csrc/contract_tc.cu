@@ -51,7 +51,6 @@ constexpr int A_TILE = kATile;             // hi then lo
 constexpr int STAGES = 2;
 constexpr int EPI_WARPS = 8;                       // two per tensor-memory lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer warp, MMA warp, epilogue warps
-constexpr long long WAIT_LIMIT = 1ll << 25;
 
 __host__ __device__ inline long long tri_ll(long long m) { return m * (m + 1) / 2; }
 __host__ __device__ inline size_t doff(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
@@ -72,6 +71,7 @@ struct TcArgs {
   const float2* ph;       // e^{i pi k/N}, k in [-(N-1), N-1], at k + N - 1
   float2* out;            // inverse: theta-DFT input E [B][N][N]; forward: flm [B][L*L]
   int* status;
+  long long wait_ns;      // spin limit of the pipeline waits
 };
 
 __device__ __forceinline__ float2 ipow_signed(int s, int k) {
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
         const uint8_t* Ab = a.A + (size_t)itm.atile * A_TILE;
         for (int c = itm.c0; c < itm.c1; ++c, ++it) {
           const int s = it % STAGES, u = it / STAGES;
-          if (!mbar_wait(&empty[s], (u & 1) ^ 1, abort, WAIT_LIMIT)) {
+          if (!mbar_wait(&empty[s], (u & 1) ^ 1, abort, a.wait_ns)) {
             *abort = 1;
             break;
           }
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       }
       // drain: every issued copy must have landed before the CTA leaves
       for (int s = 0; s < STAGES; ++s)
-        if (last_use[s] >= 0) mbar_wait(&full[s], last_use[s] & 1, abort, WAIT_LIMIT);
+        if (last_use[s] >= 0) mbar_wait(&full[s], last_use[s] & 1, nullptr, kDrainNs);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
         for (int c = itm.c0; c < itm.c1; ++c, ++it) {
           const int s = it % STAGES, u = it / STAGES;
           const int seg = it & 1, us = it >> 1;
-          if (!mbar_wait(&seg_empty[seg], (us & 1) ^ 1, abort, WAIT_LIMIT) ||
-              !mbar_wait(&full[s], u & 1, abort, WAIT_LIMIT)) {
+          if (!mbar_wait(&seg_empty[seg], (us & 1) ^ 1, abort, a.wait_ns) ||
+              !mbar_wait(&full[s], u & 1, abort, a.wait_ns)) {
             *abort = 1;
             ok = false;
             break;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
         if (!ok) break;
       }
       mma_commit(&done_bar);
-      mbar_wait(&done_bar, 0, abort, WAIT_LIMIT);
+      mbar_wait(&done_bar, 0, nullptr, kDrainNs);  // every issued MMA has completed
     }
   } else {
     // ---- epilogue: running sums of the segments, then phases and outputs ----
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       bool ok = true;
       for (int c = itm.c0; c < itm.c1; ++c, ++it) {
         const int seg = it & 1, us = it >> 1;
-        if (!mbar_wait(&seg_full[seg], us & 1, abort, WAIT_LIMIT)) {
+        if (!mbar_wait(&seg_full[seg], us & 1, abort, a.wait_ns)) {
           *abort = 1;
           ok = false;
           break;
@@ -399,7 +399,7 @@ struct TcPlan {
 };
 
 static cudaError_t tc_alloc(void** p, size_t bytes, size_t* total) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  cudaError_t e = dev_malloc(p, bytes ? bytes : 16);
   if (e == cudaSuccess) *total += bytes;
   return e;
 }
@@ -566,7 +566,8 @@ TileOut tc_forward_tiles(const TcPlan* p) {
   return o;
 }
 
-cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches) {
+cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, long long wait_ns, cudaStream_t st,
+                    int* launches) {
   TcArgs a;
   a.L = p->L;
   a.s = p->s;
@@ -581,6 +582,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   a.ph = (const float2*)ph;
   a.out = (float2*)out;
   a.status = status;
+  a.wait_ns = wait_ns;
   const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
   if (forward && p->bf16)
     tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);

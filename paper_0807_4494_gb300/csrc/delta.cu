@@ -57,6 +57,7 @@ struct RisboParams {
   unsigned int* counter;    // [0] barrier counter, [1] abort flag, [4 + c] degree done by CTA c (reset before launch)
   const int4* part;         // per step l and CTA: r0, r1, o0, o1 (host-made), or null: computed here
   int* status;              // latched status bits
+  long long limit_ns;       // spin limit of every wait
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -74,7 +75,7 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 // Grid barrier with a one-second spin limit.  Returns false if this CTA must stop.  While
 // thread 0 waits, thread 32 (another warp) runs `side()`.
 template <typename Side>
-__device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status, Side side) {
+__device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status, long long limit_ns, Side side) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -86,7 +87,7 @@ __device__ bool grid_barrier(unsigned int* counter, unsigned int target, int* st
     while (ld_acquire_u32(counter) < target) {
       if ((++spins & 63u) == 0u) {
         if (*(volatile unsigned int*)(counter + 1) != 0u) { good = 0; break; }
-        if (globaltimer_ns() - t0 > 1000000000ull) {
+        if ((long long)(globaltimer_ns() - t0) > limit_ns) {
           atomicOr(status, kStatusBarrierTimeout);
           atomicExch(counter + 1, 1u);
           good = 0;
@@ -224,7 +225,7 @@ __host__ __device__ inline void step_partition(int l, int cta, int nb, int* q) {
 // Warp 0 waits until every flag of CTAs [o0, o1] has reached `degree` (acquire), one lane per
 // flag so that the polls overlap, one second at most; returns (to every lane) whether to go on.
 __device__ bool poll_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
-                           int* status) {
+                           int* status, long long limit_ns) {
   const int lane = threadIdx.x & 31;
   int good = 1;
   const unsigned long long t0 = globaltimer_ns();
@@ -239,7 +240,7 @@ __device__ bool poll_flags(const unsigned int* done, int o0, int o1, unsigned in
         if (lane == 0) {
           if (*(volatile unsigned int*)abort_flag != 0u) {
             stop = 1;
-          } else if (globaltimer_ns() - t0 > 1000000000ull) {
+          } else if ((long long)(globaltimer_ns() - t0) > limit_ns) {
             atomicOr(status, kStatusBarrierTimeout);
             atomicExch(abort_flag, 1u);
             stop = 1;
@@ -257,10 +258,10 @@ __device__ bool poll_flags(const unsigned int* done, int o0, int o1, unsigned in
 
 // poll_flags by warp 0, then a barrier; all threads learn whether to go on.
 __device__ bool wait_flags(const unsigned int* done, int o0, int o1, unsigned int degree, unsigned int* abort_flag,
-                           int* status) {
+                           int* status, long long limit_ns) {
   __shared__ int ok;
   if (threadIdx.x < 32) {
-    const bool good = poll_flags(done, o0, o1, degree, abort_flag, status);
+    const bool good = poll_flags(done, o0, o1, degree, abort_flag, status, limit_ns);
     if (threadIdx.x == 0) ok = good ? 1 : 0;
   }
   __syncthreads();
@@ -317,7 +318,7 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
     P.slab0[threadIdx.x] = threadIdx.x == 1 ? 1.0 : 0.0;
     if (threadIdx.x == 0) P.table[0] = 1.0;
   }
-  if (!grid_barrier(P.counter, nb, P.status, [&] {
+  if (!grid_barrier(P.counter, nb, P.status, P.limit_ns, [&] {
         params(0, load_part(0));
         if (P.L > 2) part_next = load_part(1);
       }))
@@ -337,7 +338,7 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
       if (threadIdx.x == 0) atomicExch(done + cta, (unsigned)lp);
       continue;
     }
-    if (s_pre != l && !wait_flags(done, o0, o1, (unsigned)l, P.counter + 1, P.status)) return;
+    if (s_pre != l && !wait_flags(done, o0, o1, (unsigned)l, P.counter + 1, P.status, P.limit_ns)) return;
     SSHT_RISBO_MARK(1);
     const double* __restrict__ Yg = (l & 1) ? P.slab1 : P.slab0;
     double* __restrict__ Yn = (l & 1) ? P.slab0 : P.slab1;
@@ -513,7 +514,7 @@ __global__ void __maxnreg__(72) risbo_kernel(RisboParams P, long long cap) {
           if (l + 2 < P.L) {
             const int* q = s_par[(l + 1) & 1];  // made by thread 32 before this step's barriers
             if (q[0] < q[1]) {
-              const bool good = poll_flags(done, q[2], q[3], (unsigned)lp, P.counter + 1, P.status);
+              const bool good = poll_flags(done, q[2], q[3], (unsigned)lp, P.counter + 1, P.status, P.limit_ns);
               if (lane == 0) s_pre = good ? lp : -2;
             }
           }
@@ -655,12 +656,12 @@ static cudaError_t risbo_setup(DeltaWork& w, int L, int device) {
   if ((e = prefer_shared(risbo_kernel)) != cudaSuccess || (e = prefer_shared(spin_column_kernel)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, risbo_kernel, kThreads, w.smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.slab[0], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.slab[1], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.barrier, (4 + (size_t)w.blocks) * sizeof(unsigned int))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.slab[0], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.slab[1], slab_doubles(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.barrier, (4 + (size_t)w.blocks) * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.status, sizeof(int))) != cudaSuccess) return e;
   {
     // the partition of every step, made once here (the kernel reads one int4 per step)
     const size_t n = (size_t)(steps > 0 ? steps : 1) * nb;
@@ -680,7 +681,7 @@ static cudaError_t risbo_setup(DeltaWork& w, int L, int device) {
         const int a = r0 - 2 > 0 ? r0 - 2 : 0, b = r1 + 1 < l ? r1 + 1 : l;
         part[(size_t)l * nb + c] = r0 < r1 ? make_int4(r0, r1, owner(l, a), owner(l, b)) : make_int4(r0, r0, 0, -1);
       }
-    if ((e = cudaMalloc(&w.part, n * sizeof(int4))) != cudaSuccess) return e;
+    if ((e = dev_malloc(&w.part, n * sizeof(int4))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(w.part, part.data(), n * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     w.bytes_part = n * sizeof(int4);
   }
@@ -710,7 +711,7 @@ void delta_free(DeltaWork& w) {
   w.status = nullptr;
 }
 
-cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
+cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st, long long wait_ns) {
   if (w.method != kDeltaRisbo) return column_run(w, L, st);
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, (4 + (size_t)w.blocks) * sizeof(unsigned int), st)) != cudaSuccess) return e;
@@ -724,6 +725,7 @@ cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st) {
   P.counter = w.barrier;
   P.status = w.status;
   P.part = w.part;
+  P.limit_ns = wait_ns > 0 ? wait_ns : kDefaultWaitNs;
   long long cap = w.cap;
   void* args[] = {&P, &cap};
   return cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(w.blocks), dim3(w.threads), args, w.smem, st);
@@ -859,6 +861,7 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   P.counter = words;
   P.status = (int*)(words + 2);
   P.part = nullptr;  // no table: the kernel computes each step's partition
+  P.limit_ns = kDefaultWaitNs;
   long long cap = (long long)((smem - sq_smem_bytes(L)) / sizeof(double));  // the chunk area, then the sqrt table
   void* args[] = {&P, &cap};
   if (cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(sms), dim3(kThreads), args, smem, st) != cudaSuccess)

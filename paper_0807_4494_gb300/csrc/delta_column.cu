@@ -256,11 +256,11 @@ cudaError_t column_setup(DeltaWork& w, int L, int device) {
   w.blocks = sms * std::min(per_sm, 2);
   w.smem = kColSmem;
   w.ntasks = (int)tasks.size();
-  if ((e = cudaMalloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.barrier, 4 * sizeof(unsigned int))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.status, sizeof(int))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.tasks, tasks.size() * sizeof(int2))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.table, delta_offset(L) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.sqrt_tab, 2 * (2 * (size_t)L + 4) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.barrier, 4 * sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.status, sizeof(int))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&w.tasks, tasks.size() * sizeof(int2))) != cudaSuccess) return e;
   if ((e = cudaMemcpy(w.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if ((e = cudaMemset(w.status, 0, sizeof(int))) != cudaSuccess) return e;
   w.bytes = (delta_offset(L) + 2 * (2 * (size_t)L + 4)) * sizeof(double) + 4 * sizeof(unsigned int) + sizeof(int) +

@@ -35,6 +35,14 @@ struct Dims {
 // Records the message returned by ssht_last_error() and returns code.
 int set_last_error(int code, const char* msg);
 
+// Every device allocation of the library goes through here (cudaMalloc), so that the test hook
+// ssht_debug_fail_allocation can make a chosen one fail as if the device were out of memory.
+cudaError_t dev_malloc(void** ptr, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** ptr, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
 inline size_t delta_offset(long long l) { return (size_t)(l * (l + 1) * (2 * l + 1) / 6); }
 inline size_t tri(long long l) { return (size_t)(l * (l + 1) / 2); }
 
@@ -65,7 +73,9 @@ struct DeltaWork {
 
 cudaError_t delta_setup(DeltaWork& w, int L, int device, int method = kDeltaColumn);
 void delta_free(DeltaWork& w);
-cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st);
+// wait_ns: spin limit of the Risbo recursion's waits (the column recursion has none).
+constexpr long long kDefaultWaitNs = 1000000000ll;
+cudaError_t delta_run(const DeltaWork& w, int L, cudaStream_t st, long long wait_ns = kDefaultWaitNs);
 // The column method's setup and launch (delta_column.cu); delta_setup / delta_run dispatch.
 cudaError_t column_setup(DeltaWork& w, int L, int device);
 cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st);
@@ -117,7 +127,8 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* 
 cudaError_t tc_pack_data(TcPlan* p, const void* src, cudaStream_t st, int* launches);
 // The contraction: forward = 0 writes the half rows F (float2 [B][N][L], m' >= 0) of the inverse;
 // forward = 1 writes flm (float2 [B][L*L]).  Timeouts set bit 2 of *status.
-cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, cudaStream_t st, int* launches);
+cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, long long wait_ns, cudaStream_t st,
+                    int* launches);
 // Where the forward theta pass writes the projection's data tiles directly (in place of H and
 // tc_pack_data): the tile array, its column count NC, chunks per m nC, and the split form
 // (mode 1: 3xTF32, 2: split-BF16; 0: no tiles, H is written).

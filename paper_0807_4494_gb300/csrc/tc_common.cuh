@@ -56,15 +56,30 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false after `limit` polls or if *abort is set.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit) {
-  const uint32_t b = smem_u32(bar);
-  for (long long i = 0; i < limit; ++i) {
-    if (mbar_test(b, parity)) return true;
-    if ((i & 255) == 255 && *abort) return false;
-  }
-  return false;
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+
+// Bounded wait for the phase of the given parity: false once limit_ns of device time has passed
+// or, if abort is not null, once *abort is set (both checked every 256 polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit_ns) {
+  const uint32_t b = smem_u32(bar);
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned i = 1;; ++i) {
+    if (mbar_test(b, parity)) return true;
+    if ((i & 255u) == 0u) {
+      if (abort && *abort) return false;
+      if ((long long)(globaltimer() - t0) > limit_ns) return false;
+    }
+  }
+}
+
+// Waits for work this CTA has already issued (bulk copies, tensor-core operations) before it
+// leaves: not cut short by the abort flag, bounded by two seconds.
+constexpr long long kDrainNs = 2000000000ll;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

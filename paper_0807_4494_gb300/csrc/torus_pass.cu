@@ -602,7 +602,7 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
     host_fft(w, -1);
     for (int k = 0; k < M; ++k) wh[k] = make_float2((float)(w[k].real() / M), (float)(w[k].imag() / M));
   }
-  cudaError_t e = cudaMalloc(&p->buf, host.size() * sizeof(float2));
+  cudaError_t e = dev_malloc(&p->buf, host.size() * sizeof(float2));
   if (e != cudaSuccess) {
     delete p;
     return e;

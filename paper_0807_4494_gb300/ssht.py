@@ -25,7 +25,7 @@ EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspac
            "ssht_plan_profile_read", "ssht_plan_profile_trace", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
-           "ssht_last_error", "ssht_version")
+           "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_last_error", "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
 
 
@@ -79,6 +79,8 @@ def _lib():
             "ssht_group_capture": ([vp, vp, vp, vp, vp], i),
             "ssht_group_replay": ([vp, vp], i),
             "ssht_group_check": ([vp], i),
+            "ssht_debug_fail_allocation": ([i], i),
+            "ssht_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
             "ssht_last_error": ([], ctypes.c_char_p),
             "ssht_version": ([], i),
         }
@@ -143,6 +145,15 @@ def ssht_wigner_delta_noalloc(L, out_ptr, stream=0):
 
 def ssht_plan_check(h):
     _check(_lib().ssht_plan_check(h), "ssht_plan_check")
+
+
+def ssht_debug_fail_allocation(n):
+    """Test hook: the n-th device allocation of the library from now on fails (0 disables)."""
+    _check(_lib().ssht_debug_fail_allocation(int(n)), "ssht_debug_fail_allocation")
+
+
+def ssht_plan_set_wait_limit(h, ns):
+    _check(_lib().ssht_plan_set_wait_limit(h, int(ns)), "ssht_plan_set_wait_limit")
 
 
 def ssht_plan_profile(h, enable):
@@ -293,6 +304,10 @@ class Plan:
 
     def check(self):
         ssht_plan_check(self._h)
+
+    def set_wait_limit(self, ns):
+        """Spin limit of the plan's device-side waits in nanoseconds (<= 0: the default, 1 s)."""
+        ssht_plan_set_wait_limit(self._h, ns)
 
     def workspace_bytes(self):
         return ssht_plan_workspace_bytes(self._h)
