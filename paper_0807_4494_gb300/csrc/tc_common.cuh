@@ -63,17 +63,15 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 // Bounded wait for the phase of the given parity: false once limit_ns of device time has passed
-// or, if abort is not null, once *abort is set (both checked every 256 polls).
+// (checked after every poll) or, if abort is not null, once *abort is set (every 256 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit_ns) {
   const uint32_t b = smem_u32(bar);
   if (mbar_test(b, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (unsigned i = 1;; ++i) {
     if (mbar_test(b, parity)) return true;
-    if ((i & 255u) == 0u) {
-      if (abort && *abort) return false;
-      if ((long long)(globaltimer() - t0) > limit_ns) return false;
-    }
+    if ((i & 255u) == 0u && abort && *abort) return false;
+    if ((long long)(globaltimer() - t0) > limit_ns) return false;
   }
 }
 
