@@ -120,6 +120,7 @@ struct ssht_plan_s {
   bool delta_ready = false;
   bool u_fixed = false;  // U / Uf made once at creation (3xTF32 plans with the recursion writing the A tiles)
   long long wait_ns = kDefaultWaitNs;  // spin limit of the device-side waits
+  LaneTables lane;  // tables of the recursion that writes the inverse's A tiles (3xTF32, own recursion)
   size_t bytes = 0;
   TcPlan* tc = nullptr;    // tensor-core contraction (precisions SSHT_TF32X3, SSHT_BF16X6)
   TorusPlan* torus = nullptr;  // fused torus passes of FP32 plans (FP64 plans: cuFFT Z2Z + glue)
@@ -276,18 +277,23 @@ int run_delta(ssht_plan_t p, cudaStream_t st) {
   return 0;
 }
 
-// 3xTF32 plans that run their own column recursion make the forward transform's A tiles in the
-// recursion itself (no FP64 table, no packing); U, the spin column, is then made once at plan
-// creation.  The inverse's tiles are the transpose (rows m', K = l) and are packed from the table.
+// 3xTF32 plans that run their own column recursion make the contraction's A tiles in the
+// recursion itself (no FP64 table, no packing): the forward's tiles (rows l, K = m') with one lane
+// per column, the inverse's (rows m', K = l) with one lane per degree.  U, the spin column, and the
+// degree-lane recursion's tables are made once at plan creation.
 bool tiles_direct(const ssht_plan_s* p) {
   return p->tc && tc_a_tiles(p->tc).A && !p->delta_shared && p->delta.method == kDeltaColumn;
 }
 
 // Delta and the contraction's A operand of one direction, on st.
 int make_operands(ssht_plan_t p, int forward, cudaStream_t st) {
-  if (forward && tiles_direct(p)) {
+  if (tiles_direct(p)) {
     StageScope sc(p, SSHT_STAGE_DELTA, st);
-    SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
+    if (forward)
+      SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
+    else
+      SSHT_CUDA(column_run_inverse_tiles(p->delta, p->lane, p->d.L, p->s, tc_inverse_tiles(p->tc), st),
+                "recursion into the inverse's A tiles");
     p->launches += 1;
     return 0;
   }
@@ -626,6 +632,7 @@ void release(ssht_plan_t p) {
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_conv) cufftDestroy(p->fft_conv);
   if (!p->delta_shared) delta_free(p->delta);
+  lane_tables_free(p->lane);
   void* ptrs[] = {p->U, p->Uf, p->W1, p->W2, p->W3, p->khat, p->ph, p->ph64, p->stage_in, p->stage_out, p->rc, p->rg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -783,10 +790,13 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     p->u_fixed = true;
     // the calls' recursions run on the plan's non-blocking stream: U must be complete first
     ce = cudaDeviceSynchronize();
+    if (ce == cudaSuccess) ce = lane_tables_setup(p->lane, p->delta, L, s, p->Uf, tc_inverse_tiles(p->tc).nC);
     if (ce != cudaSuccess) {
       release(p);
-      return fail(SSHT_ECUDA, std::string("spin column: ") + cudaGetErrorString(ce));
+      return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,
+                  std::string("spin column and recursion tables: ") + cudaGetErrorString(ce));
     }
+    p->bytes += p->lane.bytes;
   }
   if (p->delta_mode == SSHT_DELTA_CACHE) {
     if (tiles_direct(p)) {

@@ -390,6 +390,7 @@ struct TcPlan {
   uint8_t* A = nullptr;
   uint8_t* A_inv = nullptr;
   long long* abase = nullptr;
+  long long* ibase = nullptr;  // [m * nI + i]: tile index of chunk kc of inverse item (m, i) is ibase + kc
   uint8_t* X = nullptr;  // data tiles (shared by both directions; sized for the larger)
   long long* xoff = nullptr;
   int* xc0 = nullptr;
@@ -423,7 +424,7 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   p->nI = (L + TM - 1) / TM;
   const int as = s < 0 ? -s : s;
   std::vector<Item> inv, fwd;
-  std::vector<long long> xoff(L), abase(L);
+  std::vector<long long> xoff(L), abase(L), ibase((size_t)L * std::max(1, (L + TM - 1) / TM), 0);
   std::vector<int> xc0(L);
   long long at = 0, ft = 0, xt = 0;
   for (int m = 0; m < L; ++m) {
@@ -441,6 +442,7 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
       // inverse: rows m' in block i, K = l >= max(m, m', |s|)
       const int c0 = std::max(lmin / TK, (i * TM) / TK);
       if (c0 < p->nC) {
+        ibase[(size_t)m * p->nI + i] = at - c0;
         inv.push_back({m, i, c0, p->nC, at});
         at += p->nC - c0;
       }
@@ -473,8 +475,12 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   // zero once (entries no call writes stay zero); cudaMemset is asynchronous on the legacy
   // stream, and the plans' packing and recursions run on non-blocking streams: wait for it
   if ((e = cudaMemset(p->A, 0, (size_t)ft * A_TILE)) != cudaSuccess) goto fail;
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = cudaMemset(p->A_inv, 0, (size_t)at * A_TILE)) != cudaSuccess) goto fail;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->ibase, ibase.size() * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpy(p->ibase, ibase.data(), ibase.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+    goto fail;
   if ((e = tc_alloc((void**)&p->abase, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xoff, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
@@ -514,13 +520,24 @@ fail:
 
 void tc_destroy(TcPlan* p) {
   if (!p) return;
-  void* ptrs[] = {p->items_inv, p->items_fwd, p->A, p->A_inv, p->abase, p->X, p->xoff, p->xc0};
+  void* ptrs[] = {p->items_inv, p->items_fwd, p->A, p->A_inv, p->abase, p->ibase, p->X, p->xoff, p->xc0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
 }
 
 size_t tc_bytes(const TcPlan* p) { return p ? p->bytes : 0; }
+
+InvTiles tc_inverse_tiles(const TcPlan* p) {
+  InvTiles t;
+  if (p && !p->bf16) {
+    t.A = p->A_inv;
+    t.ibase = p->ibase;
+    t.nI = p->nI;
+    t.nC = p->nC;
+  }
+  return t;
+}
 
 ATiles tc_a_tiles(const TcPlan* p) {
   ATiles t;

@@ -81,6 +81,39 @@ __device__ __forceinline__ double with_exp(double v, int e) {
   return __hiloint2double(hi, __double2loint(v));
 }
 
+// First row of degree l for the 32 columns m = m0 + lane (the whole warp calls it, m0 a multiple of
+// 32): Delta_{l m} = (-1)^{l-m} v 2^{*ge - l} with v in [1, 2^194) returned, from
+// prod_{k=m+1}^{l} g(k), g(k) = sqrt((l+k)/(l-k+1)) >= 1.
+__device__ __forceinline__ double first_row(int l, int m0, int lane, const double* __restrict__ sq,
+                                            const double* __restrict__ rsq, int* ge_out) {
+  const int m = m0 + lane;
+  // G = prod_{k = m0+33}^{l} g(k) as gm * 2^ge: each lane multiplies every 32nd factor (at most
+  // 64 factors of at most sqrt(2l) <= 64, so no overflow), then the warp multiplies the lanes'
+  // products with their exponents split off (the whole product reaches 2^l).
+  double gm = 1.0;
+  for (int k = m0 + 33 + lane; k <= l; k += 32) gm = __dmul_rn(gm, __dmul_rn(sq[l + k], rsq[l - k + 1]));
+  int ge = exp_of(gm);
+  gm = with_exp(gm, 0);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const double om = __shfl_xor_sync(0xffffffffu, gm, d);
+    const int oe = __shfl_xor_sync(0xffffffffu, ge, d);
+    gm = __dmul_rn(gm, om);  // in [1, 4)
+    ge += oe + exp_of(gm);
+    gm = with_exp(gm, 0);
+  }
+  // h = prod_{k = m+1}^{min(m0+32, l)} g(k): suffix product of the lanes' own factors g(m+1)
+  // (at most 32 factors, at most 2^192).
+  double h = (m + 1 <= l) ? __dmul_rn(sq[l + m + 1], rsq[l - m]) : 1.0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, h, d);
+    if (lane + d < 32) h = __dmul_rn(h, o);
+  }
+  *ge_out = ge;
+  return __dmul_rn(h, gm);
+}
+
 // TILES: write the A tiles of a 3xTF32 plan instead of the table.  With x = Delta_{m'm} in lane m
 // at step m' (row), the entry serves two tiles: A_{m'}[l][m] = U_l[m] (-1)^{m'-m} x, a row of 32
 // consecutive K values across the warp (written at once), for every row m' >= 32b; and A_m[l][m']
@@ -103,31 +136,9 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
     const int l = task.x, m0 = 32 * task.y, m = m0 + lane;
     const bool act = m <= l;
 
-    // ---- first row: Delta_{l m} = (-1)^{l-m} 2^{-l} prod_{k=m+1}^{l} g(k) ----
-    // G = prod_{k = m0+33}^{l} g(k) as gm * 2^ge: each lane multiplies every 32nd factor (at most
-    // 64 factors of at most sqrt(2l) <= 64, so no overflow), then the warp multiplies the lanes'
-    // products with their exponents split off (the whole product reaches 2^l).
-    double gm = 1.0;
-    for (int k = m0 + 33 + lane; k <= l; k += 32) gm = __dmul_rn(gm, __dmul_rn(sq[l + k], rsq[l - k + 1]));
-    int ge = exp_of(gm);
-    gm = with_exp(gm, 0);
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-      const double om = __shfl_xor_sync(0xffffffffu, gm, d);
-      const int oe = __shfl_xor_sync(0xffffffffu, ge, d);
-      gm = __dmul_rn(gm, om);  // in [1, 4)
-      ge += oe + exp_of(gm);
-      gm = with_exp(gm, 0);
-    }
-    // h = prod_{k = m+1}^{min(m0+32, l)} g(k): suffix product of the lanes' own factors g(m+1)
-    // (at most 32 factors, at most 2^192).
-    double h = (m + 1 <= l) ? __dmul_rn(sq[l + m + 1], rsq[l - m]) : 1.0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const double o = __shfl_down_sync(0xffffffffu, h, d);
-      if (lane + d < 32) h = __dmul_rn(h, o);
-    }
-    const double v = __dmul_rn(h, gm);  // Delta_{l m} = (-1)^{l-m} v 2^{ge - l}
+    // ---- first row: Delta_{l m} = (-1)^{l-m} v 2^{ge - l} ----
+    int ge;
+    const double v = first_row(l, m0, lane, sq, rsq, &ge);
     int E = 0;                          // SCALED: true value = stored * 2^E (E < 0 while out of range)
     double cur;
     if (!act) {
@@ -223,6 +234,141 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// One lane per degree: the inverse contraction's A tiles (rows m', K = l), 3xTF32 plans.
+//
+// The inverse's tile rows run along K = l, so here a warp takes 32 consecutive degrees
+// l = 32 kc + lane and one column m and walks m' from the top degree down to m, lane l starting
+// at m' = l from its first-row entry.  At step m' the lanes hold Delta^l_{m'm} for 32 consecutive
+// l: A_m[m'][l] = U_l[m'] Delta^l_{m'm} is one 32-wide tile row, and so (for m' > m) is
+// A_{m'}[m][l] = U_l[m] (-1)^{m'-m} Delta^l_{m'm} -- every entry of A with m' >= m from the first
+// write, with m' < m from the second, each once.  The coefficients differ per lane here (they
+// depend on l), so a(l, m'), b(l, m'), the first rows and the transposed U come from plan-time
+// tables in the triangle layout [r][l], l >= r, read 32 consecutive l at a time.
+// ---------------------------------------------------------------------------------------------
+
+// Index of (r, l), 0 <= r <= l < L, in the triangle layout [r][l].
+__host__ __device__ __forceinline__ size_t tri_idx(long long r, long long l, long long L) {
+  return (size_t)(r * L - r * (r - 1) / 2 + (l - r));
+}
+
+struct LaneParams {
+  int L, as, nI, ntasks;
+  const int2* tasks;        // (m, kc), longest first
+  const double* a;          // a(l, m') at tri_idx(m', l)
+  const double* b;          // b(l, m') at tri_idx(m', l)
+  const double* t1m;        // first rows: Delta_{l m} = t1m 2^t1e at tri_idx(m, l)
+  const int* t1e;
+  const float* ufT;         // U_l[m'] at tri_idx(m', l)
+  uint8_t* A;               // inverse tiles (m, m' / 128, l / 32)
+  const long long* ibase;   // [m * nI + i]: index of the tile of chunk kc is ibase + kc
+  unsigned int* counter;
+};
+
+template <bool SCALED>
+__global__ void __launch_bounds__(kColThreads, 2) lane_recursion_kernel(LaneParams P) {
+  const int lane = threadIdx.x & 31;
+  const int L = P.L;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(P.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= P.ntasks) break;
+    const int2 task = P.tasks[t];
+    const int m = task.x, kc = task.y;
+    const int l = 32 * kc + lane;
+    const int top = min(32 * kc + 31, L - 1);
+    const bool inl = l < L && l >= m;     // degree l exists and has column m
+    const bool wr = inl && l >= P.as;     // U_l vanishes below |s|: those entries stay zero
+    const float um = wr ? __ldg(&P.ufT[tri_idx(m, l, L)]) : 0.f;
+    const double m2 = 2.0 * (double)m;
+    const long long* ib_m = P.ibase + (size_t)m * P.nI;
+    const int im = m >> 7, rowm = m & 127;
+    double cur = 0.0, prev = 0.0;
+    int E = 0;
+    for (int mp = top; mp >= m; --mp) {
+      if (mp == l && inl) {
+        const size_t k = tri_idx(m, l, L);
+        const double mant = __ldg(&P.t1m[k]);
+        const int ex = __ldg(&P.t1e[k]);
+        if (!SCALED || exp_of(mant) + ex >= -1021) {
+          cur = ldexp(mant, ex);
+          E = 0;
+        } else {
+          cur = mant;
+          E = ex;
+        }
+        prev = 0.0;
+      }
+      const bool on = inl && mp <= l;
+      if (on && wr) {
+        const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
+        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, mp & 127, lane, __ldg(&P.ufT[tri_idx(mp, l, L)]) * x);
+        if (mp > m)
+          put_a(P.A, __ldg(&P.ibase[(size_t)mp * P.nI + im]) + kc, rowm, lane, um * (((mp - m) & 1) ? -x : x));
+      }
+      if (on && mp > m) {
+        const size_t k = tri_idx(mp, l, L);
+        const double c = __dmul_rn(m2, __ldg(&P.a[k]));
+        const double t2 = __dmul_rn(__ldg(&P.b[k]), prev);
+        const double nxt = __fma_rn(c, cur, -t2);
+        prev = cur;
+        cur = nxt;
+        if (SCALED && E != 0) {
+          const int x = exp_of(cur);
+          if (x + E >= -1021) {
+            cur = ldexp(cur, E);
+            prev = ldexp(prev, E);
+            E = 0;
+          } else if (x > 512) {
+            cur = __dmul_rn(cur, 0x1p-512);
+            prev = __dmul_rn(prev, 0x1p-512);
+            E += 512;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Plan-time tables of the degree-lane recursion: the first rows (one warp per degree and block of
+// 32 columns, the arithmetic of the column recursion), a(l, m'), b(l, m') from the sqrt tables
+// (the same products as the column recursion's), and U transposed.
+__global__ void lane_first_rows_kernel(int L, const double* __restrict__ sq, const double* __restrict__ rsq,
+                                       double* __restrict__ t1m, int* __restrict__ t1e) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y, m0 = 32 * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)), m = m0 + lane;
+  if (m0 > l) return;  // whole warp
+  int ge;
+  const double v = first_row(l, m0, lane, sq, rsq, &ge);
+  if (m <= l) {
+    const size_t k = tri_idx(m, l, L);
+    t1m[k] = flip_sign(v, ((l - m) & 1) != 0);
+    t1e[k] = ge - l;
+  }
+}
+
+__global__ void lane_coef_kernel(int L, const double* __restrict__ sq, const double* __restrict__ rsq,
+                                 const float* __restrict__ Uf, double* __restrict__ a, double* __restrict__ b,
+                                 float* __restrict__ ufT) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)L * (L + 1) / 2;
+  if (e >= n) return;
+  // e = tri_idx(r, l): the row r from a root, then l
+  long long r = (long long)(((2.0 * L + 1.0) - sqrt((2.0 * L + 1.0) * (2.0 * L + 1.0) - 8.0 * (double)e)) * 0.5);
+  while (r > 0 && (long long)tri_idx(r, r, L) > e) --r;
+  while (r + 1 <= L - 1 && (long long)tri_idx(r + 1, r + 1, L) <= e) ++r;
+  const int rr = (int)r, l = (int)(e - (long long)tri_idx(r, r, L) + r);
+  double av = 0.0, bv = 0.0;
+  if (rr >= 1) {
+    av = __dmul_rn(rsq[l - rr + 1], rsq[l + rr]);
+    bv = __dmul_rn(__dmul_rn(sq[l - rr], sq[l + rr + 1]), av);
+  }
+  a[e] = av;
+  b[e] = bv;
+  ufT[e] = Uf[(size_t)l * (l + 1) / 2 + rr];
+}
+
 }  // namespace
 
 // Tasks (l, b) for every degree l < L and block b <= l / 32 of 32 columns, longest first (a task
@@ -299,6 +445,75 @@ static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATi
 }
 
 cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) { return column_launch(w, L, nullptr, ATiles(), st); }
+
+void lane_tables_free(LaneTables& t) {
+  void* ptrs[] = {t.a, t.b, t.t1m, t.t1e, t.ufT, t.tasks};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  t = LaneTables();
+}
+
+cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC) {
+  cudaError_t e;
+  const size_t n = (size_t)L * (L + 1) / 2;
+  const int as = s < 0 ? -s : s;
+  // tasks (m, kc): column m, degrees of chunk kc from max(m, |s|) on, longest walk first
+  std::vector<int2> tasks;
+  for (int m = 0; m < L; ++m)
+    for (int kc = std::max(m, as) / 32; kc < nC; ++kc) tasks.push_back(make_int2(m, kc));
+  auto len = [L](const int2& x) { return std::min(32 * x.y + 31, L - 1) - x.x; };
+  std::stable_sort(tasks.begin(), tasks.end(), [&](const int2& x, const int2& y) { return len(x) > len(y); });
+  t.ntasks = (int)tasks.size();
+  if ((e = dev_malloc(&t.a, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.b, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.t1m, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.t1e, n * sizeof(int))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.ufT, n * sizeof(float))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.tasks, std::max<size_t>(tasks.size(), 1) * sizeof(int2))) != cudaSuccess) return e;
+  t.bytes = n * (3 * sizeof(double) + sizeof(int) + sizeof(float)) + tasks.size() * sizeof(int2);
+  if (!tasks.empty() &&
+      (e = cudaMemcpy(t.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  const double* sq = w.sqrt_tab;
+  const double* rsq = w.sqrt_tab + (2 * (size_t)L + 4);
+  lane_first_rows_kernel<<<dim3((unsigned)((L + 31) / 32 + 7) / 8, (unsigned)L), 256>>>(L, sq, rsq, t.t1m, t.t1e);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lane_coef_kernel<<<(unsigned)((n + 255) / 256), 256>>>(L, sq, rsq, Uf, t.a, t.b, t.ufT);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(lane_recursion_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lane_recursion_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
+  return cudaDeviceSynchronize();
+}
+
+cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, int L, int s, InvTiles it,
+                                     cudaStream_t st) {
+  if (!it.A || !it.ibase || !t.a || w.method != kDeltaColumn) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  LaneParams P;
+  P.L = L;
+  P.as = s < 0 ? -s : s;
+  P.nI = it.nI;
+  P.ntasks = t.ntasks;
+  P.tasks = t.tasks;
+  P.a = t.a;
+  P.b = t.b;
+  P.t1m = t.t1m;
+  P.t1e = t.t1e;
+  P.ufT = t.ufT;
+  P.A = it.A;
+  P.ibase = it.ibase;
+  P.counter = w.barrier;
+  if (L > 1024)
+    lane_recursion_kernel<true><<<w.blocks, kColThreads, 0, st>>>(P);
+  else
+    lane_recursion_kernel<false><<<w.blocks, kColThreads, 0, st>>>(P);
+  return cudaGetLastError();
+}
 
 cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st) {
   if (!t.A || !t.abase || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;

@@ -147,6 +147,33 @@ ATiles tc_a_tiles(const TcPlan* p);
 // The column recursion writing the A tiles of a 3xTF32 plan directly (no FP64 table):
 // A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, split hi + lo (delta_column.cu).
 cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st);
+// The inverse contraction's A tiles (rows m', K = l) of a 3xTF32 plan: the tile array and, per
+// (m, row block i), the index from which chunk kc's tile is ibase[m * nI + i] + kc.
+struct InvTiles {
+  uint8_t* A = nullptr;
+  const long long* ibase = nullptr;
+  int nI = 0;
+  int nC = 0;
+};
+InvTiles tc_inverse_tiles(const TcPlan* p);
+// Plan-time tables of the recursion with one lane per degree, which writes the inverse's tiles
+// directly (delta_column.cu): coefficients a(l, m'), b(l, m'), first rows (mantissa, exponent), U
+// transposed, in the triangle layout [r][l] (l >= r); its tasks (column m, chunk kc of 32 degrees).
+struct LaneTables {
+  double* a = nullptr;
+  double* b = nullptr;
+  double* t1m = nullptr;
+  int* t1e = nullptr;
+  float* ufT = nullptr;
+  int2* tasks = nullptr;
+  int ntasks = 0;
+  size_t bytes = 0;
+};
+// Needs the column DeltaWork of the plan (its sqrt tables) and U (FP32) on the device; synchronises.
+cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC);
+void lane_tables_free(LaneTables& t);
+cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, int L, int s, InvTiles it,
+                                     cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Fused torus passes of FP32 plans (torus_pass.cu)

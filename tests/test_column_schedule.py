@@ -277,3 +277,67 @@ def test_tile_mode_writes_every_entry_of_A_once(L, s):
     a = np.array([out[k] for k in keys], dtype=np.float64)
     b = np.array([want[k] for k in keys], dtype=np.float64)
     assert np.abs(a - b).max() <= 2e-7 * np.abs(b).max()
+
+
+def inv_layout(L, s):
+    """The inverse A-tile layout (contract_tc.cu tc_setup): item (m, i) holds chunks kc in
+    [c0, nC), c0 = max(max(m, |s|) // 32, 4i); the tile of chunk kc is ibase[m, i] + kc."""
+    nC, nI, at = (L + 31) // 32, (L + 127) // 128, 0
+    ibase = {}
+    for m in range(L):
+        lmin = max(m, abs(s))
+        for i in range(nI):
+            c0 = max(lmin // 32, 4 * i)
+            if c0 < nC:
+                ibase[m, i] = at - c0
+                at += nC - c0
+    return ibase, at
+
+
+def lane_tasks(L, s):
+    nC = (L + 31) // 32
+    t = [(m, kc) for m in range(L) for kc in range(max(m, abs(s)) // 32, nC)]
+    t.sort(key=lambda x: -(min(32 * x[1] + 31, L - 1) - x[0]))
+    return t
+
+
+@pytest.mark.parametrize("L,s", [(40, 2), (97, -1), (150, 0), (140, 35)])
+def test_degree_lane_mode_writes_every_entry_of_the_inverse_A_once(L, s):
+    """The recursion with one lane per degree (the inverse's tiles): A_m[m'][l] = U_l[m'] Delta^l_{m'm}
+    for every 0 <= m, m' <= l < L with l >= |s| lands once at row m' mod 128, K = l mod 32 of the
+    tile of chunk l // 32 of item (m, m' // 128), and each such tile exists."""
+    tab = T.delta_quadrant(L)
+    off = T.delta_offsets(L)
+    ibase, total = inv_layout(L, s)
+    Ds = [tab[off[l]:off[l + 1]].reshape(l + 1, l + 1) for l in range(L)]
+    U = {}
+    for l in range(L):
+        for mp in range(l + 1):
+            d = 0.0 if l < abs(s) else Ds[l][mp, abs(s)] * (-1.0 if (s > 0 and (l + mp) & 1) else 1.0)
+            U[l, mp] = np.float32(np.sqrt((2 * l + 1) / (4 * np.pi)) * d)
+    out = {}
+    for m, kc in lane_tasks(L, s):
+        top = min(32 * kc + 31, L - 1)
+        for mp in range(top, m - 1, -1):
+            for lane in range(32):
+                l = 32 * kc + lane
+                if not (l < L and l >= m and mp <= l and l >= abs(s)):
+                    continue
+                x = np.float32(Ds[l][mp, m])
+                key = (ibase[m, mp // 128] + kc, mp % 128, lane)
+                assert 0 <= key[0] < total and key not in out
+                out[key] = U[l, mp] * x
+                if mp > m:
+                    key = (ibase[mp, m // 128] + kc, m % 128, lane)
+                    assert 0 <= key[0] < total and key not in out
+                    out[key] = U[l, m] * (-x if (mp - m) & 1 else x)
+    want = {}
+    for l in range(abs(s), L):
+        for m in range(l + 1):
+            for mp in range(l + 1):
+                want[(ibase[m, mp // 128] + l // 32, mp % 128, l % 32)] = U[l, mp] * np.float32(Ds[l][mp, m])
+    assert set(out) == set(want)
+    keys = sorted(want)
+    a = np.array([out[k] for k in keys], dtype=np.float64)
+    b = np.array([want[k] for k in keys], dtype=np.float64)
+    assert np.abs(a - b).max() <= 2e-7 * np.abs(b).max()

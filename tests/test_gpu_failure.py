@@ -75,6 +75,8 @@ def test_contraction_pipeline_timeout_is_latched_and_the_plan_recovers(delta_mod
 
 
 def _free_bytes():
+    import gc
+    gc.collect()  # plans of earlier tests give their memory back when collected
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return torch.cuda.mem_get_info()[0]
@@ -93,7 +95,7 @@ def test_allocation_failures_during_plan_creation_release_everything(precision):
                 plan = ssht.Plan(L, s, B, precision=precision)
             except ssht.SshtError as e:
                 assert e.code == ENOMEM, (n, e)
-                assert abs(_free_bytes() - base) < (8 << 20), n
+                assert _free_bytes() > base - (8 << 20), n  # nothing of the failed plan is kept
                 continue
             created = True  # n is past the plan's last allocation: the hook did not fire
             ssht.ssht_debug_fail_allocation(0)
@@ -102,13 +104,14 @@ def test_allocation_failures_during_plan_creation_release_everything(precision):
     finally:
         ssht.ssht_debug_fail_allocation(0)
     assert created and n > 5
-    assert abs(_free_bytes() - base) < (8 << 20)
+    assert _free_bytes() > base - (8 << 20)
     # the library still works
     flm = inputs.coeffs(L, s, B, seed=2)
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     plan = ssht.Plan(L, s, B, precision=precision)
     f = plan.inverse(torch.from_numpy(flm).to(dt).cuda()).cpu().numpy()
     plan.check()
+    plan.close()
     assert rel(f, T.inverse(flm, L, s)) < (1e-12 if precision == "fp64" else 1e-6)
 
 
@@ -122,4 +125,4 @@ def test_allocation_failure_during_group_creation():
         assert e.value.code == ENOMEM
     finally:
         ssht.ssht_debug_fail_allocation(0)
-    assert abs(_free_bytes() - base) < (8 << 20)
+    assert _free_bytes() > base - (8 << 20)

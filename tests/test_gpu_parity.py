@@ -416,8 +416,7 @@ def test_profile_totals_and_trace(precision):
         spans = [(t0, t1) for _, ln, t0, t1 in trace if ln == lane]
         assert all(a[1] <= b[0] + 1e-3 for a, b in zip(spans, spans[1:]))
     aux = {name for name, lane, _, _ in trace if lane == 1}
-    # (3xTF32: the inverse packs its A tiles from the table; the forward's recursion writes them)
-    assert aux == ({"delta", "pack"} if precision == "tf32x3" else {"delta"})
+    assert aux == {"delta"}  # (3xTF32: the recursion writes the A tiles of both directions itself)
     assert sum(1 for name, _, _, _ in trace if name == "delta") == 4
     # the trace was folded into the totals
     totals, launches = plan.profile_read()
