@@ -212,6 +212,13 @@ def column_updates(L):
     return total
 
 
+def lane_updates(L):
+    """Updates of one sweep of the degree-lane recursion: in degree l the lane of column m walks
+    rows l .. m, l - m updates."""
+    l = np.arange(L, dtype=np.float64)
+    return float(np.sum(l * (l + 1) / 2))
+
+
 def quadrant_entries(L):
     """Entries Delta^l_{m'm}, 0 <= m, m' <= l < L (the table, or the A operand, of one sweep)."""
     l = np.arange(L, dtype=np.float64)
@@ -255,8 +262,11 @@ def split_trace(trace, steps):
     names = ["theta_inverse", "phi_inverse", "phi_forward", "theta_forward"]
     for k, d in enumerate(fft):
         out.setdefault(names[k % 4], []).append(d)
+    rec = [t1 - t0 for name, lane, t0, t1 in trace if name == "delta"]
+    for k, d in enumerate(rec):  # one recursion per call: the inverse's, then the forward's
+        out.setdefault("recursion_inverse" if k % 2 == 0 else "recursion_forward", []).append(d)
     for name, lane, t0, t1 in trace:
-        key = {("delta", 1): "recursion", ("delta", 0): "recursion", ("inverse", 0): "contraction_inverse",
+        key = {("inverse", 0): "contraction_inverse",
                ("project", 0): "contraction_forward", ("pack", 0): "pack_data", ("pack", 1): "pack_a",
                ("torus", 0): "torus_glue"}.get((name, lane))
         if key:
@@ -296,7 +306,13 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
     tc = prec in ("tf32x3", "bf16x6")
     for key, v in times.items():
         ms = v["ms"]
-        if key == "recursion":
+        if key == "recursion_inverse" and tc and recursion != "risbo" and prec == "tf32x3":
+            u = lane_updates(L)
+            res[key] = entry("lane_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * 8.0,
+                             {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
+                              "work": "%.3g updates x 3 FP64 instructions (4 flops); writes the inverse's A tiles" % u,
+                              "fp64_probe_tflops": FP64_PROBE_TFLOPS})
+        elif key.startswith("recursion"):
             if recursion == "risbo":
                 nh, ni = recursion_updates(L)
                 res[key] = entry("risbo_kernel", ms, 7.0 * nh + 8.0 * ni, pk["fp64_tflops"], None, quad * 8.0,
@@ -538,7 +554,7 @@ def run_ssht(args):
                     "peak": e["flop_peak"], "unit": "TFLOP/s", "frac": e["flop_frac"],
                     "peak_source": e["flop_peak_source"]}
         roof.update({"kernel": e["kernel"], "stage": dom, "ms_per_launch": e["ms"], "traffic": e["traffic"]})
-        if delta_alone_ms and dom == "recursion":
+        if delta_alone_ms and dom.startswith("recursion"):
             u = column_updates(L)
             roof["alone"] = {"ms": delta_alone_ms, "achieved": 4.0 * u / (delta_alone_ms / 1e3) / 1e12,
                              "note": "the table-writing sweep timed by itself (ssht_wigner_delta)"}
@@ -653,7 +669,7 @@ def run_fp64(args, torch, inputs, ssht, world, device, stream, rank, pk, inv_ora
         plan.check()
         ms = max_over_ranks(e0.elapsed_time(e1), world, device)
         times = {k: v for k, v in split_trace(trace, nrep).items()
-                 if k in ("recursion", "contraction_inverse", "contraction_forward")}
+                 if k in ("recursion_inverse", "recursion_forward", "contraction_inverse", "contraction_forward")}
         line = {"batch": B, "value": throughput(world, B, nrep, ms), "unit": "transforms/s", "ms_per_step": ms / nrep,
                 "steps": nrep, "kernels": kernel_rooflines(times, L, s, B, "fp64", "column", pk)}
         if rank == 0 and not args.no_check:

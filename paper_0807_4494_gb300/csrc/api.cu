@@ -646,7 +646,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (L < 1 || L > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
   if (s <= -L || s >= L) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
   if (nfields < 1 || nfields > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
-  if ((desc->flags & ~(SSHT_FLAG_REAL | SSHT_FLAG_RISBO)) != 0) return fail(SSHT_EINVAL, "unknown flags");
+  if ((desc->flags & ~(SSHT_FLAG_REAL | SSHT_FLAG_RISBO | SSHT_FLAG_TUNE)) != 0) return fail(SSHT_EINVAL, "unknown flags");
   const bool real = (desc->flags & SSHT_FLAG_REAL) != 0;
   if (real && s != 0) return fail(SSHT_EINVAL, "real fields (SSHT_FLAG_REAL) need spin 0");
   if (real && shared) return fail(SSHT_EINVAL, "groups take complex fields only");
@@ -656,8 +656,6 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (desc->precision != SSHT_FP64 && desc->precision != SSHT_FP32 && desc->precision != SSHT_TF32X3 &&
       desc->precision != SSHT_BF16X6)
     return fail(SSHT_EINVAL, "unknown precision");
-  if ((desc->precision == SSHT_TF32X3 || desc->precision == SSHT_BF16X6) && B > 64)
-    return fail(SSHT_EUNSUPPORTED, "tensor-core plans take at most 64 complex fields (128 real fields) per plan");
 
   ssht_plan_t p = new (std::nothrow) ssht_plan_s();
   if (!p) return fail(SSHT_ENOMEM, "host allocation of the plan");
@@ -1253,13 +1251,9 @@ int group_create(ssht_group_t* out, int n, const int* Ls, const int* ss, int pre
       cands.push_back(precision);
     } else {
       cands.push_back(SSHT_FP32);
-      if (b.count <= 64) {
-        cands.push_back(SSHT_TF32X3);
-        cands.push_back(SSHT_BF16X6);
-      }
+      cands.push_back(SSHT_TF32X3);
+      cands.push_back(SSHT_BF16X6);
     }
-    if ((precision == SSHT_TF32X3 || precision == SSHT_BF16X6) && b.count > 64 && !tune)
-      return bail(fail(SSHT_EUNSUPPORTED, "tensor-core buckets take at most 64 fields"));
     float best = 0.f;
     for (int cand : cands) {
       ssht_plan_desc d{L, s, b.count, cand, delta_mode, 0};

@@ -48,7 +48,7 @@ constexpr int TM = kTileRows;              // rows per tile
 constexpr int TK = kTileK;                 // K per chunk (one 128-byte TF32 row)
 constexpr int A_PART = kAPart;             // 16 KB: one split part of an A tile
 constexpr int A_TILE = kATile;             // hi then lo
-constexpr int STAGES = 2;
+constexpr int MAX_STAGES = 4;             // pipeline depth: a plan parameter, 2 .. MAX_STAGES
 constexpr int EPI_WARPS = 8;                       // two per tensor-memory lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer warp, MMA warp, epilogue warps
 
@@ -61,7 +61,8 @@ struct Item {
 };
 
 struct TcArgs {
-  int L, s, B, NC;        // NC = 2H: padded columns, H = 2B rounded up to 16 (<= 128)
+  int L, s, B, NC;        // B: fields of this slice; NC = 2H: padded columns, H = 2 Bs rounded up to 16 (<= 128)
+  int stages;             // pipeline depth
   int nitems;
   const Item* items;
   const uint8_t* A;       // packed A tiles
@@ -135,11 +136,16 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
 constexpr int XPER = 16;  // NC <= 256: 32 * NC / 2 complex values per tile
 
 // Inverse data tile (m, c): V_m[l, j], l = 32 c + k.
+// Fields are packed in slices of Bs (blockIdx.z): slice z holds fields z Bs .. z Bs + Bs - 1 of the
+// batch in its own tile region of xslice bytes.
 template <bool BF>
-__global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int B, int NC, const int* __restrict__ xc0,
-                                                     const long long* __restrict__ xoff,
+__global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int Bs, size_t xslice, int NC,
+                                                     const int* __restrict__ xc0, const long long* __restrict__ xoff,
                                                      const float2* __restrict__ flm, uint8_t* __restrict__ X) {
   extern __shared__ __align__(16) uint8_t tile[];
+  const int B = min(Bs, Btot - (int)blockIdx.z * Bs);
+  flm += (size_t)blockIdx.z * Bs * L * L;
+  X += (size_t)blockIdx.z * xslice;
   const int m = blockIdx.y;
   const int c = xc0[m] + blockIdx.x;
   const int nC = (L + TK - 1) / TK;
@@ -200,7 +206,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int b_part = a.NC * 128;
   const int stage_bytes = A_TILE + 2 * b_part;
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], seg_full[2], seg_empty[2], done_bar;
+  const int STAGES = a.stages;
+  __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], seg_full[2], seg_empty[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
     if (lane == 0) {
       // ---- producer: bulk copies of the A and data tiles of every chunk ----
       int it = 0;
-      int last_use[STAGES] = {-1, -1};
+      int last_use[MAX_STAGES] = {-1, -1, -1, -1};
       for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
         const Item itm = a.items[w];
         const uint8_t* Ab = a.A + (size_t)itm.atile * A_TILE;
@@ -379,6 +386,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
 struct TcPlan {
   int L = 0, s = 0, B = 0, NC = 0, nC = 0, nI = 0;
   bool bf16 = false;  // split-BF16 (3 parts, 6 products) instead of 3xTF32
+  TcConfig cfg;
+  int Bs = 0, nS = 0;        // fields per slice (one GEMM launch each) and slices
+  size_t xslice = 0;         // bytes of one slice's data tiles
+  std::vector<Item> inv_h, fwd_h;  // work items in creation order (re-sorted by the configuration)
   Item* items_inv = nullptr;
   Item* items_fwd = nullptr;
   int n_inv = 0, n_fwd = 0;
@@ -386,17 +397,19 @@ struct TcPlan {
   // Forward A tiles (m, i, c): rows l = 128 i + r, K = m' = 32 c + k, tile index abase[m] +
   // 2i(i+1) - 2 i_m(i_m+1) + c with i_m = m / 128 (each (m, i), i >= i_m, holds 4i + 4 slots;
   // entries nothing writes stay zero).  Inverse A tiles A_inv (m, i, c): rows m' = 128 i + r,
-  // K = l = 32 c + k, at the item's tile index.
+  // K = l = 32 c + k, at the item's tile index.  Both are shared by every slice of fields.
   uint8_t* A = nullptr;
   uint8_t* A_inv = nullptr;
   long long* abase = nullptr;
   long long* ibase = nullptr;  // [m * nI + i]: tile index of chunk kc of inverse item (m, i) is ibase + kc
-  uint8_t* X = nullptr;  // data tiles (shared by both directions; sized for the larger)
+  uint8_t* X = nullptr;        // data tiles, nS slices of xslice bytes
+  size_t xbytes = 0;
   long long* xoff = nullptr;
   int* xc0 = nullptr;
   size_t bytes = 0;
   int grid = 0;
   size_t smem = 0;
+  int smem_max = 0;
 };
 
 static cudaError_t tc_alloc(void** p, size_t bytes, size_t* total) {
@@ -411,19 +424,70 @@ static cudaError_t gemm_attrs(K kernel, int bytes) {
   return e != cudaSuccess ? e : cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+static int nc_of(int Bs) { return 2 * (((2 * Bs + 15) / 16) * 16); }
+static size_t stage_bytes_of(int NC) { return (size_t)A_TILE + 2 * (size_t)NC * 128; }
+
+bool tc_config_fits(const TcPlan* p, const TcConfig& c) {
+  if (c.slice < 1 || c.slice > 64 || c.stages < 2 || c.stages > MAX_STAGES) return false;
+  const int Bs = std::min(c.slice, p->B);
+  return (size_t)c.stages * stage_bytes_of(nc_of(Bs)) + 1024 <= (size_t)p->smem_max;
+}
+
+cudaError_t tc_configure(TcPlan* p, const TcConfig& c) {
+  if (!tc_config_fits(p, c)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const int Bs = std::min(c.slice, p->B), nS = (p->B + Bs - 1) / Bs, NC = nc_of(Bs);
+  const size_t xslice = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * 2 * NC * 128;
+  if (xslice * nS != p->xbytes || !p->X) {
+    if (p->X) {
+      cudaFree(p->X);
+      p->bytes -= p->xbytes;
+      p->X = nullptr;
+    }
+    if ((e = tc_alloc((void**)&p->X, xslice * nS, &p->bytes)) != cudaSuccess) return e;
+    p->xbytes = xslice * nS;
+  }
+  p->Bs = Bs;
+  p->nS = nS;
+  p->NC = NC;
+  p->xslice = xslice;
+  // Work order.  Inverse: the row blocks of each group of 4 consecutive m run together, so that
+  // their data tiles are read from HBM about once (ncu, L = 1024, B = 64: 7.1 -> 5.8 GB read), or
+  // longest first.  Forward: longest first (neighbouring m together, which lets L2 merge their
+  // scattered output writes) or grouped like the inverse.
+  auto grouped = [](const Item& x, const Item& y) {
+    if (x.m / 4 != y.m / 4) return x.m / 4 < y.m / 4;
+    if (x.i != y.i) return x.i > y.i;
+    return x.m < y.m;
+  };
+  auto longest_first = [](const Item& x, const Item& y) { return (x.c1 - x.c0) > (y.c1 - y.c0); };
+  std::vector<Item> inv = p->inv_h, fwd = p->fwd_h;
+  if (c.inv_order == 0) std::stable_sort(inv.begin(), inv.end(), grouped);
+  else std::stable_sort(inv.begin(), inv.end(), longest_first);
+  if (c.fwd_order == 0) std::stable_sort(fwd.begin(), fwd.end(), longest_first);
+  else std::stable_sort(fwd.begin(), fwd.end(), grouped);
+  if ((e = cudaMemcpy(p->items_inv, inv.data(), inv.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(p->items_fwd, fwd.data(), fwd.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  p->smem = (size_t)c.stages * stage_bytes_of(NC) + 1024;
+  p->cfg = c;
+  return cudaSuccess;
+}
+
+TcConfig tc_config(const TcPlan* p) { return p->cfg; }
+
 cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   *out = nullptr;
-  if (B < 1 || B > 64) return cudaErrorInvalidValue;
+  if (B < 1) return cudaErrorInvalidValue;
   TcPlan* p = new TcPlan();
   p->bf16 = bf16 != 0;
   p->L = L;
   p->s = s;
   p->B = B;
-  p->NC = 2 * (((2 * B + 15) / 16) * 16);
   p->nC = (L + TK - 1) / TK;
   p->nI = (L + TM - 1) / TM;
   const int as = s < 0 ? -s : s;
-  std::vector<Item> inv, fwd;
+  std::vector<Item>& inv = p->inv_h;
+  std::vector<Item>& fwd = p->fwd_h;
   std::vector<long long> xoff(L), abase(L), ibase((size_t)L * std::max(1, (L + TM - 1) / TM), 0);
   std::vector<int> xc0(L);
   long long at = 0, ft = 0, xt = 0;
@@ -448,19 +512,6 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
       }
     }
   }
-  // Inverse: the row blocks of each group of 4 consecutive m run together, so that their data
-  // tiles are read from HBM about once (ncu, L = 1024, B = 64: 7.1 -> 5.8 GB read, 1.19 -> 1.06
-  // ms), dealt round-robin to one CTA fewer than the SMs so that every CTA gets every item length.
-  // Forward: longest first; there the blocks of neighbouring m run together, which lets L2 merge
-  // their scattered output writes (grouping by m raised its writes from 1.0 to 1.6 GB).
-  auto grouped = [](const Item& x, const Item& y) {
-    if (x.m / 4 != y.m / 4) return x.m / 4 < y.m / 4;
-    if (x.i != y.i) return x.i > y.i;
-    return x.m < y.m;
-  };
-  auto longest_first = [](const Item& x, const Item& y) { return (x.c1 - x.c0) > (y.c1 - y.c0); };
-  std::stable_sort(inv.begin(), inv.end(), grouped);
-  std::stable_sort(fwd.begin(), fwd.end(), longest_first);
   p->n_inv = (int)inv.size();
   p->n_fwd = (int)fwd.size();
   p->tiles_A = ft;
@@ -468,7 +519,13 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   p->xtiles_inv = xt;
   p->xtiles_fwd = (long long)L * p->nC;
   cudaError_t e;
-  const size_t xbytes = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * 2 * p->NC * 128;
+  {
+    int sms = 0, optin = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) goto fail;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) goto fail;
+    p->grid = sms;
+    p->smem_max = optin - 2048;  // the kernel's static shared memory and alignment slack
+  }
   if ((e = tc_alloc((void**)&p->items_inv, inv.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->A, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
@@ -482,35 +539,29 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   if ((e = cudaMemcpy(p->ibase, ibase.data(), ibase.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
     goto fail;
   if ((e = tc_alloc((void**)&p->abase, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = tc_alloc((void**)&p->X, xbytes, &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xoff, L * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->xc0, L * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = cudaMemcpy(p->items_inv, inv.data(), inv.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
-  if ((e = cudaMemcpy(p->items_fwd, fwd.data(), fwd.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->abase, abase.data(), L * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->xoff, xoff.data(), L * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->xc0, xc0.data(), L * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) goto fail;
   {
-    int sms = 0;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) goto fail;
-    p->grid = sms;
-    p->smem = (size_t)STAGES * (A_TILE + 2 * p->NC * 128) + 1024;
-    // Function attributes are process-wide upper bounds: set them for the largest column count
-    // (NC = 256) so that plans of other batch sizes can launch with their own amounts.
-    const int gemm_max = STAGES * (A_TILE + 2 * 256 * 128) + 1024, xsmem_max = 2 * 256 * 128;
+    // Function attributes are process-wide upper bounds: the device's limit, so that plans of
+    // every configuration can launch with their own amounts.
+    const int xsmem_max = 2 * 256 * 128;
     if ((e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
         (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
       goto fail;
     if (p->bf16) {
-      if ((e = gemm_attrs(tc_gemm_kernel<false, true>, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(tc_gemm_kernel<true, true>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, true>, p->smem_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, true>, p->smem_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(pack_v_kernel<true>, xsmem_max)) != cudaSuccess) goto fail;
     } else {
-      if ((e = gemm_attrs(tc_gemm_kernel<false, false>, gemm_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(tc_gemm_kernel<true, false>, gemm_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<false, false>, p->smem_max)) != cudaSuccess) goto fail;
+      if ((e = gemm_attrs(tc_gemm_kernel<true, false>, p->smem_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(pack_v_kernel<false>, xsmem_max)) != cudaSuccess) goto fail;
     }
   }
+  if ((e = tc_configure(p, TcConfig())) != cudaSuccess) goto fail;
   *out = p;
   return cudaSuccess;
 fail:
@@ -565,11 +616,13 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* 
 
 cudaError_t tc_pack_data(TcPlan* p, const void* src, cudaStream_t st, int* launches) {
   const int xsmem = 2 * p->NC * 128;
-  const dim3 g(p->nC, p->L);
+  const dim3 g(p->nC, p->L, p->nS);
   if (p->bf16)
-    pack_v_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);
+    pack_v_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
+                                               (const float2*)src, p->X);
   else
-    pack_v_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->NC, p->xc0, p->xoff, (const float2*)src, p->X);
+    pack_v_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
+                                                (const float2*)src, p->X);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -580,37 +633,46 @@ TileOut tc_forward_tiles(const TcPlan* p) {
   o.NC = p->NC;
   o.nC = p->nC;
   o.mode = p->bf16 ? 2 : 1;
+  o.Bs = p->Bs;
+  o.xslice = p->xslice;
   return o;
 }
 
 cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* status, long long wait_ns, cudaStream_t st,
                     int* launches) {
-  TcArgs a;
-  a.L = p->L;
-  a.s = p->s;
-  a.B = p->B;
-  a.NC = p->NC;
-  a.nitems = forward ? p->n_fwd : p->n_inv;
-  a.items = forward ? p->items_fwd : p->items_inv;
-  a.A = forward ? p->A : p->A_inv;
-  a.X = p->X;
-  a.xoff = p->xoff;
-  a.xc0 = p->xc0;
-  a.ph = (const float2*)ph;
-  a.out = (float2*)out;
-  a.status = status;
-  a.wait_ns = wait_ns;
-  const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
-  if (forward && p->bf16)
-    tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
-  else if (forward)
-    tc_gemm_kernel<true, false><<<grid, THREADS, p->smem, st>>>(a);
-  else if (p->bf16)
-    tc_gemm_kernel<false, true><<<grid, THREADS, p->smem, st>>>(a);
-  else
-    tc_gemm_kernel<false, false><<<grid, THREADS, p->smem, st>>>(a);
-  *launches += 1;
-  return cudaGetLastError();
+  // one launch per slice of fields; every slice reads the same A tiles
+  for (int sl = 0; sl < p->nS; ++sl) {
+    TcArgs a;
+    a.L = p->L;
+    a.s = p->s;
+    a.B = std::min(p->Bs, p->B - sl * p->Bs);
+    a.NC = p->NC;
+    a.stages = p->cfg.stages;
+    a.nitems = forward ? p->n_fwd : p->n_inv;
+    a.items = forward ? p->items_fwd : p->items_inv;
+    a.A = forward ? p->A : p->A_inv;
+    a.X = p->X + (size_t)sl * p->xslice;
+    a.xoff = p->xoff;
+    a.xc0 = p->xc0;
+    a.ph = (const float2*)ph;
+    const size_t per_field = forward ? (size_t)p->L * p->L : (size_t)(2 * p->L - 1) * p->L;
+    a.out = (float2*)out + (size_t)sl * p->Bs * per_field;
+    a.status = status;
+    a.wait_ns = wait_ns;
+    const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
+    if (forward && p->bf16)
+      tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
+    else if (forward)
+      tc_gemm_kernel<true, false><<<grid, THREADS, p->smem, st>>>(a);
+    else if (p->bf16)
+      tc_gemm_kernel<false, true><<<grid, THREADS, p->smem, st>>>(a);
+    else
+      tc_gemm_kernel<false, false><<<grid, THREADS, p->smem, st>>>(a);
+    *launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace ssht

@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
     }
 
     // ---- rows m' = l .. m0 ----
+    // tile output: the base of row M = m' (a load), fetched one step ahead
+    long long abase_cur = TILES ? __ldg(&P.abase[l]) : 0, abase_next = 0;
     for (int mp = l; mp >= m0; --mp) {
+      if (TILES && mp > m0) abase_next = __ldg(&P.abase[mp - 1]);
       const int j = mp & 31;
       if (mp == l || j == 31) {
         // coefficients a(m'), b(m') of the chunk of m' in [mp & ~31, (mp & ~31) + 31]
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
       if constexpr (TILES) {
         if (act) {
           const int im = mp >> 7;
-          const long long tile = __ldg(&P.abase[mp]) + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
+          const long long tile = abase_cur + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
           put_a(P.A, tile, trow, lane, u_lane * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
         }
       } else {
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
           }
         }
       }
+      if (TILES) abase_cur = abase_next;
     }
   }
 }
@@ -266,7 +270,7 @@ struct LaneParams {
 };
 
 template <bool SCALED>
-__global__ void __launch_bounds__(kColThreads, 2) lane_recursion_kernel(LaneParams P) {
+__global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LaneParams P) {
   const int lane = threadIdx.x & 31;
   const int L = P.L;
   for (;;) {
@@ -286,7 +290,29 @@ __global__ void __launch_bounds__(kColThreads, 2) lane_recursion_kernel(LanePara
     const int im = m >> 7, rowm = m & 127;
     double cur = 0.0, prev = 0.0;
     int E = 0;
+    // the per-step loads (coefficients, U, tile base) of row m' are issued one step ahead, so
+    // that their latency overlaps the previous step's FP64 chain
+    auto fetch = [&](int r, double& a_, double& b_, float& u_, long long& t_) {
+      a_ = 0.0;
+      b_ = 0.0;
+      u_ = 0.f;
+      if (inl && r <= l) {
+        const size_t k = tri_idx(r, l, L);
+        a_ = __ldg(&P.a[k]);
+        b_ = __ldg(&P.b[k]);
+        u_ = __ldg(&P.ufT[k]);
+      }
+      t_ = __ldg(&P.ibase[(size_t)r * P.nI + im]);
+    };
+    double ca, cb;
+    float cu;
+    long long ct;
+    fetch(top, ca, cb, cu, ct);
     for (int mp = top; mp >= m; --mp) {
+      double na = 0.0, nb = 0.0;
+      float nu = 0.f;
+      long long nt = 0;
+      if (mp > m) fetch(mp - 1, na, nb, nu, nt);
       if (mp == l && inl) {
         const size_t k = tri_idx(m, l, L);
         const double mant = __ldg(&P.t1m[k]);
@@ -303,14 +329,12 @@ __global__ void __launch_bounds__(kColThreads, 2) lane_recursion_kernel(LanePara
       const bool on = inl && mp <= l;
       if (on && wr) {
         const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
-        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, mp & 127, lane, __ldg(&P.ufT[tri_idx(mp, l, L)]) * x);
-        if (mp > m)
-          put_a(P.A, __ldg(&P.ibase[(size_t)mp * P.nI + im]) + kc, rowm, lane, um * (((mp - m) & 1) ? -x : x));
+        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, mp & 127, lane, cu * x);
+        if (mp > m) put_a(P.A, ct + kc, rowm, lane, um * (((mp - m) & 1) ? -x : x));
       }
       if (on && mp > m) {
-        const size_t k = tri_idx(mp, l, L);
-        const double c = __dmul_rn(m2, __ldg(&P.a[k]));
-        const double t2 = __dmul_rn(__ldg(&P.b[k]), prev);
+        const double c = __dmul_rn(m2, ca);
+        const double t2 = __dmul_rn(cb, prev);
         const double nxt = __fma_rn(c, cur, -t2);
         prev = cur;
         cur = nxt;
@@ -327,6 +351,10 @@ __global__ void __launch_bounds__(kColThreads, 2) lane_recursion_kernel(LanePara
           }
         }
       }
+      ca = na;
+      cb = nb;
+      cu = nu;
+      ct = nt;
     }
   }
 }
@@ -480,6 +508,15 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   lane_coef_kernel<<<(unsigned)((n + 255) / 256), 256>>>(L, sq, rsq, Uf, t.a, t.b, t.ufT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lane_recursion_kernel<false>, kColThreads, 0)) !=
+        cudaSuccess)
+      return e;
+    t.blocks = sms * std::max(1, std::min(per_sm, 4));
+  }
   if ((e = cudaFuncSetAttribute(lane_recursion_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
     return e;
@@ -509,9 +546,9 @@ cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, in
   P.ibase = it.ibase;
   P.counter = w.barrier;
   if (L > 1024)
-    lane_recursion_kernel<true><<<w.blocks, kColThreads, 0, st>>>(P);
+    lane_recursion_kernel<true><<<t.blocks, kColThreads, 0, st>>>(P);
   else
-    lane_recursion_kernel<false><<<w.blocks, kColThreads, 0, st>>>(P);
+    lane_recursion_kernel<false><<<t.blocks, kColThreads, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -112,11 +112,24 @@ template <typename T> cudaError_t real_unpack_coeffs(int L, int nreal, const voi
 cudaError_t real_setup();
 
 // ---------------------------------------------------------------------------
-// Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16, at most 64 fields per plan
+// Tensor-core contractions (contract_tc.cu), 3xTF32 or split-BF16
 // ---------------------------------------------------------------------------
 struct TcPlan;
-// bf16 = 0: 3xTF32 split products; bf16 = 1: split-BF16 (three parts, six products).
+// The contraction's tunable shape: fields per GEMM launch (the N tile: 2 x 2 x slice real columns,
+// padded to 16), pipeline depth (stages of A and data tiles in shared memory), and the order of the
+// work items (inverse: 0 grouped by m, 1 longest first; forward: 0 longest first, 1 grouped by m).
+struct TcConfig {
+  int slice = 64;
+  int stages = 2;
+  int inv_order = 0;
+  int fwd_order = 0;
+};
+// bf16 = 0: 3xTF32 split products; bf16 = 1: split-BF16 (three parts, six products).  Any batch:
+// the fields run in slices of at most 64.
 cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device);
+bool tc_config_fits(const TcPlan* p, const TcConfig& c);  // within the device's shared memory
+cudaError_t tc_configure(TcPlan* p, const TcConfig& c);    // reallocates the data tiles if needed
+TcConfig tc_config(const TcPlan* p);
 void tc_destroy(TcPlan* p);
 size_t tc_bytes(const TcPlan* p);
 // Pack the A operand (U_l[m'] Delta^l_{m'm} in FP32, then split) of one direction from the FP64
@@ -135,6 +148,8 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
 struct TileOut {
   uint8_t* X = nullptr;
   int NC = 0, nC = 0, mode = 0;
+  int Bs = 64;        // fields per slice; slice z of the fields has its tiles at X + z * xslice
+  size_t xslice = 0;
 };
 TileOut tc_forward_tiles(const TcPlan* p);
 // Where the recursion can write the A operand itself (3xTF32 plans): the forward tile array and
@@ -167,6 +182,7 @@ struct LaneTables {
   float* ufT = nullptr;
   int2* tasks = nullptr;
   int ntasks = 0;
+  int blocks = 0;  // grid of the recursion kernel
   size_t bytes = 0;
 };
 // Needs the column DeltaWork of the plan (its sqrt tables) and U (FP32) on the device; synchronises.

@@ -336,10 +336,12 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
 // mod 32, the negative-m half carrying (-1)^{m'}): both parts of v, split.  The m = 0 tile's
 // negative half and the padding rows b >= B are written as zeros by the passes of m = 0 and of
 // the last field.
-__device__ __forceinline__ void put_tile(const TileOut& to, int b, int B, int mm, int mp, float2 v) {
+__device__ __forceinline__ void put_tile(const TileOut& to, int bg, int Bg, int mm, int mp, float2 v) {
+  // field bg of Bg lies in slice bg / Bs, as field b of its B fields
+  const int sl = bg / to.Bs, b = bg - sl * to.Bs, B = min(to.Bs, Bg - sl * to.Bs);
   const int am = mm < 0 ? -mm : mm, sign = mm < 0 ? 1 : 0;
   const int pb = to.NC * 128, half = to.NC / 2, k = mp & 31;
-  uint8_t* tile = to.X + ((size_t)am * to.nC + (mp >> 5)) * 2 * pb;
+  uint8_t* tile = to.X + (size_t)sl * to.xslice + ((size_t)am * to.nC + (mp >> 5)) * 2 * pb;
   if (sign && (mp & 1)) v = make_float2(-v.x, -v.y);
   auto put = [&](int row, float x) {
     if (to.mode == 2) tc::put_split<true>(tile, pb, row, k, x);
