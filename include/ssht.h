@@ -85,6 +85,12 @@ typedef enum {
                            * from the closed-form first row Delta_{l m}).  Both give Delta^l to
                            * rounding; the default needs no hand-off between degrees and about a
                            * third of the FP64 instructions. */
+#define SSHT_FLAG_TUNE 4  /* tensor-core plans: at creation, time the contraction's shape candidates
+                           * (fields per GEMM launch 64/32/16, pipeline depth 2-4, work order) on the
+                           * plan's own operands and keep the fastest; with the environment variable
+                           * SSHT_TUNE_CACHE naming a file, choices are read from it (no timing) and
+                           * appended to it after tuning, one JSON object per line keyed by
+                           * "L=.. s=.. B=.. precision".  Ignored by the other precisions. */
 
 typedef struct {
   int L;          /* exclusive band-limit, 1 <= L <= 2048                      */
@@ -92,7 +98,7 @@ typedef struct {
   int batch;      /* number of fields per call, 1 <= batch <= 65535            */
   int precision;  /* ssht_precision                                            */
   int delta_mode; /* ssht_delta_mode                                           */
-  int flags;      /* 0 or SSHT_FLAG_REAL and / or SSHT_FLAG_RISBO              */
+  int flags;      /* 0 or any of SSHT_FLAG_REAL, SSHT_FLAG_RISBO, SSHT_FLAG_TUNE */
 } ssht_plan_desc;
 
 typedef struct ssht_plan_s* ssht_plan_t;
@@ -104,8 +110,8 @@ SSHT_API int ssht_plan(ssht_plan_t* out, int L, int s, int batch);
 
 /* Create a plan from a descriptor (precision and Delta mode).  With SSHT_DELTA_CACHE the
  * recursion runs here, synchronously, and its table stays resident in device memory.
- * The tensor-core precisions (SSHT_TF32X3, SSHT_BF16X6) take at most 64 fields per plan;
- * a larger batch returns SSHT_EUNSUPPORTED. */
+ * The tensor-core precisions (SSHT_TF32X3, SSHT_BF16X6) take any batch: the contraction runs the
+ * fields in slices of at most 64 (one GEMM launch each, all reading the same A operand). */
 SSHT_API int ssht_plan_ex(ssht_plan_t* out, const ssht_plan_desc* desc);
 
 /* Release every resource of a plan (NULL is accepted).  Synchronises the device. */
@@ -211,8 +217,9 @@ typedef struct ssht_group_s* ssht_group_t;
  * Fields are bucketed by (L, s) and each bucket is transformed by one plan of the given
  * precision and Delta mode; buckets of the same L share one Delta table (recompute mode: one
  * recursion per distinct L per call; cache mode: made here).  tune != 0 (FP32-class
- * precisions only) times the FP32, 3xTF32 and split-BF16 contractions on each bucket (the
- * tensor-core forms up to 64 fields) and keeps the fastest.  Synchronises the device. */
+ * precisions only) times the FP32, 3xTF32 and split-BF16 contractions on each bucket, the
+ * tensor-core forms each with their own tuned shape (SSHT_FLAG_TUNE, SSHT_TUNE_CACHE), and keeps
+ * the fastest.  Synchronises the device. */
 SSHT_API int ssht_group_create(ssht_group_t* out, int n, const int* L, const int* s, int precision,
                                int delta_mode, int tune);
 SSHT_API int ssht_group_destroy(ssht_group_t group);
@@ -242,6 +249,9 @@ SSHT_API int ssht_group_adjoint(ssht_group_t group, const void* f, void* flm, vo
 SSHT_API int ssht_group_capture(ssht_group_t group, const void* flm, void* f, void* flm_out, void* stream);
 SSHT_API int ssht_group_replay(ssht_group_t group, void* stream);
 
+/* ssht_plan_tile_config of bucket `bucket` (in the order of ssht_group_buckets). */
+SSHT_API int ssht_group_bucket_tile_config(ssht_group_t group, int bucket, int* cfg);
+
 /* Wait for the group's work and report a latched kernel-side timeout (SSHT_ETIMEOUT). */
 SSHT_API int ssht_group_check(ssht_group_t group);
 
@@ -250,6 +260,12 @@ SSHT_API int ssht_group_check(ssht_group_t group);
  * returning cudaErrorMemoryAllocation); n = 0 disables it.  Plan and group creation then return
  * SSHT_ENOMEM after releasing what they had allocated.  n < 0 returns SSHT_EINVAL. */
 SSHT_API int ssht_debug_fail_allocation(int n);
+
+/* The tensor-core contraction's shape (the paper has no counterpart): cfg[0] fields per GEMM
+ * launch, cfg[1] pipeline stages, cfg[2] inverse work order (0 grouped by m, 1 longest first),
+ * cfg[3] forward work order (0 longest first, 1 grouped by m).  SSHT_EUNSUPPORTED for plans
+ * without tensor-core contraction. */
+SSHT_API int ssht_plan_tile_config(ssht_plan_t plan, int* cfg);
 
 /* Spin limit of the plan's device-side waits, in nanoseconds of the device clock (default 10^9, one
  * second): the Risbo recursion's hand-offs between CTAs (SSHT_FLAG_RISBO plans) and the

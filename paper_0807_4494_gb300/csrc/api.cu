@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -613,6 +615,134 @@ int real_call(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t 
   return 0;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tile tuning of the tensor-core contraction (SSHT_FLAG_TUNE, and the tuned buckets of groups):
+// every shape candidate -- fields per GEMM launch, pipeline depth, work order -- is timed on the
+// plan's own operands (inverse + forward contractions, CUDA events) and the fastest kept.  With
+// SSHT_TUNE_CACHE naming a file, choices are looked up there first and stored after tuning, one
+// JSON object per line: {"key": "L=1024 s=2 B=64 tf32x3", "slice": 64, "stages": 2, ...}.
+// ---------------------------------------------------------------------------------------------
+std::string tune_key(const ssht_plan_s* p) {
+  return "L=" + std::to_string(p->d.L) + " s=" + std::to_string(p->s) + " B=" + std::to_string(p->B) +
+         (p->precision == SSHT_BF16X6 ? " bf16x6" : " tf32x3");
+}
+
+bool tune_cache_lookup(const std::string& key, TcConfig* c) {
+  const char* path = std::getenv("SSHT_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  const std::string want = "{\"key\": \"" + key + "\",";
+  while (std::fgets(line, sizeof line, f)) {
+    if (std::strncmp(line, want.c_str(), want.size()) != 0) continue;
+    TcConfig t;
+    if (std::sscanf(line + want.size(), " \"slice\": %d, \"stages\": %d, \"inv_order\": %d, \"fwd_order\": %d", &t.slice,
+                    &t.stages, &t.inv_order, &t.fwd_order) == 4) {
+      *c = t;
+      found = true;  // the last entry of a key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_cache_store(const std::string& key, const TcConfig& c, float ms) {
+  const char* path = std::getenv("SSHT_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "{\"key\": \"%s\", \"slice\": %d, \"stages\": %d, \"inv_order\": %d, \"fwd_order\": %d, \"ms\": %.4f}\n",
+               key.c_str(), c.slice, c.stages, c.inv_order, c.fwd_order, ms);
+  std::fclose(f);
+}
+
+int make_operands(ssht_plan_t p, int forward, cudaStream_t st);
+
+// Mean milliseconds of one inverse + one forward contraction of the plan's current shape.
+int time_contractions(ssht_plan_t p, cudaStream_t st, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SSHT_CUDA(cudaEventCreate(&e0), "tuning event");
+  SSHT_CUDA(cudaEventCreate(&e1), "tuning event");
+  int n = 0, rc = 0;
+  for (int it = 0; it < 4 && !rc; ++it) {
+    if (it == 1) cudaEventRecord(e0, st);
+    cudaError_t e = tc_gemm(p->tc, 0, p->W1, p->ph, p->delta.status, p->wait_ns, st, &n);
+    if (e == cudaSuccess) e = tc_gemm(p->tc, 1, p->W2, p->ph, p->delta.status, p->wait_ns, st, &n);
+    if (e != cudaSuccess) rc = fail(SSHT_ECUDA, std::string("tuning contraction: ") + cudaGetErrorString(e));
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / 3.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int tune_tiles(ssht_plan_t p) {
+  if (!p->tc) return 0;
+  TcConfig best = tc_config(p->tc);
+  const std::string key = tune_key(p);
+  if (tune_cache_lookup(key, &best) && tc_config_fits(p->tc, best)) {
+    SSHT_CUDA(tc_configure(p->tc, best), "tile configuration");
+    return 0;
+  }
+  cudaStream_t st = nullptr;
+  SSHT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "tuning stream");
+  auto done = [&](int rc) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+  };
+  int rc = 0;
+  // the operands of both directions, once (the data tiles' values do not change the timing)
+  if ((rc = make_operands(p, 0, st)) || (rc = make_operands(p, 1, st))) return done(rc);
+  float best_ms = 0.f;
+  bool have = false;
+  auto trial = [&](const TcConfig& c) {
+    if (!tc_config_fits(p->tc, c)) return 0;
+    cudaError_t e = tc_configure(p->tc, c);
+    if (e != cudaSuccess) return fail(SSHT_ECUDA, std::string("tile configuration: ") + cudaGetErrorString(e));
+    float ms = 0.f;
+    int r = time_contractions(p, st, &ms);
+    if (r) return r;
+    if (!have || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+      have = true;
+    }
+    return 0;
+  };
+  std::vector<int> slices;
+  for (int sl : {64, 32, 16}) {
+    const int bs = std::min(sl, p->B);
+    if (std::find(slices.begin(), slices.end(), bs) == slices.end()) slices.push_back(bs);
+  }
+  for (int sl : slices)
+    for (int stg = 2; stg <= 4; ++stg) {
+      TcConfig c;
+      c.slice = sl;
+      c.stages = stg;
+      if ((rc = trial(c))) return done(rc);
+    }
+  const TcConfig shape = best;
+  for (int io = 0; io < 2; ++io)
+    for (int fo = 0; fo < 2; ++fo) {
+      if (io == shape.inv_order && fo == shape.fwd_order) continue;
+      TcConfig c = shape;
+      c.inv_order = io;
+      c.fwd_order = fo;
+      if ((rc = trial(c))) return done(rc);
+    }
+  cudaError_t e = tc_configure(p->tc, best);
+  if (e != cudaSuccess) return done(fail(SSHT_ECUDA, std::string("tile configuration: ") + cudaGetErrorString(e)));
+  tune_cache_store(key, best, best_ms);
+  return done(0);
+}
+
 void release(ssht_plan_t p) {
   if (!p) return;
   cudaDeviceSynchronize();
@@ -816,6 +946,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     }
     p->delta_ready = true;
   }
+  if ((desc->flags & SSHT_FLAG_TUNE) && (rc = tune_tiles(p))) return bail(rc);
   *out = p;
   g_last_error.clear();
   return SSHT_OK;
@@ -960,6 +1091,17 @@ int ssht_plan_check(ssht_plan_t p) {
                                    ((st & kStatusBarrierTimeout) && (st & 2) ? ", " : "") +
                                    ((st & 2) ? "tensor-core pipeline" : "") + ")");
   }
+  return SSHT_OK;
+}
+
+int ssht_plan_tile_config(ssht_plan_t p, int* cfg) {
+  if (!p || !cfg) return fail(SSHT_EINVAL, "null argument");
+  if (!p->tc) return fail(SSHT_EUNSUPPORTED, "the plan has no tensor-core contraction");
+  const TcConfig c = tc_config(p->tc);
+  cfg[0] = c.slice;
+  cfg[1] = c.stages;
+  cfg[2] = c.inv_order;
+  cfg[3] = c.fwd_order;
   return SSHT_OK;
 }
 
@@ -1256,7 +1398,8 @@ int group_create(ssht_group_t* out, int n, const int* Ls, const int* ss, int pre
     }
     float best = 0.f;
     for (int cand : cands) {
-      ssht_plan_desc d{L, s, b.count, cand, delta_mode, 0};
+      ssht_plan_desc d{L, s, b.count, cand, delta_mode,
+                       (tune && (cand == SSHT_TF32X3 || cand == SSHT_BF16X6)) ? SSHT_FLAG_TUNE : 0};
       ssht_plan_t p = nullptr;
       int rc = create(&p, &d, &g->holders[b.holder].dw);
       if (rc) return bail(rc);
@@ -1317,6 +1460,12 @@ int ssht_group_buckets(ssht_group_t g, int* nbuckets, int* L, int* s, int* count
     if (precision) precision[i] = g->buckets[i].plan->precision;
   }
   return SSHT_OK;
+}
+
+int ssht_group_bucket_tile_config(ssht_group_t g, int bucket, int* cfg) {
+  if (!g || !cfg) return fail(SSHT_EINVAL, "null argument");
+  if (bucket < 0 || bucket >= (int)g->buckets.size()) return fail(SSHT_EINVAL, "no such bucket");
+  return ssht_plan_tile_config(g->buckets[bucket].plan, cfg);
 }
 
 static int group_entry(ssht_group_t g, int which, const void* in, void* out, void* stream) {

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libssht.so")
 FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
 FLAG_REAL = 1
 FLAG_RISBO = 2
+FLAG_TUNE = 4
 RECOMPUTE, CACHE = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
 ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
@@ -25,7 +26,8 @@ EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspac
            "ssht_plan_profile_read", "ssht_plan_profile_trace", "ssht_wigner_delta_noalloc", "ssht_group_create", "ssht_group_destroy",
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
-           "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_last_error", "ssht_version")
+           "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_plan_tile_config",
+           "ssht_group_bucket_tile_config", "ssht_last_error", "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
 
 
@@ -81,6 +83,8 @@ def _lib():
             "ssht_group_check": ([vp], i),
             "ssht_debug_fail_allocation": ([i], i),
             "ssht_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
+            "ssht_plan_tile_config": ([vp, ctypes.POINTER(i)], i),
+            "ssht_group_bucket_tile_config": ([vp, i, ctypes.POINTER(i)], i),
             "ssht_last_error": ([], ctypes.c_char_p),
             "ssht_version": ([], i),
         }
@@ -156,6 +160,18 @@ def ssht_plan_set_wait_limit(h, ns):
     _check(_lib().ssht_plan_set_wait_limit(h, int(ns)), "ssht_plan_set_wait_limit")
 
 
+def ssht_plan_tile_config(h):
+    cfg = (ctypes.c_int * 4)()
+    _check(_lib().ssht_plan_tile_config(h, cfg), "ssht_plan_tile_config")
+    return {"slice": cfg[0], "stages": cfg[1], "inv_order": cfg[2], "fwd_order": cfg[3]}
+
+
+def ssht_group_bucket_tile_config(h, bucket):
+    cfg = (ctypes.c_int * 4)()
+    _check(_lib().ssht_group_bucket_tile_config(h, int(bucket), cfg), "ssht_group_bucket_tile_config")
+    return {"slice": cfg[0], "stages": cfg[1], "inv_order": cfg[2], "fwd_order": cfg[3]}
+
+
 def ssht_plan_profile(h, enable):
     _check(_lib().ssht_plan_profile(h, int(bool(enable))), "ssht_plan_profile")
 
@@ -209,7 +225,8 @@ class Plan:
     recursion the paper uses instead of the default three-term relation in m'.
     """
 
-    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False, recursion="column"):
+    def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False, recursion="column",
+                 tune=False):
         self.L, self.s, self.batch = int(L), int(s), int(batch)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.delta_mode = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
@@ -219,7 +236,7 @@ class Plan:
         self.grid_dtype = (torch.float64 if self.precision == FP64 else torch.float32) if self.real else self.dtype
         if recursion not in ("column", "risbo"):
             raise ValueError("recursion must be 'column' or 'risbo'")
-        flags = (FLAG_REAL if self.real else 0) | (FLAG_RISBO if recursion == "risbo" else 0)
+        flags = (FLAG_REAL if self.real else 0) | (FLAG_RISBO if recursion == "risbo" else 0) | (FLAG_TUNE if tune else 0)
         self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode, flags)
 
     def close(self):
@@ -304,6 +321,10 @@ class Plan:
 
     def check(self):
         ssht_plan_check(self._h)
+
+    def tile_config(self):
+        """Shape of the tensor-core contraction (fields per launch, stages, work orders)."""
+        return ssht_plan_tile_config(self._h)
 
     def set_wait_limit(self, ns):
         """Spin limit of the plan's device-side waits in nanoseconds (<= 0: the default, 1 s)."""
@@ -403,6 +424,10 @@ class Group:
     def buckets(self):
         """[(L, s, fields, precision)] per bucket, precision after tuning."""
         return ssht_group_buckets(self._h)
+
+    def bucket_tile_config(self, i):
+        """Tensor-core shape of bucket i (SshtError for a bucket on CUDA cores)."""
+        return ssht_group_bucket_tile_config(self._h, i)
 
     def empty_coeffs(self):
         return torch.empty(self.coff[-1], dtype=self.dtype, device=self.device)

@@ -129,5 +129,5 @@ def test_group_layout_and_errors():
     assert g.goff[-1] == sum(L * (2 * L - 1) for L in Ls)
     with pytest.raises(ssht.SshtError):
         ssht.Group([4, 4], [0, 4])        # |s| >= L
-    with pytest.raises(ssht.SshtError):
-        ssht.Group([4] * 70, [0] * 70, precision="tf32x3", tune=False)  # > 64 fields in a tensor-core bucket
+    big = ssht.Group([4] * 70, [0] * 70, precision="tf32x3", tune=False)  # > 64 fields: two GEMM slices
+    assert big.bucket_tile_config(0)["slice"] == 64

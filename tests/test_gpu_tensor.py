@@ -104,7 +104,48 @@ def test_split_forms_differ_but_agree():
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-def test_split_rejects_more_than_64_fields(precision):
-    from paper_0807_4494_gb300.ssht import SshtError
-    with pytest.raises(SshtError):
-        S().Plan(64, 0, 65, precision=precision)
+@pytest.mark.parametrize("B", [65, 128])
+def test_more_than_64_fields_run_in_slices(precision, B):
+    """Batches above 64 fields stay on the tensor cores (one GEMM launch per slice of at most 64
+    fields, all reading the same A operand): every field against the oracle."""
+    L, s = 48, 1
+    flm = inputs.coeffs(L, s, B, seed=B)
+    plan = S().Plan(L, s, B, precision=precision)
+    assert plan.tile_config()["slice"] == 64
+    f = plan.inverse(dev(flm))
+    back = plan.forward(f).cpu().numpy()
+    adj = plan.adjoint(f).cpu().numpy()
+    plan.check()
+    check_fields(flm, f.cpu().numpy(), back, adj, L, s, range(B))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_tuned_shape_matches_oracle_and_reloads_from_the_cache(precision, tmp_path, monkeypatch):
+    """SSHT_FLAG_TUNE times the shape candidates and keeps one; with SSHT_TUNE_CACHE the choice is
+    appended to the file, and a choice found there is used as it is (here a planted, non-default
+    one) -- both give the oracle's transforms."""
+    L, s, B = 96, 2, 40
+    flm = inputs.coeffs(L, s, B, seed=6)
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SSHT_TUNE_CACHE", str(cache))
+    plan = S().Plan(L, s, B, precision=precision, tune=True)
+    cfg = plan.tile_config()
+    assert cfg["slice"] in (40, 32, 16) and 2 <= cfg["stages"] <= 4
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and ('"key": "L=96 s=2 B=40 %s"' % precision) in lines[0]
+    f = plan.inverse(dev(flm))
+    back = plan.forward(f).cpu().numpy()
+    adj = plan.adjoint(f).cpu().numpy()
+    plan.check()
+    check_fields(flm, f.cpu().numpy(), back, adj, L, s, range(0, B, 3))
+    planted = {"slice": 16, "stages": 3, "inv_order": 1, "fwd_order": 1}
+    cache.write_text('{"key": "L=96 s=2 B=40 %s", "slice": 16, "stages": 3, "inv_order": 1, "fwd_order": 1, '
+                     '"ms": 1.0}\n' % precision)
+    again = S().Plan(L, s, B, precision=precision, tune=True)
+    assert again.tile_config() == planted
+    assert len(cache.read_text().splitlines()) == 1  # found there: nothing timed, nothing appended
+    f2 = again.inverse(dev(flm))
+    b2 = again.forward(f2).cpu().numpy()
+    a2 = again.adjoint(f2).cpu().numpy()
+    again.check()
+    check_fields(flm, f2.cpu().numpy(), b2, a2, L, s, range(0, B, 3))
