@@ -560,6 +560,30 @@ def run_ssht(args):
                              "note": "the table-writing sweep timed by itself (ssht_wigner_delta)"}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1] > 0}
 
+    # column pairing along theta (two phi-frequency columns of opposite parity in one DFT): the
+    # inverse theta pass transforms pairs, the adjoint's theta pass one column at a time, each
+    # with two FFTs of the same length -- their time per column shows what the pairing saves
+    pairing = None
+    if prec != "fp64":
+        plan.profile(True)
+        adj_out = torch.empty(plan.coeff_shape(), dtype=cdt, device=device)
+        for _ in range(3):
+            plan.adjoint(grid, out=adj_out)
+        atrace = plan.profile_trace()
+        plan.profile(False)
+        plan.check()
+        afft = [t1 - t0 for name, lane, t0, t1 in atrace if name == "fft" and lane == 0]
+        theta_adj = float(np.mean(afft[1::2])) if len(afft) >= 2 else None
+        theta_inv = kern.get("theta_inverse", {}).get("ms")
+        if theta_adj and theta_inv:
+            cols = B * (2 * L - 1)
+            pairing = {"theta_inverse_paired_ms": theta_inv, "theta_adjoint_unpaired_ms": theta_adj,
+                       "us_per_column_paired": 1e3 * theta_inv / cols, "us_per_column_unpaired": 1e3 * theta_adj / cols,
+                       "unpaired_over_paired": theta_adj / theta_inv,
+                       "note": "same DFT length and FFT count per transformed sequence; the adjoint's theta pass "
+                               "also writes the data tiles, the inverse's the phi input"}
+        del adj_out
+
     # the plain FP64 GPU transform of the same workload (the mixed-precision form must beat it)
     fp64_line = None
     if not args.no_fp64 and prec != "fp64":
@@ -627,6 +651,7 @@ def run_ssht(args):
             "e2e": e2e,
             "gpu_launches": int(launches1 - launches0),
             "fp64": fp64_line,
+            "theta_pairing": pairing,
             "delta_cache": cache_line,
             "uneven_batch": uneven,
             "real_fields": real_line,

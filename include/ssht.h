@@ -91,6 +91,13 @@ typedef enum {
                            * SSHT_TUNE_CACHE naming a file, choices are read from it (no timing) and
                            * appended to it after tuning, one JSON object per line keyed by
                            * "L=.. s=.. B=.. precision".  Ignored by the other precisions. */
+#define SSHT_FLAG_SPIN_PAIR 8 /* each field comes with its conjugate, the pair of spins s and -s
+                               * the paper writes f_s* = f_{-s} (Sec. 3.3; for s = 0 and real f the
+                               * reality condition).  Coefficients are [batch][2][L*L]: spin s, then
+                               * spin -s of the conjugate field, tied by _{-s}f_{l,-m} =
+                               * (-1)^{s+m} conj(_s f_lm).  forward / adjoint compute both sets with
+                               * one spin-s transform (half the work of two transforms); inverse
+                               * reads the spin-s half only and returns f.  Not with SSHT_FLAG_REAL. */
 
 typedef struct {
   int L;          /* exclusive band-limit, 1 <= L <= 2048                      */
@@ -98,7 +105,7 @@ typedef struct {
   int batch;      /* number of fields per call, 1 <= batch <= 65535            */
   int precision;  /* ssht_precision                                            */
   int delta_mode; /* ssht_delta_mode                                           */
-  int flags;      /* 0 or any of SSHT_FLAG_REAL, SSHT_FLAG_RISBO, SSHT_FLAG_TUNE */
+  int flags;      /* 0 or SSHT_FLAG_* (REAL, RISBO, TUNE, SPIN_PAIR)            */
 } ssht_plan_desc;
 
 typedef struct ssht_plan_s* ssht_plan_t;

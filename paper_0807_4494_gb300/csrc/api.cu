@@ -169,8 +169,12 @@ struct ssht_plan_s {
   void* rc = nullptr;
   void* rg = nullptr;
 
+  // Spin pairs (SSHT_FLAG_SPIN_PAIR): coefficients [B][2][L*L], spin s then spin -s of the
+  // conjugate field; rc holds the spin-s halves.
+  bool pair = false;
+
   // bytes of the caller's buffers
-  size_t coeff_bytes() const { return (size_t)(real ? nreal : B) * d.L * d.L * elem; }
+  size_t coeff_bytes() const { return (size_t)(real ? nreal : B) * d.L * d.L * elem * (pair ? 2 : 1); }
   size_t grid_bytes() const { return real ? (size_t)nreal * d.L * d.N * (elem / 2) : (size_t)B * d.L * d.N * elem; }
   size_t pair_coeff_bytes() const { return (size_t)B * d.L * d.L * elem; }
   size_t pair_grid_bytes() const { return (size_t)B * d.L * d.N * elem; }
@@ -615,6 +619,28 @@ int real_call(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t 
   return 0;
 }
 
+// Spin pairs: which = 0 inverse (from the spin-s halves), 1 forward, 2 adjoint (one spin-s
+// transform, then the spin -s coefficients of the conjugate field by the conjugate symmetry).
+template <typename T>
+int pair_call(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t st) {
+  const int L = p->d.L;
+  int rc;
+  if (which == 0) {
+    {
+      StageScope sc(p, SSHT_STAGE_PACK, st);
+      SSHT_CUDA(pair_gather<T>(L, p->B, in, p->rc, st), "spin-pair gather");
+      p->launches += 1;
+    }
+    return inverse_impl<T>(p, p->rc, out, st);
+  }
+  rc = which == 1 ? forward_impl<T>(p, in, p->rc, st) : adjoint_impl<T>(p, in, p->rc, st);
+  if (rc) return rc;
+  StageScope sc(p, SSHT_STAGE_PACK, st);
+  SSHT_CUDA(pair_expand<T>(L, p->s, p->B, p->rc, out, st), "spin-pair expansion");
+  p->launches += 1;
+  return 0;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Tile tuning of the tensor-core contraction (SSHT_FLAG_TUNE, and the tuned buckets of groups):
 // every shape candidate -- fields per GEMM launch, pipeline depth, work order -- is timed on the
@@ -776,7 +802,11 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   if (L < 1 || L > 2048) return fail(SSHT_EINVAL, "band-limit L must be in [1, 2048]");
   if (s <= -L || s >= L) return fail(SSHT_EINVAL, "spin must satisfy |s| < L");
   if (nfields < 1 || nfields > 65535) return fail(SSHT_EINVAL, "batch must be in [1, 65535]");
-  if ((desc->flags & ~(SSHT_FLAG_REAL | SSHT_FLAG_RISBO | SSHT_FLAG_TUNE)) != 0) return fail(SSHT_EINVAL, "unknown flags");
+  if ((desc->flags & ~(SSHT_FLAG_REAL | SSHT_FLAG_RISBO | SSHT_FLAG_TUNE | SSHT_FLAG_SPIN_PAIR)) != 0)
+    return fail(SSHT_EINVAL, "unknown flags");
+  const bool pair = (desc->flags & SSHT_FLAG_SPIN_PAIR) != 0;
+  if (pair && (desc->flags & SSHT_FLAG_REAL)) return fail(SSHT_EINVAL, "SSHT_FLAG_SPIN_PAIR and SSHT_FLAG_REAL exclude each other");
+  if (pair && shared) return fail(SSHT_EINVAL, "groups take single fields, not spin pairs");
   const bool real = (desc->flags & SSHT_FLAG_REAL) != 0;
   if (real && s != 0) return fail(SSHT_EINVAL, "real fields (SSHT_FLAG_REAL) need spin 0");
   if (real && shared) return fail(SSHT_EINVAL, "groups take complex fields only");
@@ -811,6 +841,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   p->delta_mode = desc->delta_mode;
   p->real = real;
   p->nreal = real ? nfields : 0;
+  p->pair = pair;
   p->f64 = desc->precision == SSHT_FP64;
   p->elem = p->f64 ? 16 : 8;
   const Dims& d = p->d;
@@ -840,6 +871,11 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   // FP64: full N x N torus rows and an M-point convolution buffer; FP32 (fused torus passes): half
   // rows of N x L only, plus one row a field for the column pairs of the phi pass's output.
   const size_t torus = (size_t)B * (p->f64 ? (size_t)d.N * d.N : (size_t)(d.N + 1) * d.L) * p->elem;
+  if (pair && (rc = dalloc(p, &p->rc, (size_t)B * L * L * p->elem, "spin-pair coefficients"))) return bail(rc);
+  if ((real || pair) && (ce = real_setup()) != cudaSuccess) {
+    release(p);
+    return fail(SSHT_ECUDA, std::string("packing kernel attributes: ") + cudaGetErrorString(ce));
+  }
   if (real) {
     if ((rc = dalloc(p, &p->rc, p->pair_coeff_bytes(), "real-field pair coefficients"))) return bail(rc);
     if ((rc = dalloc(p, &p->rg, p->pair_grid_bytes(), "real-field pair samples"))) return bail(rc);
@@ -984,6 +1020,8 @@ int ssht_inverse(ssht_plan_t p, const void* flm, void* f, void* stream) {
   if ((rc = io_begin(p, flm, p->coeff_bytes(), f, p->grid_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 0, io.in_dev, io.out_dev, st) : real_call<float>(p, 0, io.in_dev, io.out_dev, st);
+  else if (p->pair)
+    rc = p->f64 ? pair_call<double>(p, 0, io.in_dev, io.out_dev, st) : pair_call<float>(p, 0, io.in_dev, io.out_dev, st);
   else
     rc = p->f64 ? inverse_impl<double>(p, io.in_dev, io.out_dev, st) : inverse_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;
@@ -1000,6 +1038,8 @@ int ssht_forward(ssht_plan_t p, const void* f, void* flm, void* stream) {
   if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 1, io.in_dev, io.out_dev, st) : real_call<float>(p, 1, io.in_dev, io.out_dev, st);
+  else if (p->pair)
+    rc = p->f64 ? pair_call<double>(p, 1, io.in_dev, io.out_dev, st) : pair_call<float>(p, 1, io.in_dev, io.out_dev, st);
   else
     rc = p->f64 ? forward_impl<double>(p, io.in_dev, io.out_dev, st) : forward_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;
@@ -1016,6 +1056,8 @@ int ssht_adjoint(ssht_plan_t p, const void* g, void* flm, void* stream) {
   if ((rc = io_begin(p, g, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 2, io.in_dev, io.out_dev, st) : real_call<float>(p, 2, io.in_dev, io.out_dev, st);
+  else if (p->pair)
+    rc = p->f64 ? pair_call<double>(p, 2, io.in_dev, io.out_dev, st) : pair_call<float>(p, 2, io.in_dev, io.out_dev, st);
   else
     rc = p->f64 ? adjoint_impl<double>(p, io.in_dev, io.out_dev, st) : adjoint_impl<float>(p, io.in_dev, io.out_dev, st);
   if (rc) return rc;

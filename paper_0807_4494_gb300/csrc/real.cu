@@ -88,6 +88,43 @@ __global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const ty
   }
 }
 
+// Spin pairs (SSHT_FLAG_SPIN_PAIR): the pair of fields (f, f*) of spins s and -s -- the signals the
+// paper calls f_s* = f_{-s} -- has one set of coefficients determined by the other through the
+// conjugate symmetry of Sec. 2.3: _{-s}f_{l,-m} = (-1)^{s+m} conj(_s f_{lm}).  So the pair's
+// forward (or adjoint) is one spin-s transform followed by this expansion:
+//   out[b][0][l,m] = c[b][l,m],  out[b][1][l,m] = (-1)^{s+m} conj(c[b][l,-m])   (zero for l < |s|);
+// and its inverse needs the spin-s half only (gathered by pair_gather_kernel).
+template <typename T>
+__global__ void pair_expand_kernel(int L, int s, long long B, const typename Cx<T>::type* __restrict__ c,
+                                   typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * L, total = B * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / n2, e = i - b * n2;
+    int l = (int)sqrtf((float)e);
+    while ((long long)l * l > e) --l;
+    while ((long long)(l + 1) * (l + 1) <= e) ++l;
+    const int m = (int)(e - (long long)l * l - l);
+    const C d = c[b * n2 + (long long)l * l + l - m];
+    const T sg = ((s + m) & 1) ? T(-1) : T(1);
+    C q;
+    q.x = sg * d.x;
+    q.y = -sg * d.y;
+    out[2 * b * n2 + e] = c[i];
+    out[(2 * b + 1) * n2 + e] = q;
+  }
+}
+
+template <typename T>
+__global__ void pair_gather_kernel(long long n2, long long B, const typename Cx<T>::type* __restrict__ in,
+                                   typename Cx<T>::type* __restrict__ c) {
+  const long long total = B * n2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / n2, e = i - b * n2;
+    c[i] = in[2 * b * n2 + e];
+  }
+}
+
 unsigned blocks_for(long long n) {
   const long long b = (n + 255) / 256;
   return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
@@ -127,6 +164,21 @@ cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cuda
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t pair_expand(int L, int s, int B, const void* c, void* out, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  pair_expand_kernel<T><<<blocks_for((long long)B * L * L), 256, 0, st>>>(L, s, B, (const C*)c, (C*)out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pair_gather(int L, int B, const void* in, void* c, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long n2 = (long long)L * L;
+  pair_gather_kernel<T><<<blocks_for(B * n2), 256, 0, st>>>(n2, B, (const C*)in, (C*)c);
+  return cudaGetLastError();
+}
+
 cudaError_t real_setup() {
   cudaError_t e;
   if ((e = prefer_shared(pack_coeffs_kernel<double>)) != cudaSuccess) return e;
@@ -136,6 +188,10 @@ cudaError_t real_setup() {
   if ((e = prefer_shared(unpack_grid_kernel<double>)) != cudaSuccess) return e;
   if ((e = prefer_shared(unpack_grid_kernel<float>)) != cudaSuccess) return e;
   if ((e = prefer_shared(unpack_coeffs_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pair_expand_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pair_expand_kernel<float>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pair_gather_kernel<double>)) != cudaSuccess) return e;
+  if ((e = prefer_shared(pair_gather_kernel<float>)) != cudaSuccess) return e;
   return prefer_shared(unpack_coeffs_kernel<float>);
 }
 
@@ -143,7 +199,9 @@ cudaError_t real_setup() {
   template cudaError_t real_pack_coeffs<T>(int, int, const void*, void*, cudaStream_t);          \
   template cudaError_t real_pack_grid<T>(int, int, const void*, void*, cudaStream_t);            \
   template cudaError_t real_unpack_grid<T>(int, int, const void*, void*, cudaStream_t);          \
-  template cudaError_t real_unpack_coeffs<T>(int, int, const void*, void*, cudaStream_t);
+  template cudaError_t real_unpack_coeffs<T>(int, int, const void*, void*, cudaStream_t);        \
+  template cudaError_t pair_expand<T>(int, int, int, const void*, void*, cudaStream_t);          \
+  template cudaError_t pair_gather<T>(int, int, const void*, void*, cudaStream_t);
 SSHT_REAL_INST(double)
 SSHT_REAL_INST(float)
 #undef SSHT_REAL_INST

@@ -108,6 +108,10 @@ template <typename T> cudaError_t real_pack_coeffs(int L, int nreal, const void*
 template <typename T> cudaError_t real_pack_grid(int L, int nreal, const void* f, void* rg, cudaStream_t st);
 template <typename T> cudaError_t real_unpack_grid(int L, int nreal, const void* rg, void* f, cudaStream_t st);
 template <typename T> cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cudaStream_t st);
+// Spin pairs (real.cu): c [B][L*L] spin-s coefficients -> out [B][2][L*L] (spin s, then spin -s of
+// the conjugate field); in [B][2][L*L] -> c [B][L*L] (the spin-s halves).
+template <typename T> cudaError_t pair_expand(int L, int s, int B, const void* c, void* out, cudaStream_t st);
+template <typename T> cudaError_t pair_gather(int L, int B, const void* in, void* c, cudaStream_t st);
 // Kernel attributes of the packing kernels (on the current device).
 cudaError_t real_setup();
 

@@ -17,6 +17,7 @@ FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
 FLAG_REAL = 1
 FLAG_RISBO = 2
 FLAG_TUNE = 4
+FLAG_SPIN_PAIR = 8
 RECOMPUTE, CACHE = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "bf16x6": BF16X6}
 ERRORS = {0: "SSHT_OK", -1: "SSHT_EINVAL", -2: "SSHT_ENOMEM", -3: "SSHT_ECUDA", -4: "SSHT_ETIMEOUT",
@@ -226,7 +227,7 @@ class Plan:
     """
 
     def __init__(self, L, s, batch=1, precision="fp64", delta_mode="recompute", real=False, recursion="column",
-                 tune=False):
+                 tune=False, spin_pair=False):
         self.L, self.s, self.batch = int(L), int(s), int(batch)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.delta_mode = {"recompute": RECOMPUTE, "cache": CACHE}[delta_mode] if isinstance(delta_mode, str) else int(delta_mode)
@@ -236,7 +237,9 @@ class Plan:
         self.grid_dtype = (torch.float64 if self.precision == FP64 else torch.float32) if self.real else self.dtype
         if recursion not in ("column", "risbo"):
             raise ValueError("recursion must be 'column' or 'risbo'")
+        self.spin_pair = bool(spin_pair)
         flags = (FLAG_REAL if self.real else 0) | (FLAG_RISBO if recursion == "risbo" else 0) | (FLAG_TUNE if tune else 0)
+        flags |= FLAG_SPIN_PAIR if self.spin_pair else 0
         self._h = ssht_plan_ex(self.L, self.s, self.batch, self.precision, self.delta_mode, flags)
 
     def close(self):
@@ -255,7 +258,7 @@ class Plan:
         return 2 * self.L - 1
 
     def coeff_shape(self):
-        return (self.batch, self.L * self.L)
+        return (self.batch, 2, self.L * self.L) if self.spin_pair else (self.batch, self.L * self.L)
 
     def grid_shape(self):
         return (self.batch, self.L, self.N)

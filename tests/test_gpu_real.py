@@ -73,3 +73,31 @@ def test_real_flag_needs_spin_zero():
     ssht = S()
     with pytest.raises(ssht.SshtError):
         ssht.Plan(16, 1, 2, real=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("L,s,B", [(33, 2, 3), (64, -1, 4), (20, 0, 2)])
+def test_spin_pairs_give_both_spins_from_one_transform(precision, L, s, B):
+    """SSHT_FLAG_SPIN_PAIR: for each field f of spin s, the forward and the adjoint return the spin-s
+    coefficients of f and the spin -s coefficients of conj(f) (the pair f_s* = f_{-s}) from one
+    spin-s transform; every field of both halves against the oracle's transform of f (spin s) and
+    of conj(f) (spin -s).  The inverse of the pair reads its spin-s half."""
+    ssht = S()
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    flm = inputs.coeffs(L, s, B, seed=L + 7)
+    f = T.inverse(flm, L, s)
+    g = np.random.default_rng(3).standard_normal(f.shape) + 1j * np.random.default_rng(4).standard_normal(f.shape)
+    plan = ssht.Plan(L, s, B, precision=precision, spin_pair=True)
+    fwd = plan.forward(torch.from_numpy(f).to(dt).cuda()).cpu().numpy()
+    adj = plan.adjoint(torch.from_numpy(g).to(dt).cuda()).cpu().numpy()
+    pair_in = np.stack([flm, np.zeros_like(flm)], axis=1)  # the spin -s half is not read
+    inv = plan.inverse(torch.from_numpy(pair_in).to(dt).cuda()).cpu().numpy()
+    plan.check()
+    assert fwd.shape == (B, 2, L * L)
+    tol = TOL[precision]
+    for b in range(B):
+        assert rel(fwd[b, 0], T.forward(f[b], L, s)) < tol
+        assert rel(fwd[b, 1], T.forward(np.conj(f[b]), L, -s)) < tol
+        assert rel(adj[b, 0], T.adjoint(g[b], L, s)) < tol
+        assert rel(adj[b, 1], T.adjoint(np.conj(g[b]), L, -s)) < tol
+        assert rel(inv[b], f[b]) < tol
