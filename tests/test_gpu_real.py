@@ -85,7 +85,7 @@ def test_spin_pairs_give_both_spins_from_one_transform(precision, L, s, B):
     ssht = S()
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     flm = inputs.coeffs(L, s, B, seed=L + 7)
-    f = T.inverse(flm, L, s)
+    f = np.ascontiguousarray(T.inverse(flm, L, s))
     g = np.random.default_rng(3).standard_normal(f.shape) + 1j * np.random.default_rng(4).standard_normal(f.shape)
     plan = ssht.Plan(L, s, B, precision=precision, spin_pair=True)
     fwd = plan.forward(torch.from_numpy(f).to(dt).cuda()).cpu().numpy()
