@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (captured graph) line")
     ap.add_argument("--no-real", action="store_true", help="skip the real spin-0 fields line")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 transform line")
+    ap.add_argument("--no-tune", action="store_true", help="default contraction shape instead of the tuned one")
     ap.add_argument("--error-sweep", action="store_true",
                     help="print errors vs the FP64 oracle for L = 32 .. 2048 and every precision, then exit")
     return ap.parse_args()
@@ -393,7 +394,10 @@ def run_ssht(args):
     prec = args.precision
     if prec == "auto":
         prec = "tf32x3" if B <= 64 else "fp32"
-    plan = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode)
+    t_plan = time.perf_counter()
+    plan = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode, tune=not args.no_tune)
+    plan_s = time.perf_counter() - t_plan
+    tile_cfg = plan.tile_config() if prec in ("tf32x3", "bf16x6") else None
     cdt = plan.dtype
     flm_np = inputs.coeffs(L, s, B, seed=rank_seed(rank, B), spectrum="cmb")
     flm = torch.from_numpy(flm_np).to(cdt).to(device)
@@ -640,6 +644,7 @@ def run_ssht(args):
             "data": "synthetic: sf_lm ~ CN(0, 1/(l+1)^2) (Re, Im each N(0, 1/(2(l+1)^2))), seeds rank*B .. rank*B+B-1",
             "config": {"workload": "L=%d s=%d B=%d fwd+inv per step" % (L, s, B), "L": L, "s": s, "batch": B,
                        "precision": prec, "delta_mode": args.delta_mode, "parallelism": "dp%d (independent fields)" % world,
+                       "contraction_shape": tile_cfg, "plan_create_s": plan_s,
                        "l2": "inputs larger than L2 (%.2f GB of coefficients, %.2f GB of samples per step)" % (
                            flm.numel() * flm.element_size() / 1e9, grid.numel() * grid.element_size() / 1e9)},
             "rel_err": check,

@@ -224,55 +224,24 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
   fft<M, 1>(buf, tid, tw, back, out);
 }
 
-#ifndef SSHT_TORUS_TW_SMEM
-#define SSHT_TORUS_TW_SMEM 1  // 1: twiddles staged in shared memory per CTA; 0: read through L1 from global
-#endif
-
 template <int M> struct Geo {
   static constexpr int T = M / 16;
   static constexpr int G = (T >= 256) ? 1 : 256 / T;  // row groups per CTA
   static constexpr int THREADS = T * G;
   static constexpr int BUF = M + M / 16;
-  // Input staging: each row group loads the input of its next row into one of two buffers
-  // (cp.async) while it transforms the current one.  An input row is at most M/2 + 1 values
-  // (N samples, or the 2L values of a column pair).
-  static constexpr int STG = M / 2 + 16;
-  static constexpr int TWS = SSHT_TORUS_TW_SMEM ? Plan16<M>::TW : 0;  // shared-memory twiddle entries
-  static constexpr int STG_BASE = (TWS + G * BUF + 1) & ~1;  // 16-byte aligned (read as float4)
   static constexpr int MINB = THREADS >= 512 ? 1 : 3;  // CTAs per SM the register budget is sized for
-  static constexpr int SMEM = (STG_BASE + 2 * G * STG) * 8;
+  static constexpr int SMEM = (Plan16<M>::TW + G * BUF) * 8;
 };
-
-// Asynchronous global -> shared copies of 8 bytes (both addresses 8-byte aligned) and their
-// completion groups.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Waits until at most one group (the most recent) of this thread's copies is still in flight.
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// The two staging buffers of this thread's row group.
-template <int M>
-__device__ __forceinline__ float2* staging(int which) {
-  extern __shared__ float2 sm[];
-  return sm + Geo<M>::STG_BASE + ((threadIdx.x / Geo<M>::T) * 2 + which) * Geo<M>::STG;
-}
 
 // Stage the twiddle table in shared memory; returns the row group's buffer.
 template <int M>
 __device__ __forceinline__ float2* setup_smem(const TorusTables& tb, float2** tw_out) {
   extern __shared__ float2 sm[];
-  if (SSHT_TORUS_TW_SMEM) {
-    float2* tw = sm;
-    for (int k = threadIdx.x; k < Plan16<M>::TW; k += blockDim.x) tw[k] = __ldg(&tb.tw[k]);
-    __syncthreads();
-    *tw_out = tw;
-  } else {
-    *tw_out = const_cast<float2*>(tb.tw);
-  }
-  return sm + Geo<M>::TWS + (threadIdx.x / Geo<M>::T) * Geo<M>::BUF;
+  float2* tw = sm;
+  for (int k = threadIdx.x; k < Plan16<M>::TW; k += blockDim.x) tw[k] = __ldg(&tb.tw[k]);
+  __syncthreads();
+  *tw_out = tw;
+  return sm + Plan16<M>::TW + (threadIdx.x / Geo<M>::T) * Geo<M>::BUF;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -286,36 +255,20 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
   const int Lp = L - 1, N = 2 * L - 1;
   const int tid = threadIdx.x % Geo<M>::T;
   const long long npairs = (long long)B * L;  // pair p: m = -Lp + 2p (and m + 1 when p < Lp)
-  const long long step = (long long)gridDim.x * Geo<M>::G;
-  const int grp = threadIdx.x / Geo<M>::T;
-  // the half rows of columns m and m + 1 of pair u, staged as [F_m | F_{m+1}]
-  auto load_row = [&](long long u, float2* dst) {
-    if (u >= npairs) return;
-    const int b = (int)(u / L), p = (int)(u % L);
-    const float2* F0 = F + ((size_t)b * N + 2 * p) * L;
-    const int n = p < Lp ? 2 * L : L;
-    for (int i = tid; i < n; i += Geo<M>::T) cp_async8(dst + i, F0 + i);
-  };
-  int cur = 0;
-  load_row((long long)blockIdx.x * Geo<M>::G + grp, staging<M>(0));
-  cp_async_commit();
-  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += step) {
-    const long long u = u0 + grp;
-    load_row(u + step, staging<M>(cur ^ 1));
-    cp_async_commit();
-    cp_async_wait_prior();
-    __syncthreads();
-    const float2* X = staging<M>(cur);
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < npairs;
     const int b = active ? (int)(u / L) : 0, p = active ? (int)(u % L) : 0;
     const int m = -Lp + 2 * p;
     const bool two = p < Lp;
     const float sig = ((m + s) & 1) ? -1.f : 1.f;  // parity of column m; column m+1 has -sig
+    const float2* F0 = F + ((size_t)b * N + (m + Lp)) * L;
+    const float2* F1 = F0 + L;
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
       const int mp = n < L ? n : N - n;  // theta frequency m' (>= 0) of DFT bin n
-      float2 a = X[mp];
-      const float2 c = two ? X[L + mp] : make_float2(0.f, 0.f);
+      float2 a = F0[mp];
+      const float2 c = two ? F1[mp] : make_float2(0.f, 0.f);
       float2 z = (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);  // F_{m,-m'} = sig F_{m m'}, column m+1: -sig
       return cmul(z, tb.ph[(n < L ? mp : -mp) + N - 1]);           // e^{i pi (+-m')/N}
     };
@@ -339,7 +292,6 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
       }
     }
     __syncthreads();
-    cur ^= 1;
   }
 }
 
@@ -354,25 +306,11 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
   const int Lp = L - 1, N = 2 * L - 1;
   const int tid = threadIdx.x % Geo<M>::T;
   const long long nrows = (long long)B * L;
-  const long long step = (long long)gridDim.x * Geo<M>::G;
-  const int grp = threadIdx.x / Geo<M>::T;
-  auto load_row = [&](long long u, float2* dst) {
-    if (u >= nrows) return;
-    const float2* x = in + (size_t)u * N;
-    for (int i = tid; i < N; i += Geo<M>::T) cp_async8(dst + i, x + i);
-  };
-  int cur = 0;
-  load_row((long long)blockIdx.x * Geo<M>::G + grp, staging<M>(0));
-  cp_async_commit();
-  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += step) {
-    const long long u = u0 + grp;
-    load_row(u + step, staging<M>(cur ^ 1));
-    cp_async_commit();
-    cp_async_wait_prior();
-    __syncthreads();
-    const float2* X = staging<M>(cur);
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < nrows;
-    auto src = [&](int n) { return active ? X[n] : make_float2(0.f, 0.f); };
+    const float2* x = in + (size_t)(active ? u : 0) * N;
+    auto src = [&](int n) { return active ? x[n] : make_float2(0.f, 0.f); };
     if constexpr (SIGN > 0) {
       float2* y = out + (size_t)(active ? u : 0) * N;
       auto sink = [&](int k, float2 v) {
@@ -390,7 +328,6 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
       bluestein<M, SIGN, true>(buf, tid, tw, tb, N, src, sink);
     }
     __syncthreads();
-    cur ^= 1;
   }
 }
 
@@ -436,31 +373,15 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
   const int tid = threadIdx.x % Geo<M>::T;
   const float invN = 1.f / (float)N;
   const long long npairs = (long long)B * L;
-  const long long step = (long long)gridDim.x * Geo<M>::G;
-  const int grp = threadIdx.x / Geo<M>::T;
-  // the L rings of columns m, m + 1 of pair u, as stored (X[b][p][t][0..1])
-  auto load_row = [&](long long u, float2* dst) {
-    if (u >= npairs) return;
-    const int b = (int)(u / L), p = (int)(u % L);
-    const float2* x = X + ((size_t)b * (N + 1) + 2 * p) * L;
-    for (int i = tid; i < 2 * L; i += Geo<M>::T) cp_async8(dst + i, x + i);
-  };
-  int cur = 0;
-  load_row((long long)blockIdx.x * Geo<M>::G + grp, staging<M>(0));
-  cp_async_commit();
-  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += step) {
-    const long long u = u0 + grp;
-    load_row(u + step, staging<M>(cur ^ 1));
-    cp_async_commit();
-    cp_async_wait_prior();
-    __syncthreads();
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < npairs;
     const int b = active ? (int)(u / L) : 0, p = active ? (int)(u % L) : 0;
     const int m = -Lp + 2 * p;
     const bool two = p < Lp;
     const bool odd0 = ((m + s) & 1) != 0;
     const float sig = odd0 ? -1.f : 1.f;
-    const float4* Xp = (const float4*)staging<M>(cur);  // pair p: columns m, m + 1
+    const float4* Xp = (const float4*)(X + ((size_t)b * (N + 1) + 2 * p) * L);  // pair p: columns m, m + 1
     // extended samples of both columns on theta in [0, 2 pi): the odd one vanishes at theta = pi
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
@@ -536,7 +457,6 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
       }
     }
     __syncthreads();
-    cur ^= 1;
   }
 }
 
@@ -551,29 +471,13 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
   const int Lp = L - 1, N = 2 * L - 1;
   const int tid = threadIdx.x % Geo<M>::T;
   const long long nrows = (long long)B * N;
-  const long long step = (long long)gridDim.x * Geo<M>::G;
-  const int grp = threadIdx.x / Geo<M>::T;
-  // the L rings of column m + Lp = u mod N (every other value of its pair's rows)
-  auto load_row = [&](long long u, float2* dst) {
-    if (u >= nrows) return;
-    const int mr = (int)(u % N);
-    const float2* x = X + ((size_t)(u / N) * (N + 1) + (mr & ~1)) * L + (mr & 1);
-    for (int i = tid; i < L; i += Geo<M>::T) cp_async8(dst + i, x + 2 * i);
-  };
-  int cur = 0;
-  load_row((long long)blockIdx.x * Geo<M>::G + grp, staging<M>(0));
-  cp_async_commit();
-  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += step) {
-    const long long u = u0 + grp;
-    load_row(u + step, staging<M>(cur ^ 1));
-    cp_async_commit();
-    cp_async_wait_prior();
-    __syncthreads();
-    const float2* xs = staging<M>(cur);
+  for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < nrows; u0 += (long long)gridDim.x * Geo<M>::G) {
+    const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < nrows;
     const int mr = active ? (int)(u % N) : 0;  // column m + Lp of field u / N
     const int m = mr - Lp;
-    auto src = [&](int n) { return (active && n < L) ? xs[n] : make_float2(0.f, 0.f); };
+    const float2* x = X + ((size_t)(active ? u / N : 0) * (N + 1) + (mr & ~1)) * L + (mr & 1);
+    auto src = [&](int n) { return (active && n < L) ? x[2 * n] : make_float2(0.f, 0.f); };
     auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };  // H'_{m''} at bin k (phase in the chirp)
     bluestein<M, -1, true>(buf, tid, tw, tb, N, src, sink);
     __syncthreads();
@@ -599,7 +503,6 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
       }
     }
     __syncthreads();
-    cur ^= 1;
   }
 }
 
