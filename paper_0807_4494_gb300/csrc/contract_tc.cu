@@ -131,53 +131,50 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
 // Packing: data tiles (rows j = (sign, part, b), K-major over 32 l or m')
 // ---------------------------------------------------------------------------------------------
 
-// Each thread loads up to 16 complex values (one (sign, b, k) each) before converting any of
-// them, and writes both parts of each: rows j = sign * NC/2 + 2b (real) and 2b + 1 (imaginary).
-constexpr int XPER = 16;  // NC <= 256: 32 * NC / 2 complex values per tile
-
-// Inverse data tile (m, c): V_m[l, j], l = 32 c + k.
-// Fields are packed in slices of Bs (blockIdx.z): slice z holds fields z Bs .. z Bs + Bs - 1 of the
-// batch in its own tile region of xslice bytes.
+// Inverse data tiles (m, c): V_m[l, j], l = 32 c + k, rows j = sign * NC/2 + 2b (real part) and
+// 2b + 1 (imaginary part), for 16 consecutive m at once.  For every field the coefficients
+// sf_{l,+-m} of the 32 degrees of chunk c are read as runs of 16 consecutive orders (coalesced),
+// turned around in shared memory, and every tile row -- 32 consecutive K = l -- is written by one
+// warp at once; the rows of padding fields are written as zeros.  Fields run in slices of Bs
+// (blockIdx.z): slice z holds fields z Bs .. z Bs + Bs - 1 in its own tile region of xslice bytes.
 template <bool BF>
 __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int Bs, size_t xslice, int NC,
                                                      const int* __restrict__ xc0, const long long* __restrict__ xoff,
                                                      const float2* __restrict__ flm, uint8_t* __restrict__ X) {
-  extern __shared__ __align__(16) uint8_t tile[];
+  __shared__ float2 sv[32][33];
   const int B = min(Bs, Btot - (int)blockIdx.z * Bs);
   flm += (size_t)blockIdx.z * Bs * L * L;
   X += (size_t)blockIdx.z * xslice;
-  const int m = blockIdx.y;
-  const int c = xc0[m] + blockIdx.x;
-  const int nC = (L + TK - 1) / TK;
-  if (c >= nC) return;
-  const int as = s < 0 ? -s : s, lmin = m > as ? m : as;
-  const int part_bytes = NC * 128, half = NC / 2, nb = half / 2, total = TK * half;
-  float2 v[XPER];
-#pragma unroll
-  for (int q = 0; q < XPER; ++q) {
-    const int e = threadIdx.x + q * 256;
-    const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
-    const int l = c * TK + k;
-    v[q] = make_float2(0.f, 0.f);
-    if (e < total && b < B && l < L && l >= lmin && !(sign && m == 0)) {
-      v[q] = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
-      if (sign && (l & 1)) v[q] = make_float2(-v[q].x, -v[q].y);
+  const int c = blockIdx.x, m0 = 16 * blockIdx.y;
+  const int as = s < 0 ? -s : s;
+  const int part_bytes = NC * 128, half = NC / 2, nb = half / 2;  // nb: fields of a sign half, padded
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = 0; b < nb; ++b) {
+    if (b < B) {
+      // 32 degrees l x (orders m0 .. m0 + 15, then -m0 .. -m0 - 15)
+      for (int q = threadIdx.x; q < 1024; q += 256) {
+        const int lo = q >> 5, col = q & 31, sign = col >> 4, m = m0 + (col & 15);
+        const int l = c * TK + lo;
+        float2 v = make_float2(0.f, 0.f);
+        if (m < L && l < L && l >= m && l >= as && !(sign && m == 0)) {
+          v = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
+          if (sign && (l & 1)) v = make_float2(-v.x, -v.y);
+        }
+        sv[lo][col] = v;
+      }
     }
-  }
-#pragma unroll
-  for (int q = 0; q < XPER; ++q) {
-    const int e = threadIdx.x + q * 256;
-    if (e < total) {
-      const int k = e % TK, p = e / TK, sign = p / nb, b = p % nb;
+    __syncthreads();
+    for (int cb = warp; cb < 32; cb += 8) {
+      const int sign = cb >> 4, m = m0 + (cb & 15);
+      if (m >= L || c < xc0[m]) continue;  // tile (m, c) is not stored
+      uint8_t* tile = X + (size_t)(xoff[m] + (c - xc0[m])) * 2 * part_bytes;
+      const float2 v = b < B ? sv[lane][cb] : make_float2(0.f, 0.f);
       const int j = sign * half + 2 * b;
-      put_split<BF>(tile, part_bytes, j, k, v[q].x);
-      put_split<BF>(tile, part_bytes, j + 1, k, v[q].y);
+      put_split<BF>(tile, part_bytes, j, lane, v.x);
+      put_split<BF>(tile, part_bytes, j + 1, lane, v.y);
     }
+    __syncthreads();
   }
-  __syncthreads();
-  uint4* dst = (uint4*)(X + (size_t)(xoff[m] + blockIdx.x) * 2 * part_bytes);
-  const uint4* src = (const uint4*)tile;
-  for (int e = threadIdx.x; e < 2 * part_bytes / 16; e += blockDim.x) dst[e] = src[e];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -547,18 +544,17 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   {
     // Function attributes are process-wide upper bounds: the device's limit, so that plans of
     // every configuration can launch with their own amounts.
-    const int xsmem_max = 2 * 256 * 128;
     if ((e = prefer_shared(pack_a_kernel<true, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<true, false>)) != cudaSuccess ||
         (e = prefer_shared(pack_a_kernel<false, true>)) != cudaSuccess || (e = prefer_shared(pack_a_kernel<false, false>)) != cudaSuccess)
       goto fail;
     if (p->bf16) {
       if ((e = gemm_attrs(tc_gemm_kernel<false, true>, p->smem_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(tc_gemm_kernel<true, true>, p->smem_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(pack_v_kernel<true>, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = prefer_shared(pack_v_kernel<true>)) != cudaSuccess) goto fail;
     } else {
       if ((e = gemm_attrs(tc_gemm_kernel<false, false>, p->smem_max)) != cudaSuccess) goto fail;
       if ((e = gemm_attrs(tc_gemm_kernel<true, false>, p->smem_max)) != cudaSuccess) goto fail;
-      if ((e = gemm_attrs(pack_v_kernel<false>, xsmem_max)) != cudaSuccess) goto fail;
+      if ((e = prefer_shared(pack_v_kernel<false>)) != cudaSuccess) goto fail;
     }
   }
   if ((e = tc_configure(p, TcConfig())) != cudaSuccess) goto fail;
@@ -615,14 +611,13 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* 
 }
 
 cudaError_t tc_pack_data(TcPlan* p, const void* src, cudaStream_t st, int* launches) {
-  const int xsmem = 2 * p->NC * 128;
-  const dim3 g(p->nC, p->L, p->nS);
+  const dim3 g(p->nC, (p->L + 15) / 16, p->nS);
   if (p->bf16)
-    pack_v_kernel<true><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
-                                               (const float2*)src, p->X);
+    pack_v_kernel<true><<<g, 256, 0, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
+                                           (const float2*)src, p->X);
   else
-    pack_v_kernel<false><<<g, 256, xsmem, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
-                                                (const float2*)src, p->X);
+    pack_v_kernel<false><<<g, 256, 0, st>>>(p->L, p->s, p->B, p->Bs, p->xslice, p->NC, p->xc0, p->xoff,
+                                            (const float2*)src, p->X);
   *launches += 1;
   return cudaGetLastError();
 }
