@@ -224,12 +224,16 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
   fft<M, 1>(buf, tid, tw, back, out);
 }
 
+#ifndef SSHT_TORUS_MINB
+#define SSHT_TORUS_MINB 3  // resident CTAs of 256 threads an SM the passes' registers are sized for
+#endif
+
 template <int M> struct Geo {
   static constexpr int T = M / 16;
   static constexpr int G = (T >= 256) ? 1 : 256 / T;  // row groups per CTA
   static constexpr int THREADS = T * G;
   static constexpr int BUF = M + M / 16;
-  static constexpr int MINB = THREADS >= 512 ? 1 : 3;  // CTAs per SM the register budget is sized for
+  static constexpr int MINB = THREADS >= 512 ? 1 : SSHT_TORUS_MINB;  // CTAs per SM the register budget is sized for
   static constexpr int SMEM = (Plan16<M>::TW + G * BUF) * 8;
 };
 
