@@ -897,6 +897,13 @@ def error_sweep(args):
                     "inverse": float(np.abs(f0 - f_or).max() / np.abs(f_or).max()),
                     "forward": float(np.abs(back[0].cpu().numpy() - fw).max() / np.abs(fw).max()),
                     "roundtrip": float((back - x).abs().max() / x.abs().max())}
+            if prec == "fp64" and L <= 2048:
+                # the same inverse with the paper's Risbo recursion for Delta
+                rplan = ssht.Plan(L, s, 1, precision="fp64", recursion="risbo")
+                fr = rplan.inverse(x)[0].cpu().numpy()
+                rplan.check()
+                rplan.close()
+                line["inverse_risbo_recursion"] = float(np.abs(fr - f_or).max() / np.abs(f_or).max())
             if prec == "fp64":
                 # the paper's triangular forward of the same grid: its five error metrics against
                 # the coefficients the grid was made from, next to the quadrature forward's
