@@ -868,7 +868,7 @@ def error_sweep(args):
     for s in (0, 2):
         for L in (32, 64, 128, 256, 512):
             flm = inputs.coeffs(L, s, 1, seed=0)
-            f_or = T.inverse(flm[0], L, s)
+            f_or = np.ascontiguousarray(T.inverse(flm[0], L, s))
             plan = ssht.Plan(L, s, 1, precision="fp64")
             x = torch.from_numpy(flm).cuda()
             f = plan.inverse(x)

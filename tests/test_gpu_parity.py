@@ -230,6 +230,25 @@ def test_host_pointers_match_device_pointers():
     plan.check()
 
 
+@pytest.mark.parametrize("precision,real", [("tf32x3", False), ("fp32", False), ("fp64", False), ("tf32x3", True)])
+def test_page_locked_host_inputs_match_device_inputs(precision, real):
+    """Page-locked host inputs are read in place by the call's first kernel where it reads them once
+    (tensor-core inverse, FP32-class forward and adjoint, real-field packing), else copied: either
+    way the results equal those of device inputs bit for bit."""
+    L, s, B = 40, 0 if real else 2, 3
+    plan = S().Plan(L, s, B, precision=precision, real=real)
+    flm = inputs.coeffs(L, s, B, seed=8, spectrum="paper", real=True) if real else inputs.coeffs(L, s, B, seed=8)
+    x = torch.from_numpy(flm).to(plan.dtype)
+    f_dev = plan.inverse(x.cuda())
+    f_pin = plan.inverse(x.pin_memory()).cuda()
+    torch.cuda.synchronize()
+    assert torch.equal(f_dev, f_pin)
+    g_pin = f_dev.cpu().pin_memory()
+    assert torch.equal(plan.forward(g_pin).cuda(), plan.forward(f_dev))
+    assert torch.equal(plan.adjoint(g_pin).cuda(), plan.adjoint(f_dev))
+    plan.check()
+
+
 def test_cache_mode_equals_recompute_mode():
     L, s, B = 48, -2, 2
     flm = dev(inputs.coeffs(L, s, B, seed=9))
