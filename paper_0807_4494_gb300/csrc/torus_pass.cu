@@ -172,19 +172,72 @@ __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Sr
   __syncthreads();
 }
 
-template <int M, int SIGN, int I, class Src, class Sink>
-__device__ __forceinline__ void run_passes(float2* buf, int tid, const float2* tw, Src& src, Sink& sink) {
-  using P = Plan16<M>;
-  pass<M, P::radix(I), pow16(I), SIGN, I == 0, I == P::NP - 1>(buf, tid, tw + P::off(I), src, sink);
-  if constexpr (I + 1 < P::NP) run_passes<M, SIGN, I + 1>(buf, tid, tw, src, sink);
+// Passes [I, IEND) of an FFT of size M and sign SIGN; pass 0 reads src, pass NP - 1 writes sink.
+template <int M, int SIGN, int I, int IEND, class Src, class Sink>
+__device__ __forceinline__ void run_range(float2* buf, int tid, const float2* tw, Src& src, Sink& sink) {
+  if constexpr (I < IEND) {
+    using P = Plan16<M>;
+    pass<M, P::radix(I), pow16(I), SIGN, I == 0, I == P::NP - 1>(buf, tid, tw + P::off(I), src, sink);
+    run_range<M, SIGN, I + 1, IEND>(buf, tid, tw, src, sink);
+  }
 }
 
 // FFT of size M (sign SIGN, unnormalised): inputs through src(i), outputs through sink(k, v),
 // both in natural order.  Ends with a barrier; buf is free afterwards.
 template <int M, int SIGN, class Src, class Sink>
 __device__ __forceinline__ void fft(float2* buf, int tid, const float2* tw, Src src, Sink sink) {
-  run_passes<M, SIGN, 0>(buf, tid, tw, src, sink);
+  run_range<M, SIGN, 0, Plan16<M>::NP>(buf, tid, tw, src, sink);
 }
+
+// The last pass of an FFT of sign SA fused with the first pass of the next FFT, of sign SB, with a
+// pointwise map op(k, v) on the spectrum in between.  In both passes thread tid owns the positions
+// tid + T c, c < 16 (the last pass writes j + r NS with j < NS, NS a multiple of T; the first pass
+// reads tid + r T), so the map runs on registers and the spectrum never goes to shared memory.
+template <int M, int SA, int SB, class Op>
+__device__ __forceinline__ void boundary(float2* buf, int tid, const float2* tw, Op& op) {
+  using P = Plan16<M>;
+  constexpr int I = P::NP - 1, R = P::radix(I), NS = pow16(I), T = M / 16, J = M / R, PER = J / T;
+  static_assert(I >= 1 && NS % T == 0 && PER * R == 16, "pass geometry");
+  const float2* twp = tw + P::off(I);
+  float2 v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid + q * T;
+    const int jm = j & (NS - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 x = buf[pidx(j + r * J)];
+      if (r > 0) {
+        float2 w = twp[(r - 1) * NS + jm];
+        if (SA > 0) w = conjf2(w);
+        x = cmul(x, w);
+      }
+      v[q][r] = x;
+    }
+    dft_reg<R, SA>(v[q]);
+  }
+  float2 u[16];
+#pragma unroll
+  for (int q = 0; q < PER; ++q)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      constexpr int S = NS / T;
+      const int c = q + r * S;
+      u[c] = op(tid + T * c, v[q][r]);
+    }
+  dft_reg<16, SB>(u);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) buf[pidx(16 * tid + r)] = u[r];
+  __syncthreads();
+}
+
+struct NoSrc {
+  __device__ float2 operator()(int) const { return make_float2(0.f, 0.f); }
+};
+struct NoSink {
+  __device__ void operator()(int, float2) const {}
+};
 
 struct TorusTables {
   const float2* chirp;  // e^{-i pi n^2/N}, n < N
@@ -195,11 +248,14 @@ struct TorusTables {
   const float2* ph;     // e^{i pi k/N}, |k| < N, at k + N - 1
   const float2* chirp_ph;  // chirp[k] e^{-i pi m/N}, m = k (k < L) or k - N: the forward DFT's
                            // output chirp with the phase of eqn dft_spatial, one rounding
+  const float2* khat_c;    // spectrum of the forward-DFT chirp kernel for centred outputs, / M
+  const float2* chirp_c;   // at k = m mod M, |m| < L: e^{-i pi (m^2 + m)/N} / N; 0 for L <= k <= M - L
 };
 
 // Bluestein DFT of one row: out_k = sum_n in_n e^{SIGN 2 pi i n k/N}.  in through src(n) (n < N),
 // out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.  PHASE (forward DFTs
-// only): out_k also carries e^{-i pi m/N}, m = k or k - N.
+// only): out_k also carries e^{-i pi m/N}, m = k or k - N.  The chirped row's FFT and the inverse
+// FFT of its product with the kernel's spectrum meet in one fused pass.
 template <int M, int SIGN, bool PHASE = false, class Src, class Sink>
 __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw, const TorusTables& tb, int N, Src src,
                                           Sink sink) {
@@ -211,9 +267,7 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
     if (SIGN > 0) c = conjf2(c);
     return cmul(src(n), c);
   };
-  auto mid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&khat[k])); };
-  fft<M, -1>(buf, tid, tw, in, mid);
-  auto back = [&](int n) { return buf[pidx(n)]; };
+  auto mid = [&](int k, float2 v) { return cmul(v, __ldg(&khat[k])); };
   auto out = [&](int k, float2 v) {
     if (k < N) {
       float2 c = __ldg(PHASE ? &tb.chirp_ph[k] : &tb.chirp[k]);
@@ -221,7 +275,20 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
       sink(k, cmul(v, c));
     }
   };
-  fft<M, 1>(buf, tid, tw, back, out);
+  NoSrc none_in;
+  NoSink none_out;
+  constexpr int NP = Plan16<M>::NP;
+  run_range<M, -1, 0, NP - 1>(buf, tid, tw, in, none_out);
+  boundary<M, -1, 1>(buf, tid, tw, mid);
+  run_range<M, 1, 1, NP>(buf, tid, tw, none_in, out);
+}
+
+// Ask L2 for [p, p + bytes), one 128-byte line a thread of the row group (T threads): the input of
+// the row group's next row, fetched while the current row is transformed.  Every line named holds
+// bytes of the buffer.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int tid, int T) {
+  const unsigned long long a = (unsigned long long)p, first = a >> 7, last = (a + bytes - 1) >> 7;
+  for (unsigned long long l = first + tid; l <= last; l += T) asm volatile("prefetch.L2 [%0];" ::"l"(l << 7));
 }
 
 #ifndef SSHT_TORUS_MINB
@@ -268,6 +335,13 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
     const float sig = ((m + s) & 1) ? -1.f : 1.f;  // parity of column m; column m+1 has -sig
     const float2* F0 = F + ((size_t)b * N + (m + Lp)) * L;
     const float2* F1 = F0 + L;
+    {
+      const long long un = u + (long long)gridDim.x * Geo<M>::G;
+      if (un < npairs) {
+        const int bn = (int)(un / L), pn = (int)(un % L);
+        prefetch_l2(F + ((size_t)bn * N + 2 * pn) * L, (pn < Lp ? 2 : 1) * (size_t)L * sizeof(float2), tid, Geo<M>::T);
+      }
+    }
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
       const int mp = n < L ? n : N - n;  // theta frequency m' (>= 0) of DFT bin n
@@ -314,6 +388,8 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
     const long long u = u0 + threadIdx.x / Geo<M>::T;
     const bool active = u < nrows;
     const float2* x = in + (size_t)(active ? u : 0) * N;
+    if (u + (long long)gridDim.x * Geo<M>::G < nrows)
+      prefetch_l2(in + (size_t)(u + (long long)gridDim.x * Geo<M>::G) * N, (size_t)N * sizeof(float2), tid, Geo<M>::T);
     auto src = [&](int n) { return active ? x[n] : make_float2(0.f, 0.f); };
     if constexpr (SIGN > 0) {
       float2* y = out + (size_t)(active ? u : 0) * N;
@@ -375,7 +451,6 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
   const int tid = threadIdx.x % Geo<M>::T;
-  const float invN = 1.f / (float)N;
   const long long npairs = (long long)B * L;
   for (long long u0 = (long long)blockIdx.x * Geo<M>::G; u0 < npairs; u0 += (long long)gridDim.x * Geo<M>::G) {
     const long long u = u0 + threadIdx.x / Geo<M>::T;
@@ -386,6 +461,11 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
     const bool odd0 = ((m + s) & 1) != 0;
     const float sig = odd0 ? -1.f : 1.f;
     const float4* Xp = (const float4*)(X + ((size_t)b * (N + 1) + 2 * p) * L);  // pair p: columns m, m + 1
+    {
+      const long long un = u + (long long)gridDim.x * Geo<M>::G;
+      if (un < npairs)
+        prefetch_l2(X + ((size_t)(un / L) * (N + 1) + 2 * (un % L)) * L, (size_t)L * sizeof(float4), tid, Geo<M>::T);
+    }
     // extended samples of both columns on theta in [0, 2 pi): the odd one vanishes at theta = pi
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
@@ -399,39 +479,31 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
       }
       return (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);
     };
-    // theta DFT -> F (both columns summed) placed at m'' mod M with e^{-i pi m''/N}/N; the M - N
-    // remaining positions receive zeros (k >= N maps onto the gap [L, M - Lp)).
-    auto to_conv = [&](int k, float2 v) {
-      int pos;
-      float2 val;
-      if (k < N) {
-        const int mpp = k <= Lp ? k : k - N;
-        pos = mpp >= 0 ? mpp : mpp + M;
-        val = cscale(v, invN);  // e^{-i pi m''/N} in the output chirp
-      } else {
-        pos = k - N + L;
-        val = make_float2(0.f, 0.f);
-      }
-      buf[pidx(pos)] = val;
-    };
-    // Bluestein with an all-index sink: run the two FFTs directly so that k >= N reaches to_conv.
+    // Four FFTs of size M chained by fused passes: the theta DFT by Bluestein with centred
+    // outputs (the kernel's spectrum khat_c puts F_{m''}, |m''| < L, at position m'' mod M), then
+    // the circular convolution with the even weight, y = IFFT(FFT(F) * what), what = FFT(w_e)/M.
+    // Between the DFT and the convolution F_{m''} takes its output chirp, the phase
+    // e^{-i pi m''/N} and 1/N, and the positions L .. M - L (no frequency) become zeros.
     {
       auto in = [&](int n) {
         if (n >= N) return make_float2(0.f, 0.f);
         return cmul(src(n), __ldg(&tb.chirp[n]));
       };
-      auto mid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&tb.khat_f[k])); };
-      fft<M, -1>(buf, tid, tw, in, mid);
-      auto back = [&](int n) { return buf[pidx(n)]; };
-      auto out = [&](int k, float2 v) { to_conv(k, k < N ? cmul(v, __ldg(&tb.chirp_ph[k])) : v); };
-      fft<M, 1>(buf, tid, tw, back, out);
+      auto kmul = [&](int k, float2 v) { return cmul(v, __ldg(&tb.khat_c[k])); };
+      auto fmul = [&](int k, float2 v) { return cmul(v, __ldg(&tb.chirp_c[k])); };
+      auto wmul = [&](int k, float2 v) { return cmul(v, __ldg(&tb.what[k])); };
+      auto cout = [&](int k, float2 v) { buf[pidx(k)] = v; };
+      NoSrc none_in;
+      NoSink none_out;
+      constexpr int NP = Plan16<M>::NP;
+      run_range<M, -1, 0, NP - 1>(buf, tid, tw, in, none_out);
+      boundary<M, -1, 1>(buf, tid, tw, kmul);
+      run_range<M, 1, 1, NP - 1>(buf, tid, tw, none_in, none_out);
+      boundary<M, 1, -1>(buf, tid, tw, fmul);
+      run_range<M, -1, 1, NP - 1>(buf, tid, tw, none_in, none_out);
+      boundary<M, -1, 1>(buf, tid, tw, wmul);
+      run_range<M, 1, 1, NP>(buf, tid, tw, none_in, cout);
     }
-    // circular convolution with the even weight: y = IFFT(FFT(x) * what), what = FFT(w_e)/M
-    auto cin = [&](int n) { return buf[pidx(n)]; };
-    auto cmid = [&](int k, float2 v) { buf[pidx(k)] = cmul(v, __ldg(&tb.what[k])); };
-    fft<M, -1>(buf, tid, tw, cin, cmid);
-    auto cout = [&](int k, float2 v) { buf[pidx(k)] = v; };
-    fft<M, 1>(buf, tid, tw, cin, cout);
     if (active) {
       // y[m'] = H'_m[m'] + H'_{m+1}[m'], y[-m'] = sig (H'_m[m'] - H'_{m+1}[m']); fold m' < 0:
       // H = (2 - delta_{m'0}) 2 pi H'.  Tiles: the last chunk's columns m' >= L are zeros.
@@ -481,6 +553,13 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
     const int mr = active ? (int)(u % N) : 0;  // column m + Lp of field u / N
     const int m = mr - Lp;
     const float2* x = X + ((size_t)(active ? u / N : 0) * (N + 1) + (mr & ~1)) * L + (mr & 1);
+    {
+      const long long un = u + (long long)gridDim.x * Geo<M>::G;
+      if (un < nrows) {
+        const int mrn = (int)(un % N);
+        prefetch_l2(X + ((size_t)(un / N) * (N + 1) + (mrn & ~1)) * L, (size_t)L * sizeof(float4), tid, Geo<M>::T);
+      }
+    }
     auto src = [&](int n) { return (active && n < L) ? x[2 * n] : make_float2(0.f, 0.f); };
     auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };  // H'_{m''} at bin k (phase in the chirp)
     bluestein<M, -1, true>(buf, tid, tw, tb, N, src, sink);
@@ -564,13 +643,15 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
   const int NP = P16 + (REST > 1 ? 1 : 0);
   int TW = 0;
   for (int i = 1, ns = 16; i < NP; ++i, ns *= 16) TW += ((i < P16 ? 16 : REST) - 1) * ns;
-  std::vector<float2> host((size_t)N + 3 * (size_t)M + (size_t)TW + (size_t)N);
+  std::vector<float2> host((size_t)N + 3 * (size_t)M + (size_t)TW + (size_t)N + 2 * (size_t)M);
   float2* chirp = host.data();
   float2* kf = chirp + N;
   float2* ki = kf + M;
   float2* wh = ki + M;
   float2* tw = wh + M;
   float2* cph = tw + TW;
+  float2* kc = cph + N;
+  float2* cc = kc + M;
   for (int n = 0; n < N; ++n) {
     const long long r = ((long long)n * n) % (2LL * N);
     chirp[n] = make_float2((float)std::cos(-pi * r / N), (float)std::sin(-pi * r / N));
@@ -590,15 +671,28 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
         }
     }
   }
-  for (int dir = 0; dir < 2; ++dir) {
+  // output chirp of the centred forward DFT: F_m at m mod M with e^{-i pi (m^2 + m)/N}/N, zero
+  // where no frequency sits
+  for (int k = 0; k < M; ++k) {
+    const long long m = k < L ? k : k > M - L ? (long long)k - M : 0;
+    const bool in_band = k < L || k > M - L;
+    const long long r = (((m * m + m) % (2LL * N)) + 2LL * N) % (2LL * N);
+    cc[k] = in_band ? make_float2((float)(std::cos(-pi * r / N) / N), (float)(std::sin(-pi * r / N) / N))
+                    : make_float2(0.f, 0.f);
+  }
+  // chirp kernel e^{+- i pi j^2/N} at j mod M: j in (-N, N) for outputs k in [0, N) (dir 0 forward,
+  // 1 inverse); j in [-(N - 1) - (L - 1), L - 1] for the centred outputs |k| < L (dir 2), the same
+  // count 2N - 1 <= M of distinct positions
+  for (int dir = 0; dir < 3; ++dir) {
     std::vector<std::complex<double>> b(M, 0.0);
-    for (int j = -(N - 1); j <= N - 1; ++j) {
+    const int jlo = dir == 2 ? -(N - 1) - (L - 1) : -(N - 1), jhi = dir == 2 ? L - 1 : N - 1;
+    for (int j = jlo; j <= jhi; ++j) {
       const long long jj = (long long)j * j % (2LL * N);
-      const double a = (dir == 0 ? 1.0 : -1.0) * pi * (double)jj / (double)N;
-      b[(j + M) % M] = std::complex<double>(std::cos(a), std::sin(a));
+      const double a = (dir == 1 ? -1.0 : 1.0) * pi * (double)jj / (double)N;
+      b[((j % M) + M) % M] = std::complex<double>(std::cos(a), std::sin(a));
     }
     host_fft(b, -1);
-    float2* dst = dir == 0 ? kf : ki;
+    float2* dst = dir == 0 ? kf : dir == 1 ? ki : kc;
     for (int k = 0; k < M; ++k) dst[k] = make_float2((float)(b[k].real() / M), (float)(b[k].imag() / M));
   }
   {
@@ -626,6 +720,8 @@ cudaError_t torus_setup(TorusPlan** out, int L, const void* ph, int device) {
   p->tb.tw = p->buf + N + 3 * M;
   p->tb.ph = (const float2*)ph;
   p->tb.chirp_ph = p->buf + N + 3 * M + TW;
+  p->tb.khat_c = p->tb.chirp_ph + N;
+  p->tb.chirp_c = p->tb.khat_c + M;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   p->grid = sms * 8;
