@@ -263,9 +263,15 @@ def split_trace(trace, steps):
     names = ["theta_inverse", "phi_inverse", "phi_forward", "theta_forward"]
     for k, d in enumerate(fft):
         out.setdefault(names[k % 4], []).append(d)
+    rec_inv = [t1 - t0 for name, lane, t0, t1 in trace if name == "delta_inverse"]
     rec = [t1 - t0 for name, lane, t0, t1 in trace if name == "delta"]
-    for k, d in enumerate(rec):  # one recursion per call: the inverse's, then the forward's
-        out.setdefault("recursion_inverse" if k % 2 == 0 else "recursion_forward", []).append(d)
+    if rec_inv:  # 3xTF32 plans: the recursions writing the A tiles of each direction
+        out["recursion_inverse"] = rec_inv
+        if rec:
+            out["recursion_forward"] = rec
+    else:
+        for k, d in enumerate(rec):  # one recursion per call: the inverse's, then the forward's
+            out.setdefault("recursion_inverse" if k % 2 == 0 else "recursion_forward", []).append(d)
     for name, lane, t0, t1 in trace:
         key = {("inverse", 0): "contraction_inverse",
                ("project", 0): "contraction_forward", ("pack", 0): "pack_data", ("pack", 1): "pack_a",

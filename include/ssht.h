@@ -184,13 +184,15 @@ SSHT_API int ssht_wigner_delta_noalloc(int L, double* out, void* stream);
 SSHT_API int ssht_plan_check(ssht_plan_t plan);
 
 /* Stages of a transform, for ssht_plan_profile_read. */
-#define SSHT_STAGE_DELTA 0      /* Risbo recursion of Delta^l (and the spin column)       */
+#define SSHT_STAGE_DELTA 0      /* recursion of Delta^l (and the spin column); for plans  */
+                                /* whose recursion writes the A tiles, the forward's      */
 #define SSHT_STAGE_INVERSE 1    /* inverse contraction (eqn fourier_coeff)                */
 #define SSHT_STAGE_PROJECT 2    /* forward / adjoint contraction (harmonic projection)    */
 #define SSHT_STAGE_FFT 3        /* torus DFTs: fused torus passes (FP32 plans) or cuFFT   */
 #define SSHT_STAGE_TORUS 4      /* extension, phase, transpose and weight-product kernels */
 #define SSHT_STAGE_PACK 5       /* operand packing for the tensor-core contraction        */
-#define SSHT_NUM_STAGES 6
+#define SSHT_STAGE_DELTA_INVERSE 6 /* the recursion writing the inverse's A tiles (3xTF32) */
+#define SSHT_NUM_STAGES 7
 
 /* Enable (1) or disable (0) per-stage timing: each stage of each later call is bracketed by
  * CUDA events recorded on the call's stream.  Enabling resets the accumulated times. */
@@ -270,7 +272,7 @@ SSHT_API int ssht_debug_fail_allocation(int n);
 
 /* The tensor-core contraction's shape (the paper has no counterpart): cfg[0] fields per GEMM
  * launch, cfg[1] pipeline stages, cfg[2] inverse work order (0 grouped by m, 1 longest first),
- * cfg[3] forward work order (0 longest first, 1 grouped by m).  SSHT_EUNSUPPORTED for plans
+ * cfg[3] forward work order (0 grouped by m, 1 longest first).  SSHT_EUNSUPPORTED for plans
  * without tensor-core contraction. */
 SSHT_API int ssht_plan_tile_config(ssht_plan_t plan, int* cfg);
 

@@ -294,7 +294,7 @@ bool tiles_direct(const ssht_plan_s* p) {
 // Delta and the contraction's A operand of one direction, on st.
 int make_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (tiles_direct(p)) {
-    StageScope sc(p, SSHT_STAGE_DELTA, st);
+    StageScope sc(p, forward ? SSHT_STAGE_DELTA : SSHT_STAGE_DELTA_INVERSE, st);
     if (forward)
       SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
     else

@@ -37,6 +37,7 @@
 #include "tc_common.cuh"
 
 #include <algorithm>
+#include <queue>
 #include <vector>
 
 namespace ssht {
@@ -63,7 +64,7 @@ struct Item {
 struct TcArgs {
   int L, s, B, NC;        // B: fields of this slice; NC = 2H: padded columns, H = 2 Bs rounded up to 16 (<= 128)
   int stages;             // pipeline depth
-  int nitems;
+  const int* sched;       // CTA b runs items [sched[b], sched[b + 1]) in order
   const Item* items;
   const uint8_t* A;       // packed A tiles
   const uint8_t* X;       // packed data tiles
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       // ---- producer: bulk copies of the A and data tiles of every chunk ----
       int it = 0;
       int last_use[MAX_STAGES] = {-1, -1, -1, -1};
-      for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+      for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1] && !*abort; ++w) {
         const Item itm = a.items[w];
         const uint8_t* Ab = a.A + (size_t)itm.atile * A_TILE;
         for (int c = itm.c0; c < itm.c1; ++c, ++it) {
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       // ---- MMA issuer: one tensor-memory segment per chunk, corrections first ----
       const uint32_t idesc = BF ? idesc_bf16(TM, a.NC) : idesc_tf32(TM, a.NC);
       int it = 0;
-      for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+      for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1] && !*abort; ++w) {
         const Item itm = a.items[w];
         bool ok = true;
         for (int c = itm.c0; c < itm.c1; ++c, ++it) {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
     const int H = a.NC / 2;
     const uint32_t tq = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * H);
     int it = 0;
-    for (int w = blockIdx.x; w < a.nitems && !*abort; w += gridDim.x) {
+    for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1] && !*abort; ++w) {
       const Item itm = a.items[w];
       float acc[128];
 #pragma unroll
@@ -387,8 +388,11 @@ struct TcPlan {
   int Bs = 0, nS = 0;        // fields per slice (one GEMM launch each) and slices
   size_t xslice = 0;         // bytes of one slice's data tiles
   std::vector<Item> inv_h, fwd_h;  // work items in creation order (re-sorted by the configuration)
-  Item* items_inv = nullptr;
+  Item* items_inv = nullptr;  // in schedule order: CTA-major
   Item* items_fwd = nullptr;
+  int* sched_inv = nullptr;   // per CTA: first item (grid + 1 entries)
+  int* sched_fwd = nullptr;
+  int grid_inv = 0, grid_fwd = 0;
   int n_inv = 0, n_fwd = 0;
   long long tiles_A = 0, tiles_inv = 0, xtiles_inv = 0, xtiles_fwd = 0;
   // Forward A tiles (m, i, c): rows l = 128 i + r, K = m' = 32 c + k, tile index abase[m] +
@@ -430,6 +434,34 @@ bool tc_config_fits(const TcPlan* p, const TcConfig& c) {
   return (size_t)c.stages * stage_bytes_of(nc_of(Bs)) + 1024 <= (size_t)p->smem_max;
 }
 
+// Assign the items, in list order, each to the CTA that becomes free first, with a cost of its
+// chunk count plus a fixed share for its epilogue: the schedule a shared work counter would give,
+// made on the host.  Items next to each other in the list then run at about the same time on
+// different SMs, so that the data tiles they share are read from HBM about once, and the longest
+// CTA finishes close to the mean.  Uploads the items CTA-major and the per-CTA offsets.
+static cudaError_t schedule(const std::vector<Item>& items, int grid, Item* d_items, int* d_sched) {
+  constexpr long long kEpilogueChunks = 2;
+  std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>, std::greater<>> free_at;
+  for (int b = 0; b < grid; ++b) free_at.push({0, b});
+  std::vector<std::vector<int>> per(grid);
+  for (int w = 0; w < (int)items.size(); ++w) {
+    const auto top = free_at.top();
+    free_at.pop();
+    per[top.second].push_back(w);
+    free_at.push({top.first + (items[w].c1 - items[w].c0) + kEpilogueChunks, top.second});
+  }
+  std::vector<Item> out;
+  std::vector<int> start(grid + 1, 0);
+  out.reserve(items.size());
+  for (int b = 0; b < grid; ++b) {
+    start[b] = (int)out.size();
+    for (int w : per[b]) out.push_back(items[w]);
+  }
+  start[grid] = (int)out.size();
+  cudaError_t e = cudaMemcpy(d_items, out.data(), out.size() * sizeof(Item), cudaMemcpyHostToDevice);
+  return e != cudaSuccess ? e : cudaMemcpy(d_sched, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
+}
+
 cudaError_t tc_configure(TcPlan* p, const TcConfig& c) {
   if (!tc_config_fits(p, c)) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -448,10 +480,10 @@ cudaError_t tc_configure(TcPlan* p, const TcConfig& c) {
   p->nS = nS;
   p->NC = NC;
   p->xslice = xslice;
-  // Work order.  Inverse: the row blocks of each group of 4 consecutive m run together, so that
-  // their data tiles are read from HBM about once (ncu, L = 1024, B = 64: 7.1 -> 5.8 GB read), or
-  // longest first.  Forward: longest first (neighbouring m together, which lets L2 merge their
-  // scattered output writes) or grouped like the inverse.
+  // Work order (the schedule then hands the items out in this order).  Grouped: the row blocks of
+  // each group of 4 consecutive m run together, so that their data tiles are read from HBM about
+  // once and the output rows of neighbouring m meet in L2.  Longest first: the classic order for
+  // balance.  Order 0 (the default) is grouped in both directions.
   auto grouped = [](const Item& x, const Item& y) {
     if (x.m / 4 != y.m / 4) return x.m / 4 < y.m / 4;
     if (x.i != y.i) return x.i > y.i;
@@ -461,10 +493,10 @@ cudaError_t tc_configure(TcPlan* p, const TcConfig& c) {
   std::vector<Item> inv = p->inv_h, fwd = p->fwd_h;
   if (c.inv_order == 0) std::stable_sort(inv.begin(), inv.end(), grouped);
   else std::stable_sort(inv.begin(), inv.end(), longest_first);
-  if (c.fwd_order == 0) std::stable_sort(fwd.begin(), fwd.end(), longest_first);
-  else std::stable_sort(fwd.begin(), fwd.end(), grouped);
-  if ((e = cudaMemcpy(p->items_inv, inv.data(), inv.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-  if ((e = cudaMemcpy(p->items_fwd, fwd.data(), fwd.size() * sizeof(Item), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if (c.fwd_order == 0) std::stable_sort(fwd.begin(), fwd.end(), grouped);
+  else std::stable_sort(fwd.begin(), fwd.end(), longest_first);
+  if ((e = schedule(inv, p->grid_inv, p->items_inv, p->sched_inv)) != cudaSuccess) return e;
+  if ((e = schedule(fwd, p->grid_fwd, p->items_fwd, p->sched_fwd)) != cudaSuccess) return e;
   p->smem = (size_t)c.stages * stage_bytes_of(NC) + 1024;
   p->cfg = c;
   return cudaSuccess;
@@ -523,8 +555,13 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
     p->grid = sms;
     p->smem_max = optin - 2048;  // the kernel's static shared memory and alignment slack
   }
+  // the inverse leaves one SM to the recursion that writes the forward's operands meanwhile
+  p->grid_inv = std::max(1, std::min(p->grid - 1, (int)inv.size()));
+  p->grid_fwd = std::max(1, std::min(p->grid, (int)fwd.size()));
   if ((e = tc_alloc((void**)&p->items_inv, inv.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->sched_inv, (p->grid_inv + 1) * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->sched_fwd, (p->grid_fwd + 1) * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->A, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
   // zero once (entries no call writes stay zero); cudaMemset is asynchronous on the legacy
   // stream, and the plans' packing and recursions run on non-blocking streams: wait for it
@@ -567,7 +604,7 @@ fail:
 
 void tc_destroy(TcPlan* p) {
   if (!p) return;
-  void* ptrs[] = {p->items_inv, p->items_fwd, p->A, p->A_inv, p->abase, p->ibase, p->X, p->xoff, p->xc0};
+  void* ptrs[] = {p->items_inv, p->items_fwd, p->sched_inv, p->sched_fwd, p->A, p->A_inv, p->abase, p->ibase, p->X, p->xoff, p->xc0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -643,7 +680,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
     a.B = std::min(p->Bs, p->B - sl * p->Bs);
     a.NC = p->NC;
     a.stages = p->cfg.stages;
-    a.nitems = forward ? p->n_fwd : p->n_inv;
+    a.sched = forward ? p->sched_fwd : p->sched_inv;
     a.items = forward ? p->items_fwd : p->items_inv;
     a.A = forward ? p->A : p->A_inv;
     a.X = p->X + (size_t)sl * p->xslice;
@@ -654,7 +691,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
     a.out = (float2*)out + (size_t)sl * p->Bs * per_field;
     a.status = status;
     a.wait_ns = wait_ns;
-    const int grid = std::min(forward ? p->grid : std::max(p->grid - 1, 1), std::max(a.nitems, 1));
+    const int grid = forward ? p->grid_fwd : p->grid_inv;
     if (forward && p->bf16)
       tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
     else if (forward)

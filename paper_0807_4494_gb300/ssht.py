@@ -29,7 +29,7 @@ EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspac
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
            "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_plan_tile_config",
            "ssht_group_bucket_tile_config", "ssht_last_error", "ssht_version")
-STAGES = ("delta", "inverse", "project", "fft", "torus", "pack")
+STAGES = ("delta", "inverse", "project", "fft", "torus", "pack", "delta_inverse")
 
 
 class SshtError(RuntimeError):

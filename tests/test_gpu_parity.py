@@ -435,8 +435,15 @@ def test_profile_totals_and_trace(precision):
         spans = [(t0, t1) for _, ln, t0, t1 in trace if ln == lane]
         assert all(a[1] <= b[0] + 1e-3 for a, b in zip(spans, spans[1:]))
     aux = {name for name, lane, _, _ in trace if lane == 1}
-    assert aux == {"delta"}  # (3xTF32: the recursion writes the A tiles of both directions itself)
-    assert sum(1 for name, _, _, _ in trace if name == "delta") == 4
+    if precision == "fp64":
+        # one table recursion per call
+        assert aux == {"delta"}
+        assert sum(1 for name, _, _, _ in trace if name == "delta") == 4
+    else:
+        # 3xTF32: the recursions write the A tiles of both directions themselves, one per call
+        assert aux == {"delta", "delta_inverse"}
+        assert sum(1 for name, _, _, _ in trace if name == "delta") == 2
+        assert sum(1 for name, _, _, _ in trace if name == "delta_inverse") == 2
     # the trace was folded into the totals
     totals, launches = plan.profile_read()
     assert launches > 0
