@@ -270,6 +270,16 @@ SSHT_API int ssht_group_check(ssht_group_t group);
  * SSHT_ENOMEM after releasing what they had allocated.  n < 0 returns SSHT_EINVAL. */
 SSHT_API int ssht_debug_fail_allocation(int n);
 
+/* Index checks of the bounds-checked build (the paper has no counterpart; the library compiled
+ * with -DSSHT_DEBUG, `python -m paper_0807_4494_gb300.build --debug`): in that build every checked
+ * global access of the kernels (torus passes, packing, tensor-core contraction, recursions writing
+ * the tiles, real-field and spin-pair kernels, SIMT contractions) tests its index against the extent
+ * of its buffer and skips it when it lies outside.  *count receives the number of such accesses
+ * since the last call, *site / *index / *extent the first one's site (an internal number), index
+ * and extent (null pointers are skipped); the record is then cleared.  Synchronises the device.
+ * Release builds check nothing: SSHT_EUNSUPPORTED. */
+SSHT_API int ssht_debug_bounds(long long* count, int* site, long long* index, long long* extent);
+
 /* The tensor-core contraction's shape (the paper has no counterpart): cfg[0] fields per GEMM
  * launch, cfg[1] pipeline stages, cfg[2] inverse work order (0 grouped by m, 1 longest first),
  * cfg[3] forward work order (0 grouped by m, 1 longest first).  SSHT_EUNSUPPORTED for plans

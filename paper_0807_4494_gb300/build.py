@@ -2,6 +2,10 @@
 
 Usage: ``python -m paper_0807_4494_gb300.build`` (or ``build()`` from Python).  The result is
 ``paper_0807_4494_gb300/lib/libssht.so``; object files go to ``paper_0807_4494_gb300/_build/``.
+``--debug`` (``build(debug=True)``) makes the bounds-checked library instead,
+``lib/libssht_debug.so`` (objects in ``_build_debug/``), compiled with -DSSHT_DEBUG: every checked
+kernel access tests its index against its buffer's extent (see ssht_debug_bounds); load it with
+SSHT_LIBRARY=<path>.
 """
 import concurrent.futures as cf
 import glob
@@ -32,27 +36,34 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(ROOT, "include", "ssht.h")]
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+            [os.path.join(ROOT, "include", "ssht.h")])
 
 
-def _up_to_date():
-    if not os.path.exists(LIB):
+DEBUG_LIB = os.path.join(LIBDIR, "libssht_debug.so")
+
+
+def _up_to_date(lib):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose=False):
-    if not force and _up_to_date():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force=False, verbose=False, debug=False):
+    lib = DEBUG_LIB if debug else LIB
+    obj_dir = OBJ + "_debug" if debug else OBJ
+    flags = FLAGS + (["-DSSHT_DEBUG"] if debug else [])
+    if not force and _up_to_date(lib):
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-        cmd = [cc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
+        cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -62,14 +73,15 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+    print(build(force=True, verbose=True, debug="--debug" in sys.argv[1:]))

@@ -1,6 +1,7 @@
 // C ABI of libssht (declared in include/ssht.h): plans, workspaces, the order of the
 // stages of each transform, host-pointer staging and error reporting.
 #include "ssht_internal.h"
+#include "bounds.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -109,6 +110,7 @@ struct ssht_plan_s {
   float* Uf = nullptr;  // U in FP32 (tensor-core operand packing)
   void* W1 = nullptr;
   void* W2 = nullptr;
+  size_t w_bytes = 0;  // each of W1, W2
   void* W3 = nullptr;
   void* khat = nullptr;
   void* ph = nullptr;       // phase table, element precision
@@ -244,9 +246,13 @@ int run_dft(ssht_plan_t p, cufftHandle h, int sign, void* in, void* out, cudaStr
 }
 
 // One fused torus pass of an FP32 plan (DFT along theta or phi with its glue), timed as FFT work.
+// in / out: a plan workspace (W1, W2) or a grid of the plan's B complex fields.
 int run_torus(ssht_plan_t p, int which, const void* in, void* out, cudaStream_t st) {
   StageScope sc(p, SSHT_STAGE_FFT, st);
-  SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, in, out, st), "torus pass");
+  const size_t grid = p->pair_grid_bytes();
+  const size_t ib = (in == p->W1 || in == p->W2) ? p->w_bytes : grid;
+  const size_t ob = (out == p->W1 || out == p->W2) ? p->w_bytes : grid;
+  SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, in, ib, out, ob, st), "torus pass");
   p->launches += 1;
   return 0;
 }
@@ -411,7 +417,7 @@ int theta_to_tiles(ssht_plan_t p, int which, void* flm, cudaStream_t st) {
   const TileOut tiles = tc_forward_tiles(p->tc);
   {
     StageScope sc(p, SSHT_STAGE_FFT, st);
-    SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, p->W2, nullptr, st, &tiles), "torus pass");
+    SSHT_CUDA(torus_pass(p->torus, which, p->s, p->B, p->W2, p->w_bytes, nullptr, 0, st, &tiles), "torus pass");
     p->launches += 1;
   }
   if ((rc = join_operands(p, st)) || (rc = tc_multiply(p, 1, flm, st))) return rc;
@@ -426,7 +432,8 @@ int project(ssht_plan_t p, const void* H, void* flm, cudaStream_t st) {
   if ((rc = join_operands(p, st))) return rc;
   {
     StageScope sc(p, SSHT_STAGE_PROJECT, st);
-    SSHT_CUDA(contract_project_simt<T>(p->d, p->s, p->B, p->delta.table, p->U, H, flm, st), "projection");
+    SSHT_CUDA(contract_project_simt<T>(p->d, p->s, p->B, p->delta.table, p->U, H, p->w_bytes, flm, p->pair_coeff_bytes(), st),
+              "projection");
     p->launches += 1;
   }
   return mark_free(p, st);
@@ -527,7 +534,8 @@ int inverse_impl(ssht_plan_t p, const void* flm, void* f, cudaStream_t st) {
   } else {
     if ((rc = join_operands(p, st))) return rc;
     StageScope sc(p, SSHT_STAGE_INVERSE, st);
-    SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->W1, p->ph64, p->torus ? 1 : 0, st),
+    SSHT_CUDA(contract_inverse_simt<T>(d, p->s, p->B, p->delta.table, p->U, flm, p->pair_coeff_bytes(), p->W1, p->w_bytes,
+                                       p->ph64, p->torus ? 1 : 0, st),
               "inverse contraction");
     p->launches += 1;
   }
@@ -900,6 +908,7 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
   }
   if ((rc = dalloc(p, &p->W1, torus, "torus workspace 1"))) return bail(rc);
   if ((rc = dalloc(p, &p->W2, torus, "torus workspace 2"))) return bail(rc);
+  p->w_bytes = torus;
   if (p->f64) {
     if ((rc = dalloc(p, &p->W3, (size_t)B * d.N * d.M * p->elem, "convolution workspace"))) return bail(rc);
     if ((rc = dalloc(p, &p->khat, (size_t)d.M * p->elem, "weight spectrum"))) return bail(rc);
@@ -1241,6 +1250,26 @@ int ssht_debug_fail_allocation(int n) {
   if (n < 0) return fail(SSHT_EINVAL, "ssht_debug_fail_allocation: n must be >= 0");
   g_alloc_countdown.store(n);
   return SSHT_OK;
+}
+
+int ssht_debug_bounds(long long* count, int* site, long long* index, long long* extent) {
+  if (!kBoundsChecked) return fail(SSHT_EUNSUPPORTED, "ssht_debug_bounds: this library was built without index checks");
+  SSHT_CUDA(cudaDeviceSynchronize(), "synchronize");
+  cudaError_t (*take[])(BoundsRecord*) = {bounds_take_torus_pass, bounds_take_contract_tc, bounds_take_delta_column,
+                                          bounds_take_real, bounds_take_contract_simt};
+  BoundsRecord first{};
+  long long total = 0;
+  for (auto f : take) {
+    BoundsRecord r{};
+    SSHT_CUDA(f(&r), "index-check record");
+    if (r.count && !total) first = r;
+    total += (long long)r.count;
+  }
+  if (count) *count = total;
+  if (site) *site = total ? first.kernel : 0;
+  if (index) *index = total ? first.index : 0;
+  if (extent) *extent = total ? first.extent : 0;
+  return 0;
 }
 
 int ssht_version(void) { return 100; }

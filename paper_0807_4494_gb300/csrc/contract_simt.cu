@@ -15,6 +15,7 @@
 // owns (l, |m|); the lanes stride over m' and the sums are closed with warp shuffles.  Rows
 // of the quadrant table are read contiguously through Delta^l_{m' m} = (-1)^{m'-m} Delta^l_{m m'}.
 #include "ssht_internal.h"
+#include "bounds.cuh"
 
 namespace ssht {
 namespace {
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(256) inverse_kernel(int L, int s, int B, const
                                                       const double* __restrict__ U,
                                                       const typename Cplx<T>::type* __restrict__ flm,
                                                       typename Cplx<T>::type* __restrict__ E,
-                                                      const double2* __restrict__ ph, int half) {
+                                                      const double2* __restrict__ ph, int half, long long in_n,
+                                                      long long out_n) {
   using C = typename Cplx<T>::type;
   const int Lp = L - 1, N = 2 * L - 1;
   const int m = blockIdx.x * 32 + threadIdx.x;  // |m|
@@ -60,8 +62,11 @@ __global__ void __launch_bounds__(256) inverse_kernel(int L, int s, int B, const
 #pragma unroll
     for (int j = 0; j < BB; ++j) {
       if (b0 + j < B) {
-        const C a = flm[(size_t)(b0 + j) * L * L + cp];
-        const C an = flm[(size_t)(b0 + j) * L * L + cn];
+        const long long fb = (long long)(b0 + j) * L * L;
+        C a, an;
+        a.x = a.y = an.x = an.y = T(0);
+        if (in_bounds(fb + (long long)cp, in_n, kbSimtIn)) a = flm[fb + cp];
+        if (in_bounds(fb + (long long)cn, in_n, kbSimtIn)) an = flm[fb + cn];
         pr[j] = fma(t, (T)a.x, pr[j]);
         pi[j] = fma(t, (T)a.y, pi[j]);
         if (l & 1) {
@@ -95,17 +100,19 @@ __global__ void __launch_bounds__(256) inverse_kernel(int L, int s, int B, const
       if (half) {
         v.x = (T)Fr;
         v.y = (T)Fi;
-        E[((size_t)(b0 + j) * N + (mm + Lp)) * L + mp] = v;
+        const long long o = ((long long)(b0 + j) * N + (mm + Lp)) * L + mp;
+        if (in_bounds(o, out_n, kbSimtOut)) E[o] = v;
         continue;
       }
       C* row = E + ((size_t)(b0 + j) * N + (mm + Lp)) * N;
       v.x = (T)(Fr * eth.x - Fi * eth.y);
       v.y = (T)(Fr * eth.y + Fi * eth.x);
-      row[mp] = v;
+      const long long o = ((long long)(b0 + j) * N + (mm + Lp)) * N;
+      if (in_bounds(o + mp, out_n, kbSimtOut)) row[mp] = v;
       if (mp > 0) {
         v.x = (T)(sig * (Fr * ethc.x - Fi * ethc.y));
         v.y = (T)(sig * (Fr * ethc.y + Fi * ethc.x));
-        row[N - mp] = v;
+        if (in_bounds(o + N - mp, out_n, kbSimtOut)) row[N - mp] = v;
       }
     }
   }
@@ -115,7 +122,8 @@ template <typename T, int BB>
 __global__ void __launch_bounds__(256) project_kernel(int L, int s, int B, const double* __restrict__ table,
                                                       const double* __restrict__ U,
                                                       const typename Cplx<T>::type* __restrict__ H,
-                                                      typename Cplx<T>::type* __restrict__ flm) {
+                                                      typename Cplx<T>::type* __restrict__ flm, long long in_n,
+                                                      long long out_n) {
   using C = typename Cplx<T>::type;
   const int Lp = L - 1;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -137,8 +145,11 @@ __global__ void __launch_bounds__(256) project_kernel(int L, int s, int B, const
 #pragma unroll
     for (int j = 0; j < BB; ++j) {
       if (b0 + j < B) {
-        const C hp = H[((size_t)(b0 + j) * N + (m + Lp)) * L + mp];
-        const C hn = H[((size_t)(b0 + j) * N + (Lp - m)) * L + mp];
+        const long long ip = ((long long)(b0 + j) * N + (m + Lp)) * L + mp, in = ((long long)(b0 + j) * N + (Lp - m)) * L + mp;
+        C hp, hn;
+        hp.x = hp.y = hn.x = hn.y = T(0);
+        if (in_bounds(ip, in_n, kbSimtIn)) hp = H[ip];
+        if (in_bounds(in, in_n, kbSimtIn)) hn = H[in];
         ppr[j] = fma(v, (T)hp.x, ppr[j]);
         ppi[j] = fma(v, (T)hp.y, ppi[j]);
         npr[j] = fma(v, (T)hn.x, npr[j]);
@@ -176,7 +187,8 @@ __global__ void __launch_bounds__(256) project_kernel(int L, int s, int B, const
       C out;
       out.x = (T)(fr * ar - fi * ai);
       out.y = (T)(fr * ai + fi * ar);
-      flm[(size_t)(b0 + j) * L * L + (size_t)l * l + l + mm] = out;
+      const long long o = (long long)(b0 + j) * L * L + (long long)l * l + l + mm;
+      if (in_bounds(o, out_n, kbSimtOut)) flm[o] = out;
     }
   }
 }
@@ -185,30 +197,39 @@ __global__ void __launch_bounds__(256) project_kernel(int L, int s, int B, const
 
 template <typename T>
 cudaError_t contract_inverse_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* flm, void* E, const double2* ph, int half, cudaStream_t st) {
+                                  const void* flm, size_t flm_bytes, void* E, size_t e_bytes, const double2* ph, int half,
+                                  cudaStream_t st) {
   using C = typename Cplx<T>::type;
   constexpr int BB = 2;
   dim3 block(32, 8);
   dim3 grid((d.L + 31) / 32, (d.L + 7) / 8, (B + BB - 1) / BB);
-  inverse_kernel<T, BB><<<grid, block, 0, st>>>(d.L, s, B, table, U, (const C*)flm, (C*)E, ph, half);
+  inverse_kernel<T, BB><<<grid, block, 0, st>>>(d.L, s, B, table, U, (const C*)flm, (C*)E, ph, half,
+                                                    (long long)(flm_bytes / sizeof(C)), (long long)(e_bytes / sizeof(C)));
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* H, void* flm, cudaStream_t st) {
+                                  const void* H, size_t h_bytes, void* flm, size_t flm_bytes, cudaStream_t st) {
   using C = typename Cplx<T>::type;
   constexpr int BB = 2;
   const long long warps = tri_ll(d.L);
   const int threads = 256;
   dim3 grid((unsigned)((warps * 32 + threads - 1) / threads), (B + BB - 1) / BB);
-  project_kernel<T, BB><<<grid, threads, 0, st>>>(d.L, s, B, table, U, (const C*)H, (C*)flm);
+  project_kernel<T, BB><<<grid, threads, 0, st>>>(d.L, s, B, table, U, (const C*)H, (C*)flm, (long long)(h_bytes / sizeof(C)),
+                                                   (long long)(flm_bytes / sizeof(C)));
   return cudaGetLastError();
 }
 
-template cudaError_t contract_inverse_simt<double>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, int, cudaStream_t);
-template cudaError_t contract_inverse_simt<float>(const Dims&, int, int, const double*, const double*, const void*, void*, const double2*, int, cudaStream_t);
-template cudaError_t contract_project_simt<double>(const Dims&, int, int, const double*, const double*, const void*, void*, cudaStream_t);
-template cudaError_t contract_project_simt<float>(const Dims&, int, int, const double*, const double*, const void*, void*, cudaStream_t);
+template cudaError_t contract_inverse_simt<double>(const Dims&, int, int, const double*, const double*, const void*, size_t, void*,
+                                                   size_t, const double2*, int, cudaStream_t);
+template cudaError_t contract_inverse_simt<float>(const Dims&, int, int, const double*, const double*, const void*, size_t, void*,
+                                                  size_t, const double2*, int, cudaStream_t);
+template cudaError_t contract_project_simt<double>(const Dims&, int, int, const double*, const double*, const void*, size_t, void*,
+                                                   size_t, cudaStream_t);
+template cudaError_t contract_project_simt<float>(const Dims&, int, int, const double*, const double*, const void*, size_t, void*,
+                                                  size_t, cudaStream_t);
+
+SSHT_BOUNDS_TU(contract_simt)
 
 }  // namespace ssht

@@ -33,6 +33,7 @@
 // the CTAs.  Every wait is bounded; a
 // timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
 #include "ssht_internal.h"
+#include "bounds.cuh"
 #include "f32_round.h"
 #include "tc_common.cuh"
 
@@ -74,6 +75,7 @@ struct TcArgs {
   float2* out;            // inverse: theta-DFT input E [B][N][N]; forward: flm [B][L*L]
   int* status;
   long long wait_ns;      // spin limit of the pipeline waits
+  long long a_tiles, x_tiles, out_n;  // extents of A, this slice's data tiles and out (index checks)
 };
 
 __device__ __forceinline__ float2 ipow_signed(int s, int k) {
@@ -94,7 +96,7 @@ __device__ __forceinline__ float2 ipow_signed(int s, int k) {
 template <bool FWD, bool BF>
 __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* __restrict__ items,
                                                      const double* __restrict__ table, const float* __restrict__ Uf,
-                                                     uint8_t* __restrict__ A) {
+                                                     uint8_t* __restrict__ A, long long a_tiles) {
   __shared__ __align__(16) uint8_t tile[A_TILE];
   constexpr int PER = TM * TK / 256;
   const Item it = items[blockIdx.y];
@@ -111,8 +113,9 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
     const int mp = FWD ? colv : rowv, l = FWD ? rowv : colv;
     const bool ok = l <= Lp && mp <= Lp && l >= m && l >= mp && l >= as;
     // Delta^l_{m' m} = (-1)^{m'-m} Delta^l_{m m'}: row m of degree l, contiguous in m'
-    d[q] = ok ? __ldg(&table[doff(l) + (size_t)m * (l + 1) + mp]) : 0.0;
-    u[q] = ok ? __ldg(&Uf[tri_ll(l) + mp]) : 0.f;
+    const long long ti = (long long)doff(l) + (long long)m * (l + 1) + mp, ui = (long long)tri_ll(l) + mp;
+    d[q] = (ok && in_bounds(ti, (long long)doff(L), kbPackAIn)) ? __ldg(&table[ti]) : 0.0;
+    u[q] = (ok && in_bounds(ui, (long long)tri_ll(L), kbPackAIn)) ? __ldg(&Uf[ui]) : 0.f;
   }
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
     put_split<BF>(tile, A_PART, r, k, ((mp - m) & 1) ? -a : a);
   }
   __syncthreads();
+  if (!in_bounds(it.atile + blockIdx.x, a_tiles, kbPackAOut)) return;
   uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * A_TILE);
   const uint4* src = (const uint4*)tile;
   for (int e = threadIdx.x; e < A_TILE / 16; e += blockDim.x) dst[e] = src[e];
@@ -144,6 +148,8 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
                                                      const float2* __restrict__ flm, uint8_t* __restrict__ X) {
   __shared__ float2 sv[32][33];
   const int B = min(Bs, Btot - (int)blockIdx.z * Bs);
+  const long long flm_n = (long long)Btot * L * L, flm0 = (long long)blockIdx.z * Bs * L * L;
+  const long long x_tiles = (long long)(xslice / (2 * (size_t)NC * 128));
   flm += (size_t)blockIdx.z * Bs * L * L;
   X += (size_t)blockIdx.z * xslice;
   const int c = blockIdx.x, m0 = 16 * blockIdx.y;
@@ -157,8 +163,9 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
         const int lo = q >> 5, col = q & 31, sign = col >> 4, m = m0 + (col & 15);
         const int l = c * TK + lo;
         float2 v = make_float2(0.f, 0.f);
-        if (m < L && l < L && l >= m && l >= as && !(sign && m == 0)) {
-          v = flm[(size_t)b * L * L + (size_t)l * l + l + (sign ? -m : m)];
+        const long long fi = (long long)b * L * L + (long long)l * l + l + (sign ? -m : m);
+        if (m < L && l < L && l >= m && l >= as && !(sign && m == 0) && in_bounds(flm0 + fi, flm_n, kbPackVIn)) {
+          v = flm[fi];
           if (sign && (l & 1)) v = make_float2(-v.x, -v.y);
         }
         sv[lo][col] = v;
@@ -168,6 +175,8 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
     for (int cb = warp; cb < 32; cb += 8) {
       const int sign = cb >> 4, m = m0 + (cb & 15);
       if (m >= L || c < xc0[m]) continue;  // tile (m, c) is not stored
+      if (!in_bounds(xoff[m] + (c - xc0[m]), x_tiles, kbPackVOut) || !in_bounds(sign * half + 2 * b + 1, NC, kbPackVOut))
+        continue;
       uint8_t* tile = X + (size_t)(xoff[m] + (c - xc0[m])) * 2 * part_bytes;
       const float2 v = b < B ? sv[lane][cb] : make_float2(0.f, 0.f);
       const int j = sign * half + 2 * b;
@@ -246,8 +255,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
           }
           uint8_t* st = smem + s * stage_bytes;
           mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
-          bulk_g2s(st, Ab + (size_t)(c - itm.c0) * A_TILE, A_TILE, &full[s]);
-          const long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
+          // a tile index outside its array is recorded and tile 0 copied instead (the pipeline
+          // still completes; the result is wrong and the record says why)
+          const long long at = itm.atile + (c - itm.c0);
+          const uint8_t* asrc = in_bounds(at, a.a_tiles, kbGemmA) ? Ab + (size_t)(c - itm.c0) * A_TILE : a.A;
+          bulk_g2s(st, asrc, A_TILE, &full[s]);
+          long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
+          if (!in_bounds(xt, a.x_tiles, kbGemmX)) xt = 0;
           bulk_g2s(st + A_TILE, a.X + (size_t)xt * 2 * b_part, (uint32_t)(2 * b_part), &full[s]);
           last_use[s] = u;
         }
@@ -360,11 +374,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
         if (b >= B) break;
         const float xr = rs * acc[2 * b], xi = rs * acc[2 * b + 1];
         const float2 F = make_float2(pz.x * xr - pz.y * xi, pz.x * xi + pz.y * xr);
-        if (FWD) {
-          a.out[(size_t)b * L * L + (size_t)rowv * rowv + rowv + mm] = F;
-        } else {
-          a.out[((size_t)b * NT + (mm + Lp)) * L + rowv] = F;  // half row m' >= 0
-        }
+        const long long o = FWD ? (long long)b * L * L + (long long)rowv * rowv + rowv + mm
+                                : ((long long)b * NT + (mm + Lp)) * L + rowv;  // half row m' >= 0
+        if (in_bounds(o, a.out_n, kbGemmOut)) a.out[o] = F;
       }
     }
   }
@@ -619,6 +631,7 @@ InvTiles tc_inverse_tiles(const TcPlan* p) {
     t.ibase = p->ibase;
     t.nI = p->nI;
     t.nC = p->nC;
+    t.ntiles = p->tiles_inv;
   }
   return t;
 }
@@ -628,6 +641,7 @@ ATiles tc_a_tiles(const TcPlan* p) {
   if (p && !p->bf16) {
     t.A = p->A;
     t.abase = p->abase;
+    t.ntiles = p->tiles_A;
   }
   return t;
 }
@@ -636,13 +650,13 @@ cudaError_t tc_pack_a(TcPlan* p, int forward, const double* table, const float* 
   // one block per (item, chunk): grid.x covers the longest item (at most nC chunks), grid.y the items
   const dim3 gf(p->nC, p->n_fwd), gi(p->nC, p->n_inv);
   if (forward && p->bf16)
-    pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
+    pack_a_kernel<true, true><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A, p->tiles_A);
   else if (forward)
-    pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A);
+    pack_a_kernel<true, false><<<gf, 256, 0, st>>>(p->L, p->s, p->items_fwd, table, U, p->A, p->tiles_A);
   else if (p->bf16)
-    pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+    pack_a_kernel<false, true><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv, p->tiles_inv);
   else
-    pack_a_kernel<false, false><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv);
+    pack_a_kernel<false, false><<<gi, 256, 0, st>>>(p->L, p->s, p->items_inv, table, U, p->A_inv, p->tiles_inv);
   *launches += 1;
   return cudaGetLastError();
 }
@@ -667,6 +681,7 @@ TileOut tc_forward_tiles(const TcPlan* p) {
   o.mode = p->bf16 ? 2 : 1;
   o.Bs = p->Bs;
   o.xslice = p->xslice;
+  o.xbytes = p->xbytes;
   return o;
 }
 
@@ -691,6 +706,9 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
     a.out = (float2*)out + (size_t)sl * p->Bs * per_field;
     a.status = status;
     a.wait_ns = wait_ns;
+    a.a_tiles = forward ? p->tiles_A : p->tiles_inv;
+    a.x_tiles = (long long)(p->xslice / (2 * (size_t)p->NC * 128));
+    a.out_n = (long long)a.B * (long long)per_field;
     const int grid = forward ? p->grid_fwd : p->grid_inv;
     if (forward && p->bf16)
       tc_gemm_kernel<true, true><<<grid, THREADS, p->smem, st>>>(a);
@@ -706,5 +724,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
   }
   return cudaSuccess;
 }
+
+SSHT_BOUNDS_TU(contract_tc)
 
 }  // namespace ssht

@@ -29,6 +29,7 @@
 // value is back in range; entries below 2^-1021 are written as 0 (they are below 1e-307 and
 // contribute nothing to any transform).
 #include "ssht_internal.h"
+#include "bounds.cuh"
 #include "f32_round.h"
 #include "tc_common.cuh"
 
@@ -59,10 +60,12 @@ struct ColumnParams {
   const float* Uf;         // U_l[m'] in FP32 at l(l+1)/2 + m'
   uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m', hi then lo
   const long long* abase;  // per m: index of the tile (m, m / 128, 0)
+  long long extent;        // entries of the table, or tiles of A (index checks)
 };
 
 // Writes A_M[l][K] = x (already in FP32) split hi + lo into row l mod 128 of tile (M, l / 128, K / 32).
-__device__ __forceinline__ void put_a(uint8_t* A, long long tile, int row, int k, float x) {
+__device__ __forceinline__ void put_a(uint8_t* A, long long tile, long long ntiles, int site, int row, int k, float x) {
+  if (!in_bounds(tile, ntiles, site)) return;
   float hi, lo;
   tc::split_tf32(x, &hi, &lo);
   uint8_t* t = A + (size_t)tile * tc::kATile;
@@ -189,10 +192,11 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
         if (act) {
           const int im = mp >> 7;
           const long long tile = abase_cur + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
-          put_a(P.A, tile, trow, lane, u_lane * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
+          put_a(P.A, tile, P.extent, kbColumnTile, trow, lane, u_lane * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
         }
       } else {
-        if (act) T[(size_t)mp * row + m] = out;
+        if (act && in_bounds((long long)delta_offset_dev(l) + (long long)(mp * row + m), P.extent, kbColumnTable))
+          T[(size_t)mp * row + m] = out;
       }
       if (mp >= m0 + 32) {
         // table: transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}; tiles: A_m[l][m'] =
@@ -205,11 +209,13 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
             const float uc = c <= l ? __ldg(&P.Uf[(size_t)l * (l + 1) / 2 + c]) : 0.f;
             for (int r = 0; r < 32 && m0 + r <= l; ++r) {
               const long long tile = __shfl_sync(0xffffffffu, base_lane, r) + (mp >> 5);
-              if (c <= l) put_a(P.A, tile, trow, lane, uc * f64_to_f32_rn(stage[r * 33 + lane]));
+              if (c <= l) put_a(P.A, tile, P.extent, kbColumnTile, trow, lane, uc * f64_to_f32_rn(stage[r * 33 + lane]));
             }
           } else {
             for (int r = 0; r < 32 && m0 + r <= l; ++r)
-              if (c <= l) T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
+              if (c <= l && in_bounds((long long)delta_offset_dev(l) + (long long)((m0 + r) * row + c), P.extent,
+                                      kbColumnTable))
+                T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
           }
           __syncwarp();
         }
@@ -267,6 +273,7 @@ struct LaneParams {
   uint8_t* A;               // inverse tiles (m, m' / 128, l / 32)
   const long long* ibase;   // [m * nI + i]: index of the tile of chunk kc is ibase + kc
   unsigned int* counter;
+  long long ntiles;         // tiles of A (index checks)
 };
 
 template <bool SCALED>
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
       a_ = 0.0;
       b_ = 0.0;
       u_ = 0.f;
-      if (inl && r <= l) {
+      if (inl && r <= l && in_bounds((long long)tri_idx(r, l, L), (long long)L * (L + 1) / 2, kbLaneTable)) {
         const size_t k = tri_idx(r, l, L);
         a_ = __ldg(&P.a[k]);
         b_ = __ldg(&P.b[k]);
@@ -329,8 +336,8 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
       const bool on = inl && mp <= l;
       if (on && wr) {
         const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
-        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, mp & 127, lane, cu * x);
-        if (mp > m) put_a(P.A, ct + kc, rowm, lane, um * (((mp - m) & 1) ? -x : x));
+        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, P.ntiles, kbLaneTile, mp & 127, lane, cu * x);
+        if (mp > m) put_a(P.A, ct + kc, P.ntiles, kbLaneTile, rowm, lane, um * (((mp - m) & 1) ? -x : x));
       }
       if (on && mp > m) {
         const double c = __dmul_rn(m2, ca);
@@ -461,6 +468,7 @@ static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATi
   P.A = t.A;
   P.abase = t.abase;
   const bool tiles = t.A != nullptr;
+  P.extent = tiles ? t.ntiles : (long long)delta_offset(L);
   if (L > 1024 && tiles)
     column_recursion_kernel<true, true><<<w.blocks, w.threads, w.smem, st>>>(P);
   else if (L > 1024)
@@ -545,6 +553,7 @@ cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, in
   P.A = it.A;
   P.ibase = it.ibase;
   P.counter = w.barrier;
+  P.ntiles = it.ntiles;
   if (L > 1024)
     lane_recursion_kernel<true><<<t.blocks, kColThreads, 0, st>>>(P);
   else
@@ -556,5 +565,7 @@ cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles 
   if (!t.A || !t.abase || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;
   return column_launch(w, L, Uf, t, st);
 }
+
+SSHT_BOUNDS_TU(delta_column)
 
 }  // namespace ssht

@@ -9,6 +9,7 @@
 // (e = sf1 - i sf2 because each of sf1, sf2 has the symmetry).  Field 2p and 2p+1 of the caller
 // pair into complex field p; an odd count pairs the last field with zero.
 #include "ssht_internal.h"
+#include "bounds.cuh"
 
 namespace ssht {
 namespace {
@@ -19,52 +20,52 @@ template <> struct Cx<float> { using type = float2; };
 
 template <typename T>
 __global__ void pack_coeffs_kernel(long long n2, long long npair, int nreal, const typename Cx<T>::type* __restrict__ flm,
-                                   typename Cx<T>::type* __restrict__ rc) {
+                                   typename Cx<T>::type* __restrict__ rc, long long in_n, long long out_n) {
   using C = typename Cx<T>::type;
   const long long total = npair * n2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / n2, e = i - p * n2;
-    const C a = flm[2 * p * n2 + e];
-    C b;
-    b.x = 0;
-    b.y = 0;
-    if (2 * p + 1 < nreal) b = flm[(2 * p + 1) * n2 + e];
+    C a, b;
+    a.x = a.y = b.x = b.y = 0;
+    if (in_bounds(2 * p * n2 + e, in_n, kbRealIn)) a = flm[2 * p * n2 + e];
+    if (2 * p + 1 < nreal && in_bounds((2 * p + 1) * n2 + e, in_n, kbRealIn)) b = flm[(2 * p + 1) * n2 + e];
     C r;
     r.x = a.x - b.y;  // a + i b
     r.y = a.y + b.x;
-    rc[i] = r;
+    if (in_bounds(i, out_n, kbRealOut)) rc[i] = r;
   }
 }
 
 template <typename T>
 __global__ void pack_grid_kernel(long long n2, long long npair, int nreal, const T* __restrict__ f,
-                                 typename Cx<T>::type* __restrict__ rg) {
+                                 typename Cx<T>::type* __restrict__ rg, long long in_n, long long out_n) {
   using C = typename Cx<T>::type;
   const long long total = npair * n2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / n2, e = i - p * n2;
     C r;
-    r.x = f[2 * p * n2 + e];
-    r.y = (2 * p + 1 < nreal) ? f[(2 * p + 1) * n2 + e] : T(0);
-    rg[i] = r;
+    r.x = in_bounds(2 * p * n2 + e, in_n, kbRealIn) ? f[2 * p * n2 + e] : T(0);
+    r.y = (2 * p + 1 < nreal && in_bounds((2 * p + 1) * n2 + e, in_n, kbRealIn)) ? f[(2 * p + 1) * n2 + e] : T(0);
+    if (in_bounds(i, out_n, kbRealOut)) rg[i] = r;
   }
 }
 
 template <typename T>
 __global__ void unpack_grid_kernel(long long n2, long long npair, int nreal, const typename Cx<T>::type* __restrict__ rg,
-                                   T* __restrict__ f) {
+                                   T* __restrict__ f, long long in_n, long long out_n) {
   const long long total = npair * n2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / n2, e = i - p * n2;
+    if (!in_bounds(i, in_n, kbRealIn)) continue;
     const auto z = rg[i];
-    f[2 * p * n2 + e] = z.x;
-    if (2 * p + 1 < nreal) f[(2 * p + 1) * n2 + e] = z.y;
+    if (in_bounds(2 * p * n2 + e, out_n, kbRealOut)) f[2 * p * n2 + e] = z.x;
+    if (2 * p + 1 < nreal && in_bounds((2 * p + 1) * n2 + e, out_n, kbRealOut)) f[(2 * p + 1) * n2 + e] = z.y;
   }
 }
 
 template <typename T>
 __global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const typename Cx<T>::type* __restrict__ rc,
-                                     typename Cx<T>::type* __restrict__ flm) {
+                                     typename Cx<T>::type* __restrict__ flm, long long in_n, long long out_n) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * L;
   const long long total = npair * n2;
@@ -74,8 +75,10 @@ __global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const ty
     while ((long long)l * l > e) --l;
     while ((long long)(l + 1) * (l + 1) <= e) ++l;
     const int m = (int)(e - (long long)l * l - l);
+    const long long di = p * n2 + (long long)l * l + l - m;
+    if (!in_bounds(i, in_n, kbRealIn) || !in_bounds(di, in_n, kbRealIn)) continue;
     const C c = rc[i];
-    const C d = rc[p * n2 + (long long)l * l + l - m];
+    const C d = rc[di];
     const T sg = (m & 1) ? T(-1) : T(1);
     const T ex = sg * d.x, ey = -sg * d.y;  // e = (-1)^m conj(d)
     C a, b;
@@ -83,8 +86,8 @@ __global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const ty
     a.y = T(0.5) * (c.y + ey);
     b.x = T(0.5) * (c.y - ey);  // (c - e) / (2i)
     b.y = -T(0.5) * (c.x - ex);
-    flm[2 * p * n2 + e] = a;
-    if (2 * p + 1 < nreal) flm[(2 * p + 1) * n2 + e] = b;
+    if (in_bounds(2 * p * n2 + e, out_n, kbRealOut)) flm[2 * p * n2 + e] = a;
+    if (2 * p + 1 < nreal && in_bounds((2 * p + 1) * n2 + e, out_n, kbRealOut)) flm[(2 * p + 1) * n2 + e] = b;
   }
 }
 
@@ -96,7 +99,7 @@ __global__ void unpack_coeffs_kernel(int L, long long npair, int nreal, const ty
 // and its inverse needs the spin-s half only (gathered by pair_gather_kernel).
 template <typename T>
 __global__ void pair_expand_kernel(int L, int s, long long B, const typename Cx<T>::type* __restrict__ c,
-                                   typename Cx<T>::type* __restrict__ out) {
+                                   typename Cx<T>::type* __restrict__ out, long long in_n, long long out_n) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * L, total = B * n2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -105,23 +108,25 @@ __global__ void pair_expand_kernel(int L, int s, long long B, const typename Cx<
     while ((long long)l * l > e) --l;
     while ((long long)(l + 1) * (l + 1) <= e) ++l;
     const int m = (int)(e - (long long)l * l - l);
-    const C d = c[b * n2 + (long long)l * l + l - m];
+    const long long di = b * n2 + (long long)l * l + l - m;
+    if (!in_bounds(i, in_n, kbPairIn) || !in_bounds(di, in_n, kbPairIn)) continue;
+    const C d = c[di];
     const T sg = ((s + m) & 1) ? T(-1) : T(1);
     C q;
     q.x = sg * d.x;
     q.y = -sg * d.y;
-    out[2 * b * n2 + e] = c[i];
-    out[(2 * b + 1) * n2 + e] = q;
+    if (in_bounds(2 * b * n2 + e, out_n, kbPairOut)) out[2 * b * n2 + e] = c[i];
+    if (in_bounds((2 * b + 1) * n2 + e, out_n, kbPairOut)) out[(2 * b + 1) * n2 + e] = q;
   }
 }
 
 template <typename T>
 __global__ void pair_gather_kernel(long long n2, long long B, const typename Cx<T>::type* __restrict__ in,
-                                   typename Cx<T>::type* __restrict__ c) {
+                                   typename Cx<T>::type* __restrict__ c, long long in_n, long long out_n) {
   const long long total = B * n2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / n2, e = i - b * n2;
-    c[i] = in[2 * b * n2 + e];
+    if (in_bounds(2 * b * n2 + e, in_n, kbPairIn) && in_bounds(i, out_n, kbPairOut)) c[i] = in[2 * b * n2 + e];
   }
 }
 
@@ -136,7 +141,7 @@ template <typename T>
 cudaError_t real_pack_coeffs(int L, int nreal, const void* flm, void* rc, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * L, np = (nreal + 1) / 2;
-  pack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)flm, (C*)rc);
+  pack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)flm, (C*)rc, nreal * n2, np * n2);
   return cudaGetLastError();
 }
 
@@ -144,7 +149,7 @@ template <typename T>
 cudaError_t real_pack_grid(int L, int nreal, const void* f, void* rg, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * (2 * L - 1), np = (nreal + 1) / 2;
-  pack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const T*)f, (C*)rg);
+  pack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const T*)f, (C*)rg, nreal * n2, np * n2);
   return cudaGetLastError();
 }
 
@@ -152,7 +157,7 @@ template <typename T>
 cudaError_t real_unpack_grid(int L, int nreal, const void* rg, void* f, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * (2 * L - 1), np = (nreal + 1) / 2;
-  unpack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)rg, (T*)f);
+  unpack_grid_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(n2, np, nreal, (const C*)rg, (T*)f, np * n2, nreal * n2);
   return cudaGetLastError();
 }
 
@@ -160,14 +165,14 @@ template <typename T>
 cudaError_t real_unpack_coeffs(int L, int nreal, const void* rc, void* flm, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * L, np = (nreal + 1) / 2;
-  unpack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(L, np, nreal, (const C*)rc, (C*)flm);
+  unpack_coeffs_kernel<T><<<blocks_for(np * n2), 256, 0, st>>>(L, np, nreal, (const C*)rc, (C*)flm, np * n2, nreal * n2);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t pair_expand(int L, int s, int B, const void* c, void* out, cudaStream_t st) {
   using C = typename Cx<T>::type;
-  pair_expand_kernel<T><<<blocks_for((long long)B * L * L), 256, 0, st>>>(L, s, B, (const C*)c, (C*)out);
+  pair_expand_kernel<T><<<blocks_for((long long)B * L * L), 256, 0, st>>>(L, s, B, (const C*)c, (C*)out, (long long)B * L * L, 2LL * B * L * L);
   return cudaGetLastError();
 }
 
@@ -175,7 +180,7 @@ template <typename T>
 cudaError_t pair_gather(int L, int B, const void* in, void* c, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const long long n2 = (long long)L * L;
-  pair_gather_kernel<T><<<blocks_for(B * n2), 256, 0, st>>>(n2, B, (const C*)in, (C*)c);
+  pair_gather_kernel<T><<<blocks_for(B * n2), 256, 0, st>>>(n2, B, (const C*)in, (C*)c, 2LL * B * n2, (long long)B * n2);
   return cudaGetLastError();
 }
 
@@ -205,5 +210,7 @@ cudaError_t real_setup() {
 SSHT_REAL_INST(double)
 SSHT_REAL_INST(float)
 #undef SSHT_REAL_INST
+
+SSHT_BOUNDS_TU(real)
 
 }  // namespace ssht

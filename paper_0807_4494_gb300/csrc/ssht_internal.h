@@ -91,11 +91,12 @@ cudaError_t delta_spin_column(const double* table, int L, int s, double* U, floa
 // the half rows F[b][m + Lp][m'], 0 <= m' < L, without phases (the torus passes' input).
 template <typename T>
 cudaError_t contract_inverse_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* flm, void* E, const double2* ph, int half, cudaStream_t st);
+                                  const void* flm, size_t flm_bytes, void* E, size_t e_bytes, const double2* ph, int half,
+                                  cudaStream_t st);
 // Projection: flm[b][l*l+l+m] = (-1)^s i^{m+s} c_l sum_{m'>=0} Delta_{m'm} Delta_{m',-s} H[b][m+Lp][m']
 template <typename T>
 cudaError_t contract_project_simt(const Dims& d, int s, int B, const double* table, const double* U,
-                                  const void* H, void* flm, cudaStream_t st);
+                                  const void* H, size_t h_bytes, void* flm, size_t flm_bytes, cudaStream_t st);
 
 // The paper's triangular forward (triangular.cu), FP64: Fk = theta-DFT bins of the extended
 // columns [B][N][N] (no phase, no 1/N), flm [B][L*L] double2.
@@ -154,6 +155,7 @@ struct TileOut {
   int NC = 0, nC = 0, mode = 0;
   int Bs = 64;        // fields per slice; slice z of the fields has its tiles at X + z * xslice
   size_t xslice = 0;
+  size_t xbytes = 0;  // the whole tile array (index checks)
 };
 TileOut tc_forward_tiles(const TcPlan* p);
 // Where the recursion can write the A operand itself (3xTF32 plans): the forward tile array and
@@ -161,6 +163,7 @@ TileOut tc_forward_tiles(const TcPlan* p);
 struct ATiles {
   uint8_t* A = nullptr;
   const long long* abase = nullptr;
+  long long ntiles = 0;  // tiles in A (index checks)
 };
 ATiles tc_a_tiles(const TcPlan* p);
 // The column recursion writing the A tiles of a 3xTF32 plan directly (no FP64 table):
@@ -173,6 +176,7 @@ struct InvTiles {
   const long long* ibase = nullptr;
   int nI = 0;
   int nC = 0;
+  long long ntiles = 0;  // tiles in A (index checks)
 };
 InvTiles tc_inverse_tiles(const TcPlan* p);
 // Plan-time tables of the recursion with one lane per degree, which writes the inverse's tiles
@@ -208,8 +212,9 @@ size_t torus_bytes(const TorusPlan* p);
 // which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
 // 3 adjoint phi (f -> X), 4 forward theta with the weight convolution (X -> H), 5 adjoint theta (X -> H).
 // which = 4 with tiles (mode != 0): the data tiles of the forward projection instead of H.
-cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st,
-                       const TileOut* tiles = nullptr);
+// in_bytes / out_bytes: the extents of the buffers (the index checks of bounds-checked builds).
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, size_t in_bytes, void* out,
+                       size_t out_bytes, cudaStream_t st, const TileOut* tiles = nullptr);
 
 // ---------------------------------------------------------------------------
 // Torus kernels (torus.cu)
@@ -242,5 +247,17 @@ cudaError_t adj_theta_fold(const Dims& d, int s, int B, const void* Fk, void* H,
 // complex in the element precision T (double2 or float2).
 template <typename T>
 cudaError_t make_weight_kernel(const Dims& d, void* kappa, cudaStream_t st);
+
+
+// ---------------------------------------------------------------------------
+// Index checks of bounds-checked builds (bounds.cuh): each translation unit's record, copied out
+// and cleared.
+// ---------------------------------------------------------------------------
+struct BoundsRecord;
+cudaError_t bounds_take_torus_pass(BoundsRecord* r);
+cudaError_t bounds_take_contract_tc(BoundsRecord* r);
+cudaError_t bounds_take_delta_column(BoundsRecord* r);
+cudaError_t bounds_take_real(BoundsRecord* r);
+cudaError_t bounds_take_contract_simt(BoundsRecord* r);
 
 }  // namespace ssht

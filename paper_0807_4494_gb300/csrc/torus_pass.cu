@@ -33,6 +33,7 @@
 //   adjoint_theta:  X (one column) -> H[b][m][m'] or the data tiles: theta DFT of the unextended
 //                   rings, fold of m' < 0.
 #include "ssht_internal.h"
+#include "bounds.cuh"
 #include "tc_common.cuh"
 
 #include <cmath>
@@ -252,6 +253,12 @@ struct TorusTables {
   const float2* chirp_c;   // at k = m mod M, |m| < L: e^{-i pi (m^2 + m)/N} / N; 0 for L <= k <= M - L
 };
 
+// Extents of a pass's input and output buffers in float2 elements (the index checks of builds with
+// SSHT_DEBUG).
+struct Ext {
+  long long in, out;
+};
+
 // Bluestein DFT of one row: out_k = sum_n in_n e^{SIGN 2 pi i n k/N}.  in through src(n) (n < N),
 // out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.  PHASE (forward DFTs
 // only): out_k also carries e^{-i pi m/N}, m = k or k - N.  The chirped row's FFT and the inverse
@@ -320,7 +327,7 @@ __device__ __forceinline__ float2* setup_smem(const TorusTables& tb, float2** tw
 // ---------------------------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_kernel(int L, int s, int B, const float2* __restrict__ F,
-                                                                       float2* __restrict__ h, TorusTables tb) {
+                                                                       float2* __restrict__ h, TorusTables tb, Ext ext) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -345,8 +352,9 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
       const int mp = n < L ? n : N - n;  // theta frequency m' (>= 0) of DFT bin n
-      float2 a = F0[mp];
-      const float2 c = two ? F1[mp] : make_float2(0.f, 0.f);
+      const long long i0 = (F0 - F) + mp;
+      float2 a = in_bounds(i0, ext.in, kbInverseThetaIn) ? F0[mp] : make_float2(0.f, 0.f);
+      const float2 c = (two && in_bounds(i0 + L, ext.in, kbInverseThetaIn)) ? F1[mp] : make_float2(0.f, 0.f);
       float2 z = (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);  // F_{m,-m'} = sig F_{m m'}, column m+1: -sig
       return cmul(z, tb.ph[(n < L ? mp : -mp) + N - 1]);           // e^{i pi (+-m')/N}
     };
@@ -360,11 +368,12 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
       float2* hb = h + (size_t)b * L * N;
       for (int t = tid; t < L; t += Geo<M>::T) {
         const float2 z = buf[pidx(t)], zr = buf[pidx(N - 1 - t)];
+        const long long o = (hb - h) + (long long)t * N;
         if (two) {
           const float2 x0 = cscale(cadd(z, cscale(zr, sig)), 0.5f), x1 = cscale(csub(z, cscale(zr, sig)), 0.5f);
-          hb[(size_t)t * N + k0] = cmul(x0, e0);
-          hb[(size_t)t * N + k1] = cmul(x1, e1);
-        } else {
+          if (in_bounds(o + k0, ext.out, kbInverseThetaOut)) hb[(size_t)t * N + k0] = cmul(x0, e0);
+          if (in_bounds(o + k1, ext.out, kbInverseThetaOut)) hb[(size_t)t * N + k1] = cmul(x1, e1);
+        } else if (in_bounds(o + k0, ext.out, kbInverseThetaOut)) {
           hb[(size_t)t * N + k0] = cmul(z, e0);
         }
       }
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
 // ---------------------------------------------------------------------------------------------
 template <int M, int SIGN>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int L, int B, float scale, const float2* __restrict__ in,
-                                                             float2* __restrict__ out, TorusTables tb) {
+                                                             float2* __restrict__ out, TorusTables tb, Ext ext) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -390,11 +399,13 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
     const float2* x = in + (size_t)(active ? u : 0) * N;
     if (u + (long long)gridDim.x * Geo<M>::G < nrows)
       prefetch_l2(in + (size_t)(u + (long long)gridDim.x * Geo<M>::G) * N, (size_t)N * sizeof(float2), tid, Geo<M>::T);
-    auto src = [&](int n) { return active ? x[n] : make_float2(0.f, 0.f); };
+    auto src = [&](int n) {
+      return (active && in_bounds((long long)u * N + n, ext.in, kbPhiIn)) ? x[n] : make_float2(0.f, 0.f);
+    };
     if constexpr (SIGN > 0) {
       float2* y = out + (size_t)(active ? u : 0) * N;
       auto sink = [&](int k, float2 v) {
-        if (active) y[k] = v;
+        if (active && in_bounds((long long)u * N + k, ext.out, kbPhiOut)) y[k] = v;
       };
       bluestein<M, SIGN>(buf, tid, tw, tb, N, src, sink);
     } else {
@@ -403,7 +414,9 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) phi_kernel(int 
       auto sink = [&](int k, float2 v) {
         if (!active) return;
         const int mr = (k <= Lp ? k : k - N) + Lp;  // column m + Lp
-        Xb[(size_t)(mr >> 1) * 2 * L + (mr & 1)] = cscale(v, scale);  // e^{-i pi m/N} in the output chirp
+        const size_t o = (size_t)(mr >> 1) * 2 * L + (mr & 1);
+        if (in_bounds((Xb - out) + (long long)o, ext.out, kbPhiOut))
+          Xb[o] = cscale(v, scale);  // e^{-i pi m/N} in the output chirp
       };
       bluestein<M, SIGN, true>(buf, tid, tw, tb, N, src, sink);
     }
@@ -421,9 +434,12 @@ __device__ __forceinline__ void put_tile(const TileOut& to, int bg, int Bg, int 
   const int sl = bg / to.Bs, b = bg - sl * to.Bs, B = min(to.Bs, Bg - sl * to.Bs);
   const int am = mm < 0 ? -mm : mm, sign = mm < 0 ? 1 : 0;
   const int pb = to.NC * 128, half = to.NC / 2, k = mp & 31;
+  const long long tix = (long long)sl * (long long)(to.xslice / (2 * (size_t)pb)) + (long long)am * to.nC + (mp >> 5);
   uint8_t* tile = to.X + (size_t)sl * to.xslice + ((size_t)am * to.nC + (mp >> 5)) * 2 * pb;
   if (sign && (mp & 1)) v = make_float2(-v.x, -v.y);
+  const bool tile_ok = in_bounds(tix, (long long)(to.xbytes / (2 * (size_t)pb)), kbPutTile);
   auto put = [&](int row, float x) {
+    if (!tile_ok || !in_bounds(row, to.NC, kbPutTile)) return;
     if (to.mode == 2) tc::put_split<true>(tile, pb, row, k, x);
     else tc::put_split<false>(tile, pb, row, k, x);
   };
@@ -446,7 +462,8 @@ __device__ __forceinline__ void put_tile(const TileOut& to, int bg, int Bg, int 
 // ---------------------------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
-                                                                       float2* __restrict__ H, TorusTables tb, TileOut to) {
+                                                                       float2* __restrict__ H, TorusTables tb, TileOut to,
+                                                                       Ext ext) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -470,7 +487,8 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
     auto src = [&](int n) {
       if (!active) return make_float2(0.f, 0.f);
       const int t = n < L ? n : N - 1 - n;
-      const float4 ac = Xp[t];
+      const bool ok = in_bounds(((const float2*)Xp - X) + 2LL * t + 1, ext.in, kbForwardThetaIn);
+      const float4 ac = ok ? Xp[t] : make_float4(0.f, 0.f, 0.f, 0.f);
       float2 a = make_float2(ac.x, ac.y);
       float2 c = two ? make_float2(ac.z, ac.w) : make_float2(0.f, 0.f);
       if (t == Lp) {
@@ -527,8 +545,9 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
           put_tile(to, b, B, m, mp, v0);
           if (two) put_tile(to, b, B, m + 1, mp, v1);
         } else {
-          H0[mp] = v0;
-          if (two) H1[mp] = v1;
+          const long long o = (H0 - H) + mp;
+          if (in_bounds(o, ext.out, kbForwardThetaOut)) H0[mp] = v0;
+          if (two && in_bounds(o + L, ext.out, kbForwardThetaOut)) H1[mp] = v1;
         }
       }
     }
@@ -541,7 +560,8 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
 // ---------------------------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_kernel(int L, int s, int B, const float2* __restrict__ X,
-                                                                       float2* __restrict__ H, TorusTables tb, TileOut to) {
+                                                                       float2* __restrict__ H, TorusTables tb, TileOut to,
+                                                                       Ext ext) {
   float2* tw;
   float2* buf = setup_smem<M>(tb, &tw);
   const int Lp = L - 1, N = 2 * L - 1;
@@ -560,7 +580,10 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
         prefetch_l2(X + ((size_t)(un / N) * (N + 1) + (mrn & ~1)) * L, (size_t)L * sizeof(float4), tid, Geo<M>::T);
       }
     }
-    auto src = [&](int n) { return (active && n < L) ? x[2 * n] : make_float2(0.f, 0.f); };
+    auto src = [&](int n) {
+      return (active && n < L && in_bounds((x - X) + 2LL * n, ext.in, kbAdjointThetaIn)) ? x[2 * n]
+                                                                                         : make_float2(0.f, 0.f);
+    };
     auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };  // H'_{m''} at bin k (phase in the chirp)
     bluestein<M, -1, true>(buf, tid, tw, tb, N, src, sink);
     __syncthreads();
@@ -581,7 +604,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) adjoint_theta_k
         float2* Hr = H + (size_t)u * L;
         for (int mp = tid; mp < L; mp += Geo<M>::T) {
           const float2 a = buf[pidx(mp)];
-          Hr[mp] = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
+          if (in_bounds(u * L + mp, ext.out, kbAdjointThetaOut)) Hr[mp] = mp == 0 ? a : cadd(a, cscale(buf[pidx(N - mp)], sig));
         }
       }
     }
@@ -758,9 +781,10 @@ size_t torus_bytes(const TorusPlan* p) { return p ? p->bytes : 0; }
 
 // which: 0 inverse theta (F -> h), 1 inverse phi (h -> f), 2 forward phi (f -> X, scale 1/N),
 // 3 adjoint phi (f -> X, no scale), 4 forward theta (X -> H), 5 adjoint theta (X -> H).
-cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, void* out, cudaStream_t st,
-                       const TileOut* tiles) {
+cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* in, size_t in_bytes, void* out,
+                       size_t out_bytes, cudaStream_t st, const TileOut* tiles) {
   const int L = p->L, M = p->M;
+  const Ext ext{(long long)(in_bytes / sizeof(float2)), (long long)(out_bytes / sizeof(float2))};
   const TileOut to = ((which == 4 || which == 5) && tiles) ? *tiles : TileOut();
   const long long rows = (which == 1 || which == 2 || which == 3) ? (long long)B * L
                          : (which == 5)                            ? (long long)B * p->N
@@ -773,12 +797,12 @@ cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* 
     const float2* I = (const float2*)in;                                                                     \
     float2* O = (float2*)out;                                                                                \
     switch (which) {                                                                                         \
-      case 0: inverse_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb); break;          \
-      case 1: phi_kernel<MM, 1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;               \
-      case 2: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f / (float)p->N, I, O, p->tb); break; \
-      case 3: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb); break;              \
-      case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to); break;      \
-      case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to); break;      \
+      case 0: inverse_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, ext); break;     \
+      case 1: phi_kernel<MM, 1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb, ext); break;          \
+      case 2: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f / (float)p->N, I, O, p->tb, ext); break; \
+      case 3: phi_kernel<MM, -1><<<blocks, thr, p->smem, st>>>(L, B, 1.f, I, O, p->tb, ext); break;         \
+      case 4: forward_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to, ext); break; \
+      case 5: adjoint_theta_kernel<MM><<<blocks, thr, p->smem, st>>>(L, s, B, I, O, p->tb, to, ext); break; \
       default: return cudaErrorInvalidValue;                                                                 \
     }                                                                                                        \
     return cudaGetLastError();                                                                               \
@@ -788,5 +812,7 @@ cudaError_t torus_pass(const TorusPlan* p, int which, int s, int B, const void* 
 #undef SSHT_TP_LAUNCH
   return cudaErrorInvalidValue;
 }
+
+SSHT_BOUNDS_TU(torus_pass)
 
 }  // namespace ssht

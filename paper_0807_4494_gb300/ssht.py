@@ -11,7 +11,8 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libssht.so")
+# SSHT_LIBRARY names another build of the library (the bounds-checked lib/libssht_debug.so)
+LIB_PATH = os.environ.get("SSHT_LIBRARY") or os.path.join(HERE, "lib", "libssht.so")
 
 FP64, FP32, TF32X3, BF16X6 = 0, 1, 2, 3
 FLAG_REAL = 1
@@ -28,7 +29,7 @@ EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspac
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
            "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_plan_tile_config",
-           "ssht_group_bucket_tile_config", "ssht_last_error", "ssht_version")
+           "ssht_group_bucket_tile_config", "ssht_debug_bounds", "ssht_last_error", "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack", "delta_inverse")
 
 
@@ -86,6 +87,8 @@ def _lib():
             "ssht_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
             "ssht_plan_tile_config": ([vp, ctypes.POINTER(i)], i),
             "ssht_group_bucket_tile_config": ([vp, i, ctypes.POINTER(i)], i),
+            "ssht_debug_bounds": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)], i),
             "ssht_last_error": ([], ctypes.c_char_p),
             "ssht_version": ([], i),
         }
@@ -155,6 +158,15 @@ def ssht_plan_check(h):
 def ssht_debug_fail_allocation(n):
     """Test hook: the n-th device allocation of the library from now on fails (0 disables)."""
     _check(_lib().ssht_debug_fail_allocation(int(n)), "ssht_debug_fail_allocation")
+
+
+def ssht_debug_bounds():
+    """Index checks of the bounds-checked build: (count, site, index, extent) of the kernel
+    accesses found outside their buffers since the last call; raises in release builds."""
+    c, k, x, e = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib().ssht_debug_bounds(ctypes.byref(c), ctypes.byref(k), ctypes.byref(x), ctypes.byref(e)),
+           "ssht_debug_bounds")
+    return c.value, k.value, x.value, e.value
 
 
 def ssht_plan_set_wait_limit(h, ns):

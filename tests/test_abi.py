@@ -57,3 +57,20 @@ def test_null_arguments_are_rejected():
     n = ctypes.c_int()
     assert lib.ssht_plan_profile_trace(None, None, None, None, None, 0, ctypes.byref(n)) == -1
     assert lib.ssht_plan_destroy(None) == 0
+
+
+def test_release_build_checks_no_indices():
+    """ssht_debug_bounds answers SSHT_EUNSUPPORTED in a release build (no device call)."""
+    ssht, lib = _lib()
+    with pytest.raises(ssht.SshtError) as e:
+        ssht.ssht_debug_bounds()
+    assert e.value.code == -5
+
+
+def test_bounds_checked_build_compiles_and_exports_the_same_boundary():
+    """The library compiled with -DSSHT_DEBUG (the index-checked build its GPU test runs) builds
+    here and exports every declared function."""
+    from paper_0807_4494_gb300 import build
+    lib = ctypes.CDLL(build.build(debug=True))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
