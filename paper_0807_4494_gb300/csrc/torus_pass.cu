@@ -74,7 +74,10 @@ __device__ __forceinline__ float2 w16(int k) {
   return make_float2(cs[kk], SIGN < 0 ? -s : s);
 }
 
-template <int R, int SIGN>
+// R-point DFT on registers.  Z (R = 16 only): 1 when inputs 8..15 are zero (the zero-padded half
+// of a Bluestein row), 2 when only outputs 0..7 are wanted (the half of the spectrum a Bluestein
+// row keeps); the work that only touches the absent half is left out.
+template <int R, int SIGN, int Z = 0>
 __device__ __forceinline__ void dft_reg(float2* v) {
   if constexpr (R == 2) {
     const float2 t = v[0];
@@ -87,7 +90,7 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     dft4<SIGN>(a0, a1, a2, a3);
     dft4<SIGN>(b0, b1, b2, b3);
     b1 = cmul(b1, w16<SIGN>(2));
-    b2 = cmul(b2, w16<SIGN>(4));
+    b2 = mul_mi<SIGN>(b2);  // w16(4)
     b3 = cmul(b3, w16<SIGN>(6));
     v[0] = cadd(a0, b0); v[4] = csub(a0, b0);
     v[1] = cadd(a1, b1); v[5] = csub(a1, b1);
@@ -96,14 +99,40 @@ __device__ __forceinline__ void dft_reg(float2* v) {
   } else {
     // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
 #pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    for (int n2 = 0; n2 < 4; ++n2) {
+      if constexpr (Z == 1) {
+        // inputs n1 = 2, 3 are zero
+        const float2 a0 = v[n2], a1 = v[4 + n2], ia1 = mul_mi<SIGN>(a1);
+        v[n2] = cadd(a0, a1);
+        v[4 + n2] = cadd(a0, ia1);
+        v[8 + n2] = csub(a0, a1);
+        v[12 + n2] = csub(a0, ia1);
+      } else {
+        dft4<SIGN>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+      }
+    }
     // now v[4 k1 + n2] holds Y[n2][k1]
 #pragma unroll
     for (int n2 = 1; n2 < 4; ++n2)
 #pragma unroll
-      for (int k1 = 1; k1 < 4; ++k1) v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<SIGN>(n2 * k1));
+      for (int k1 = 1; k1 < 4; ++k1) {
+        if (n2 * k1 == 4) v[4 * k1 + n2] = mul_mi<SIGN>(v[4 * k1 + n2]);
+        else v[4 * k1 + n2] = cmul(v[4 * k1 + n2], w16<SIGN>(n2 * k1));
+      }
 #pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    for (int k1 = 0; k1 < 4; ++k1) {
+      if constexpr (Z == 2) {
+        // outputs k2 = 0, 1 only
+        float2& a0 = v[4 * k1 + 0];
+        float2& a1 = v[4 * k1 + 1];
+        const float2 a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+        const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<SIGN>(csub(a1, a3));
+        a0 = cadd(t0, t2);
+        a1 = cadd(t1, t3);
+      } else {
+        dft4<SIGN>(v[4 * k1 + 0], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+      }
+    }
     // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4x4 block into natural order
     float2 t[16];
 #pragma unroll
@@ -133,11 +162,14 @@ template <int M> struct Plan16 {
 
 // One Stockham pass of radix R and stride NS: inputs through src(i) (first pass) or shared memory,
 // outputs through sink(k, v) (last pass) or shared memory.  twp: this pass's twiddle table.
-template <int M, int R, int NS, int SIGN, bool FROM_SRC, bool TO_SINK, class Src, class Sink>
+// Z = 1 (first pass, read from src): inputs at positions >= M/2 (r >= R/2) are zero and not read;
+// Z = 2 (last pass, written to sink): outputs at positions >= M/2 are not wanted.
+template <int M, int R, int NS, int SIGN, bool FROM_SRC, bool TO_SINK, int Z, class Src, class Sink>
 __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Src& src, Sink& sink) {
   constexpr int T = M / 16;
   constexpr int J = M / R;
   constexpr int PER = J / T;
+  constexpr bool ZIN = FROM_SRC && Z == 1, ZOUT = TO_SINK && Z == 2;
   float2 v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -146,6 +178,12 @@ __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Sr
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       float2 x;
+      if constexpr (ZIN) {
+        if (r >= R / 2) {
+          v[q][r] = make_float2(0.f, 0.f);
+          continue;
+        }
+      }
       if constexpr (FROM_SRC) x = src(j + r * J);
       else x = buf[pidx(j + r * J)];
       if constexpr (NS > 1) {
@@ -157,7 +195,7 @@ __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Sr
       }
       v[q][r] = x;
     }
-    dft_reg<R, SIGN>(v[q]);
+    dft_reg<R, SIGN, ZIN ? 1 : ZOUT ? 2 : 0>(v[q]);
   }
   __syncthreads();
 #pragma unroll
@@ -166,6 +204,9 @@ __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Sr
     const int d = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      if constexpr (ZOUT) {
+        if (r >= R / 2) continue;
+      }
       if constexpr (TO_SINK) sink(d + r * NS, v[q][r]);
       else buf[pidx(d + r * NS)] = v[q][r];
     }
@@ -174,12 +215,13 @@ __device__ __forceinline__ void pass(float2* buf, int tid, const float2* twp, Sr
 }
 
 // Passes [I, IEND) of an FFT of size M and sign SIGN; pass 0 reads src, pass NP - 1 writes sink.
-template <int M, int SIGN, int I, int IEND, class Src, class Sink>
+// Z: 1 when the inputs at positions >= M/2 are zero, 2 when only outputs below M/2 are wanted.
+template <int M, int SIGN, int I, int IEND, int Z = 0, class Src, class Sink>
 __device__ __forceinline__ void run_range(float2* buf, int tid, const float2* tw, Src& src, Sink& sink) {
   if constexpr (I < IEND) {
     using P = Plan16<M>;
-    pass<M, P::radix(I), pow16(I), SIGN, I == 0, I == P::NP - 1>(buf, tid, tw + P::off(I), src, sink);
-    run_range<M, SIGN, I + 1, IEND>(buf, tid, tw, src, sink);
+    pass<M, P::radix(I), pow16(I), SIGN, I == 0, I == P::NP - 1, Z>(buf, tid, tw + P::off(I), src, sink);
+    run_range<M, SIGN, I + 1, IEND, Z>(buf, tid, tw, src, sink);
   }
 }
 
@@ -284,10 +326,11 @@ __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw
   };
   NoSrc none_in;
   NoSink none_out;
+  // the chirped row is zero from N <= M/2 on, and only outputs below N are kept
   constexpr int NP = Plan16<M>::NP;
-  run_range<M, -1, 0, NP - 1>(buf, tid, tw, in, none_out);
+  run_range<M, -1, 0, NP - 1, 1>(buf, tid, tw, in, none_out);
   boundary<M, -1, 1>(buf, tid, tw, mid);
-  run_range<M, 1, 1, NP>(buf, tid, tw, none_in, out);
+  run_range<M, 1, 1, NP, 2>(buf, tid, tw, none_in, out);
 }
 
 // Ask L2 for [p, p + bytes), one 128-byte line a thread of the row group (T threads): the input of
@@ -514,7 +557,7 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) forward_theta_k
       NoSrc none_in;
       NoSink none_out;
       constexpr int NP = Plan16<M>::NP;
-      run_range<M, -1, 0, NP - 1>(buf, tid, tw, in, none_out);
+      run_range<M, -1, 0, NP - 1, 1>(buf, tid, tw, in, none_out);
       boundary<M, -1, 1>(buf, tid, tw, kmul);
       run_range<M, 1, 1, NP - 1>(buf, tid, tw, none_in, none_out);
       boundary<M, 1, -1>(buf, tid, tw, fmul);
