@@ -311,11 +311,14 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
         return e
 
     tc = prec in ("tf32x3", "bf16x6")
+    # bytes of one real operand value in the contraction's tiles in global memory: 3xTF32 tiles
+    # hold the FP32 value (split into hi + lo in shared memory), split-BF16 tiles the two parts
+    tv = 4.0 if prec == "tf32x3" else 8.0
     for key, v in times.items():
         ms = v["ms"]
         if key == "recursion_inverse" and tc and recursion != "risbo" and prec == "tf32x3":
             u = lane_updates(L)
-            res[key] = entry("lane_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * 8.0,
+            res[key] = entry("lane_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * tv,
                              {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
                               "work": "%.3g updates x 3 FP64 instructions (4 flops); writes the inverse's A tiles" % u,
                               "fp64_probe_tflops": FP64_PROBE_TFLOPS})
@@ -326,18 +329,18 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
                                  {"fp64_instr_frac": ((4.0 * nh + 5.0 * ni) / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0)})
             else:
                 u = column_updates(L)
-                res[key] = entry("column_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * 8.0,
+                res[key] = entry("column_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * (tv if tc else 8.0),
                                  {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
                                   "work": "%.3g updates x 3 FP64 instructions (4 flops); writes %s" % (
-                                      u, "the A tiles (8 B an entry)" if tc else "the FP64 table"),
+                                      u, "the A tiles (%d B an entry)" % tv if tc else "the FP64 table"),
                                   "fp64_probe_tflops": FP64_PROBE_TFLOPS})
         elif key in ("contraction_inverse", "contraction_forward") and tc:
             nprod, pkey = (3, "tf32_tflops") if prec == "tf32x3" else (6, "bf16_tflops_sustained")
             fwd = key.endswith("forward")
-            data = B * (N * L if fwd else L * L) * 16.0
+            data = B * (N * L if fwd else L * L) * 2.0 * tv
             outb = B * (L * L if fwd else N * L) * 8.0
             res[key] = entry("tc_gemm_kernel<%s>" % ("forward" if fwd else "inverse"), ms, nprod * 4.0 * macs,
-                             pk[pkey], None, quad * 8.0 + data + outb,
+                             pk[pkey], None, quad * tv + data + outb,
                              {"useful_tflops": 4.0 * macs / (ms / 1e3) / 1e12, "issued_products": nprod})
         elif key in ("contraction_inverse", "contraction_forward"):
             fwd = key.endswith("forward")
@@ -345,11 +348,11 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
             res[key] = entry(("project_kernel" if fwd else "inverse_kernel") + " (SIMT)", ms, 4.0 * macs, pk[pkey], None,
                              quad * 8.0 + B * (L * L + N * L) * (16.0 if prec == "fp64" else 8.0))
         elif key == "pack_data":
-            res[key] = entry("pack_v_kernel", ms, None, None, None, B * L * L * 24.0)
+            res[key] = entry("pack_v_kernel", ms, None, None, None, B * L * L * (8.0 + 2.0 * tv))
         elif key in ("theta_inverse", "phi_inverse", "phi_forward", "theta_forward") and prec != "fp64":
             rows = B * L
             nfft = 4 if key == "theta_forward" else 2
-            outb = B * L * (N + 1) * (16.0 if (key == "theta_forward" and tc) else 8.0)
+            outb = B * L * (N + 1) * (2.0 * tv if (key == "theta_forward" and tc) else 8.0)
             kern = {"theta_inverse": "inverse_theta_kernel", "phi_inverse": "phi_kernel<+1>",
                     "phi_forward": "phi_kernel<-1>", "theta_forward": "forward_theta_kernel"}[key]
             res[key] = entry(kern, ms, rows * nfft * fft_flops(M), pk["fp32_tflops"], None, B * L * N * 8.0 + outb,

@@ -127,9 +127,10 @@ __global__ void __launch_bounds__(256) pack_a_kernel(int L, int s, const Item* _
   }
   __syncthreads();
   if (!in_bounds(it.atile + blockIdx.x, a_tiles, kbPackAOut)) return;
-  uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * A_TILE);
+  constexpr int GA = kParts<BF> * A_PART;  // bytes of a tile in global memory
+  uint4* dst = (uint4*)(A + (size_t)(it.atile + blockIdx.x) * GA);
   const uint4* src = (const uint4*)tile;
-  for (int e = threadIdx.x; e < A_TILE / 16; e += blockDim.x) dst[e] = src[e];
+  for (int e = threadIdx.x; e < GA / 16; e += blockDim.x) dst[e] = src[e];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
   __shared__ float2 sv[32][33];
   const int B = min(Bs, Btot - (int)blockIdx.z * Bs);
   const long long flm_n = (long long)Btot * L * L, flm0 = (long long)blockIdx.z * Bs * L * L;
-  const long long x_tiles = (long long)(xslice / (2 * (size_t)NC * 128));
+  const long long x_tiles = (long long)(xslice / (kParts<BF> * (size_t)NC * 128));
   flm += (size_t)blockIdx.z * Bs * L * L;
   X += (size_t)blockIdx.z * xslice;
   const int c = blockIdx.x, m0 = 16 * blockIdx.y;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
       if (m >= L || c < xc0[m]) continue;  // tile (m, c) is not stored
       if (!in_bounds(xoff[m] + (c - xc0[m]), x_tiles, kbPackVOut) || !in_bounds(sign * half + 2 * b + 1, NC, kbPackVOut))
         continue;
-      uint8_t* tile = X + (size_t)(xoff[m] + (c - xc0[m])) * 2 * part_bytes;
+      uint8_t* tile = X + (size_t)(xoff[m] + (c - xc0[m])) * kParts<BF> * part_bytes;
       const float2 v = b < B ? sv[lane][cb] : make_float2(0.f, 0.f);
       const int j = sign * half + 2 * b;
       put_split<BF>(tile, part_bytes, j, lane, v.x);
@@ -212,9 +213,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int b_part = a.NC * 128;
-  const int stage_bytes = A_TILE + 2 * b_part;
+  const int stage_bytes = A_TILE + 2 * b_part;  // both split parts of A and of the data tile
+  constexpr int GA = kParts<BF> * A_PART;       // bytes of an A tile in global memory
+  const int gx = kParts<BF> * b_part;           // bytes of a data tile in global memory
   const int STAGES = a.stages;
-  __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], seg_full[2], seg_empty[2], done_bar;
+  // full: a stage's copies have landed; ready (3xTF32): its FP32 values are split into hi + lo
+  __shared__ __align__(8) uint64_t full[MAX_STAGES], ready[MAX_STAGES], empty[MAX_STAGES], seg_full[2], seg_empty[2],
+      done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
+      mbar_init(&ready[s], EPI_WARPS);
       mbar_init(&empty[s], 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       int last_use[MAX_STAGES] = {-1, -1, -1, -1};
       for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1] && !*abort; ++w) {
         const Item itm = a.items[w];
-        const uint8_t* Ab = a.A + (size_t)itm.atile * A_TILE;
+        const uint8_t* Ab = a.A + (size_t)itm.atile * GA;
         for (int c = itm.c0; c < itm.c1; ++c, ++it) {
           const int s = it % STAGES, u = it / STAGES;
           if (!mbar_wait(&empty[s], (u & 1) ^ 1, abort, a.wait_ns)) {
@@ -254,15 +260,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
             break;
           }
           uint8_t* st = smem + s * stage_bytes;
-          mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+          mbar_expect_tx(&full[s], (uint32_t)(GA + gx));
           // a tile index outside its array is recorded and tile 0 copied instead (the pipeline
           // still completes; the result is wrong and the record says why)
           const long long at = itm.atile + (c - itm.c0);
-          const uint8_t* asrc = in_bounds(at, a.a_tiles, kbGemmA) ? Ab + (size_t)(c - itm.c0) * A_TILE : a.A;
-          bulk_g2s(st, asrc, A_TILE, &full[s]);
+          const uint8_t* asrc = in_bounds(at, a.a_tiles, kbGemmA) ? Ab + (size_t)(c - itm.c0) * GA : a.A;
+          bulk_g2s(st, asrc, GA, &full[s]);
           long long xt = FWD ? (long long)itm.m * nC + c : a.xoff[itm.m] + (c - a.xc0[itm.m]);
           if (!in_bounds(xt, a.x_tiles, kbGemmX)) xt = 0;
-          bulk_g2s(st + A_TILE, a.X + (size_t)xt * 2 * b_part, (uint32_t)(2 * b_part), &full[s]);
+          bulk_g2s(st + A_TILE, a.X + (size_t)xt * gx, (uint32_t)gx, &full[s]);
           last_use[s] = u;
         }
       }
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
           const int s = it % STAGES, u = it / STAGES;
           const int seg = it & 1, us = it >> 1;
           if (!mbar_wait(&seg_empty[seg], (us & 1) ^ 1, abort, a.wait_ns) ||
-              !mbar_wait(&full[s], u & 1, abort, a.wait_ns)) {
+              !mbar_wait(BF ? &full[s] : &ready[s], u & 1, abort, a.wait_ns)) {
             *abort = 1;
             ok = false;
             break;
@@ -331,6 +337,25 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
     const int L = a.L, Lp = L - 1, NT = 2 * L - 1, B = a.B, s = a.s;
     const int H = a.NC / 2;
     const uint32_t tq = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * H);
+    // 3xTF32: the epilogue warps also split each arrived stage's FP32 values into hi + lo, one
+    // chunk ahead of the chunk they sum, so that the split of chunk c + 1 overlaps the MMAs of c
+    int nchunks = 0, conv = 0;
+    if constexpr (!BF)
+      for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1]; ++w) nchunks += a.items[w].c1 - a.items[w].c0;
+    const int et = threadIdx.x - 64, ent = 32 * EPI_WARPS;
+    auto convert_upto = [&](int last) -> bool {
+      for (; conv < nchunks && conv <= last; ++conv) {
+        const int sc = conv % STAGES, uc = conv / STAGES;
+        if (!mbar_wait(&full[sc], uc & 1, abort, a.wait_ns)) return false;
+        uint8_t* st = smem + sc * stage_bytes;
+        split_region_tf32(st, A_PART, A_PART, et, ent);
+        split_region_tf32(st + A_TILE, b_part, b_part, et, ent);
+        fence_proxy_async();  // the split parts are read by the tensor core (async proxy)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[sc]);
+      }
+      return true;
+    };
     int it = 0;
     for (int w = a.sched[blockIdx.x]; w < a.sched[blockIdx.x + 1] && !*abort; ++w) {
       const Item itm = a.items[w];
@@ -340,6 +365,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(TcArgs a) {
       bool ok = true;
       for (int c = itm.c0; c < itm.c1; ++c, ++it) {
         const int seg = it & 1, us = it >> 1;
+        if constexpr (!BF) {
+          if (!convert_upto(it + 1)) {
+            *abort = 1;
+            ok = false;
+            break;
+          }
+        }
         if (!mbar_wait(&seg_full[seg], us & 1, abort, a.wait_ns)) {
           *abort = 1;
           ok = false;
@@ -478,7 +510,7 @@ cudaError_t tc_configure(TcPlan* p, const TcConfig& c) {
   if (!tc_config_fits(p, c)) return cudaErrorInvalidValue;
   cudaError_t e;
   const int Bs = std::min(c.slice, p->B), nS = (p->B + Bs - 1) / Bs, NC = nc_of(Bs);
-  const size_t xslice = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * 2 * NC * 128;
+  const size_t xslice = (size_t)std::max(p->xtiles_inv, p->xtiles_fwd) * (p->bf16 ? 2 : 1) * NC * 128;
   if (xslice * nS != p->xbytes || !p->X) {
     if (p->X) {
       cudaFree(p->X);
@@ -520,6 +552,7 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   *out = nullptr;
   if (B < 1) return cudaErrorInvalidValue;
   TcPlan* p = new TcPlan();
+  size_t ga = 0;
   p->bf16 = bf16 != 0;
   p->L = L;
   p->s = s;
@@ -574,12 +607,13 @@ cudaError_t tc_setup(TcPlan** out, int L, int s, int B, int bf16, int device) {
   if ((e = tc_alloc((void**)&p->items_fwd, fwd.size() * sizeof(Item), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->sched_inv, (p->grid_inv + 1) * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->sched_fwd, (p->grid_fwd + 1) * sizeof(int), &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = tc_alloc((void**)&p->A, (size_t)ft * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
+  ga = (size_t)(p->bf16 ? 2 : 1) * A_PART;  // bytes of an A tile in global memory
+  if ((e = tc_alloc((void**)&p->A, (size_t)ft * ga, &p->bytes)) != cudaSuccess) goto fail;
   // zero once (entries no call writes stay zero); cudaMemset is asynchronous on the legacy
   // stream, and the plans' packing and recursions run on non-blocking streams: wait for it
-  if ((e = cudaMemset(p->A, 0, (size_t)ft * A_TILE)) != cudaSuccess) goto fail;
-  if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * A_TILE, &p->bytes)) != cudaSuccess) goto fail;
-  if ((e = cudaMemset(p->A_inv, 0, (size_t)at * A_TILE)) != cudaSuccess) goto fail;
+  if ((e = cudaMemset(p->A, 0, (size_t)ft * ga)) != cudaSuccess) goto fail;
+  if ((e = tc_alloc((void**)&p->A_inv, (size_t)at * ga, &p->bytes)) != cudaSuccess) goto fail;
+  if ((e = cudaMemset(p->A_inv, 0, (size_t)at * ga)) != cudaSuccess) goto fail;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) goto fail;
   if ((e = tc_alloc((void**)&p->ibase, ibase.size() * sizeof(long long), &p->bytes)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpy(p->ibase, ibase.data(), ibase.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -707,7 +741,7 @@ cudaError_t tc_gemm(TcPlan* p, int forward, void* out, const void* ph, int* stat
     a.status = status;
     a.wait_ns = wait_ns;
     a.a_tiles = forward ? p->tiles_A : p->tiles_inv;
-    a.x_tiles = (long long)(p->xslice / (2 * (size_t)p->NC * 128));
+    a.x_tiles = (long long)(p->xslice / ((p->bf16 ? 2 : 1) * (size_t)p->NC * 128));
     a.out_n = (long long)a.B * (long long)per_field;
     const int grid = forward ? p->grid_fwd : p->grid_inv;
     if (forward && p->bf16)

@@ -63,14 +63,12 @@ struct ColumnParams {
   long long extent;        // entries of the table, or tiles of A (index checks)
 };
 
-// Writes A_M[l][K] = x (already in FP32) split hi + lo into row l mod 128 of tile (M, l / 128, K / 32).
+// Writes A_M[l][K] = x (FP32) into row l mod 128 of tile (M, l / 128, K / 32): the 3xTF32 tiles
+// hold one FP32 part in global memory (the contraction splits it into hi + lo on arrival).
 __device__ __forceinline__ void put_a(uint8_t* A, long long tile, long long ntiles, int site, int row, int k, float x) {
   if (!in_bounds(tile, ntiles, site)) return;
-  float hi, lo;
-  tc::split_tf32(x, &hi, &lo);
-  uint8_t* t = A + (size_t)tile * tc::kATile;
-  *(float*)(t + tc::sw128(row, 4 * k)) = hi;
-  *(float*)(t + tc::kAPart + tc::sw128(row, 4 * k)) = lo;
+  uint8_t* t = A + (size_t)tile * tc::kAPart;
+  *(float*)(t + tc::sw128(row, 4 * k)) = x;
 }
 
 __device__ __forceinline__ double flip_sign(double v, bool neg) {

@@ -11,7 +11,9 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// A-operand tiles of the contraction: 128 rows x 32 K values, two split parts of 16 KB each.
+// A-operand tiles of the contraction: 128 rows x 32 K values.  In shared memory two split parts of
+// 16 KB each; in global memory one part of FP32 values for the 3xTF32 form (the contraction splits
+// them on arrival) and both parts for the split-BF16 form.
 constexpr int kTileRows = 128, kTileK = 32;
 constexpr int kAPart = kTileRows * kTileK * 4;
 constexpr int kATile = 2 * kAPart;
@@ -44,6 +46,10 @@ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
 __device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+
+// Orders this thread's shared-memory writes (generic proxy) before later reads of the tensor core
+// (async proxy).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -161,9 +167,10 @@ __device__ __forceinline__ void split_bf16x3(float x, uint16_t* h, uint16_t* m, 
   *l = __bfloat16_as_ushort(c);
 }
 
-// Writes element (row, k), k < 32, of a K-chunk operand tile made of two parts of part_bytes each
-// (128-byte swizzled rows).  TF32 split: part 0 = hi (4-byte elements), part 1 = lo.  BF16 split:
-// part 0 = [h | m] (2-byte elements, k at byte 2k and 64 + 2k), part 1 = [l | 0].
+// Writes element (row, k), k < 32, of a K-chunk operand tile as it is stored in global memory
+// (128-byte swizzled rows).  TF32 form: one part, the FP32 value itself (split into hi + lo by
+// the contraction when the tile arrives in shared memory).  BF16 split: part 0 = [h | m] (2-byte
+// elements, k at byte 2k and 64 + 2k), part 1 = [l | 0], each part part_bytes long.
 template <bool BF>
 __device__ __forceinline__ void put_split(uint8_t* tile, int part_bytes, int row, int k, float x) {
   if constexpr (BF) {
@@ -174,10 +181,26 @@ __device__ __forceinline__ void put_split(uint8_t* tile, int part_bytes, int row
     *(uint16_t*)(tile + part_bytes + sw128(row, 2 * k)) = l;
     *(uint16_t*)(tile + part_bytes + sw128(row, 64 + 2 * k)) = 0;
   } else {
-    float hi, lo;
-    split_tf32(x, &hi, &lo);
-    *(float*)(tile + sw128(row, 4 * k)) = hi;
-    *(float*)(tile + part_bytes + sw128(row, 4 * k)) = lo;
+    (void)part_bytes;
+    *(float*)(tile + sw128(row, 4 * k)) = x;
+  }
+}
+
+// Global parts of an operand tile: 1 for the TF32 form, 2 for split-BF16.
+template <bool BF> constexpr int kParts = BF ? 2 : 1;
+
+// Splits, in shared memory, the FP32 values of an arrived 3xTF32 operand region into hi (in place)
+// and lo (lo_offset bytes further on), 16 bytes a step; the layout's swizzle permutes whole
+// 16-byte chunks, so the split goes position by position.  Threads t of nt take steps t, t + nt, ...
+__device__ __forceinline__ void split_region_tf32(uint8_t* region, int bytes, int lo_offset, int t, int nt) {
+  for (int o = 16 * t; o < bytes; o += 16 * nt) {
+    float4 x = *(const float4*)(region + o), h, l;
+    split_tf32(x.x, &h.x, &l.x);
+    split_tf32(x.y, &h.y, &l.y);
+    split_tf32(x.z, &h.z, &l.z);
+    split_tf32(x.w, &h.w, &l.w);
+    *(float4*)(region + o) = h;
+    *(float4*)(region + lo_offset + o) = l;
   }
 }
 

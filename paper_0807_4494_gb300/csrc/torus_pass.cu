@@ -476,11 +476,13 @@ __device__ __forceinline__ void put_tile(const TileOut& to, int bg, int Bg, int 
   // field bg of Bg lies in slice bg / Bs, as field b of its B fields
   const int sl = bg / to.Bs, b = bg - sl * to.Bs, B = min(to.Bs, Bg - sl * to.Bs);
   const int am = mm < 0 ? -mm : mm, sign = mm < 0 ? 1 : 0;
-  const int pb = to.NC * 128, half = to.NC / 2, k = mp & 31;
-  const long long tix = (long long)sl * (long long)(to.xslice / (2 * (size_t)pb)) + (long long)am * to.nC + (mp >> 5);
-  uint8_t* tile = to.X + (size_t)sl * to.xslice + ((size_t)am * to.nC + (mp >> 5)) * 2 * pb;
+  // a tile is one part (3xTF32: FP32 values) or two (split-BF16) of pb bytes in global memory
+  const int pb = to.NC * 128, half = to.NC / 2, k = mp & 31, parts = to.mode == 2 ? 2 : 1;
+  const size_t tb = (size_t)parts * pb;
+  const long long tix = (long long)sl * (long long)(to.xslice / tb) + (long long)am * to.nC + (mp >> 5);
+  uint8_t* tile = to.X + (size_t)sl * to.xslice + ((size_t)am * to.nC + (mp >> 5)) * tb;
   if (sign && (mp & 1)) v = make_float2(-v.x, -v.y);
-  const bool tile_ok = in_bounds(tix, (long long)(to.xbytes / (2 * (size_t)pb)), kbPutTile);
+  const bool tile_ok = in_bounds(tix, (long long)(to.xbytes / tb), kbPutTile);
   auto put = [&](int row, float x) {
     if (!tile_ok || !in_bounds(row, to.NC, kbPutTile)) return;
     if (to.mode == 2) tc::put_split<true>(tile, pb, row, k, x);
