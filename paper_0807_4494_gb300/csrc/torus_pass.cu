@@ -303,16 +303,19 @@ struct Ext {
 
 // Bluestein DFT of one row: out_k = sum_n in_n e^{SIGN 2 pi i n k/N}.  in through src(n) (n < N),
 // out through sink(k, v) (k < N).  buf: M (+pad) values; ends with buf free.  PHASE (forward DFTs
-// only): out_k also carries e^{-i pi m/N}, m = k or k - N.  The chirped row's FFT and the inverse
-// FFT of its product with the kernel's spectrum meet in one fused pass.
-template <int M, int SIGN, bool PHASE = false, class Src, class Sink>
+// only): out_k also carries e^{-i pi m/N}, m = k or k - N.  IN_PHASE (inverse DFTs only): in_n
+// is src(n) e^{i pi m/N}, m = n or n - N (one table, the conjugate of the forward's combined
+// output chirp).  The chirped row's FFT and the inverse FFT of its product with the kernel's
+// spectrum meet in one fused pass.
+template <int M, int SIGN, bool PHASE = false, bool IN_PHASE = false, class Src, class Sink>
 __device__ __forceinline__ void bluestein(float2* buf, int tid, const float2* tw, const TorusTables& tb, int N, Src src,
                                           Sink sink) {
   static_assert(!PHASE || SIGN < 0, "the combined output table is the forward chirp's");
+  static_assert(!IN_PHASE || SIGN > 0, "the combined input table is the inverse chirp's");
   const float2* khat = SIGN < 0 ? tb.khat_f : tb.khat_i;
   auto in = [&](int n) {
     if (n >= N) return make_float2(0.f, 0.f);
-    float2 c = __ldg(&tb.chirp[n]);
+    float2 c = __ldg(IN_PHASE ? &tb.chirp_ph[n] : &tb.chirp[n]);
     if (SIGN > 0) c = conjf2(c);
     return cmul(src(n), c);
   };
@@ -398,11 +401,12 @@ __global__ void __launch_bounds__(Geo<M>::THREADS, Geo<M>::MINB) inverse_theta_k
       const long long i0 = (F0 - F) + mp;
       float2 a = in_bounds(i0, ext.in, kbInverseThetaIn) ? F0[mp] : make_float2(0.f, 0.f);
       const float2 c = (two && in_bounds(i0 + L, ext.in, kbInverseThetaIn)) ? F1[mp] : make_float2(0.f, 0.f);
-      float2 z = (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);  // F_{m,-m'} = sig F_{m m'}, column m+1: -sig
-      return cmul(z, tb.ph[(n < L ? mp : -mp) + N - 1]);           // e^{i pi (+-m')/N}
+      // F_{m,-m'} = sig F_{m m'}, column m+1: -sig; the phase e^{i pi (+-m')/N} rides on the
+      // input chirp
+      return (n < L) ? cadd(a, c) : cscale(csub(a, c), sig);
     };
     auto sink = [&](int k, float2 v) { buf[pidx(k)] = v; };
-    bluestein<M, 1>(buf, tid, tw, tb, N, src, sink);
+    bluestein<M, 1, false, true>(buf, tid, tw, tb, N, src, sink);
     __syncthreads();
     if (active) {
       // separate the two columns and write h[b][t][m mod N] with the phi phase e^{i pi m/N}
