@@ -270,6 +270,12 @@ SSHT_API int ssht_group_check(ssht_group_t group);
  * SSHT_ENOMEM after releasing what they had allocated.  n < 0 returns SSHT_EINVAL. */
 SSHT_API int ssht_debug_fail_allocation(int n);
 
+/* Test hook (the paper has no counterpart): the spin limit, in nanoseconds, of the waits of the
+ * recursion that ssht_wigner_delta_noalloc launches from now on (it takes no plan, so
+ * ssht_plan_set_wait_limit cannot reach it); 0 restores the default of one second.  A wait that
+ * runs out makes the call's table start with a NaN (out[0]).  ns < 0 returns SSHT_EINVAL. */
+SSHT_API int ssht_debug_noalloc_wait_limit(long long ns);
+
 /* Index checks of the bounds-checked build (the paper has no counterpart; the library compiled
  * with -DSSHT_DEBUG, `python -m paper_0807_4494_gb300.build --debug`): in that build every checked
  * global access of the kernels (torus passes, packing, tensor-core contraction, recursions writing

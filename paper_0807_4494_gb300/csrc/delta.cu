@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -784,6 +785,7 @@ __global__ void noalloc_finish_kernel(const int* status, double* out) {
 }
 
 std::mutex g_noalloc_mutex;
+std::atomic<long long> g_noalloc_limit_ns{0};  // test hook: the entry point's spin limit (0: the default)
 
 struct NoAllocDevice {
   double* base = nullptr;  // device address of g_noalloc_scratch on this device
@@ -861,12 +863,20 @@ extern "C" int ssht_wigner_delta_noalloc(int L, double* out, void* stream) {
   P.counter = words;
   P.status = (int*)(words + 2);
   P.part = nullptr;  // no table: the kernel computes each step's partition
-  P.limit_ns = kDefaultWaitNs;
+  const long long lim = g_noalloc_limit_ns.load();
+  P.limit_ns = lim > 0 ? lim : kDefaultWaitNs;
   long long cap = (long long)((smem - sq_smem_bytes(L)) / sizeof(double));  // the chunk area, then the sqrt table
   void* args[] = {&P, &cap};
   if (cudaLaunchCooperativeKernel((void*)risbo_kernel, dim3(sms), dim3(kThreads), args, smem, st) != cudaSuccess)
     return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: recursion launch failed");
   noalloc_finish_kernel<<<1, 32, 0, st>>>(P.status, out);
   if (cudaGetLastError() != cudaSuccess) return set_last_error(SSHT_ECUDA, "ssht_wigner_delta_noalloc: launch failed");
+  return SSHT_OK;
+}
+
+extern "C" int ssht_debug_noalloc_wait_limit(long long ns) {
+  using namespace ssht;
+  if (ns < 0) return set_last_error(SSHT_EINVAL, "ssht_debug_noalloc_wait_limit: ns must be >= 0");
+  g_noalloc_limit_ns.store(ns);
   return SSHT_OK;
 }

@@ -29,7 +29,8 @@ EXPORTS = ("ssht_plan", "ssht_plan_ex", "ssht_plan_destroy", "ssht_plan_workspac
            "ssht_group_layout", "ssht_group_buckets", "ssht_group_inverse", "ssht_group_forward",
            "ssht_group_adjoint", "ssht_group_capture", "ssht_group_replay", "ssht_group_check",
            "ssht_debug_fail_allocation", "ssht_plan_set_wait_limit", "ssht_plan_tile_config",
-           "ssht_group_bucket_tile_config", "ssht_debug_bounds", "ssht_last_error", "ssht_version")
+           "ssht_group_bucket_tile_config", "ssht_debug_bounds", "ssht_debug_noalloc_wait_limit", "ssht_last_error",
+           "ssht_version")
 STAGES = ("delta", "inverse", "project", "fft", "torus", "pack", "delta_inverse")
 
 
@@ -84,6 +85,7 @@ def _lib():
             "ssht_group_replay": ([vp, vp], i),
             "ssht_group_check": ([vp], i),
             "ssht_debug_fail_allocation": ([i], i),
+            "ssht_debug_noalloc_wait_limit": ([ctypes.c_longlong], i),
             "ssht_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
             "ssht_plan_tile_config": ([vp, ctypes.POINTER(i)], i),
             "ssht_group_bucket_tile_config": ([vp, i, ctypes.POINTER(i)], i),
@@ -158,6 +160,11 @@ def ssht_plan_check(h):
 def ssht_debug_fail_allocation(n):
     """Test hook: the n-th device allocation of the library from now on fails (0 disables)."""
     _check(_lib().ssht_debug_fail_allocation(int(n)), "ssht_debug_fail_allocation")
+
+
+def ssht_debug_noalloc_wait_limit(ns):
+    """Test hook: the spin limit of ssht_wigner_delta_noalloc's waits (0 restores the default)."""
+    _check(_lib().ssht_debug_noalloc_wait_limit(int(ns)), "ssht_debug_noalloc_wait_limit")
 
 
 def ssht_debug_bounds():

@@ -70,3 +70,23 @@ def test_noalloc_rejects_band_limits_beyond_its_scratch():
         assert rc == -1
         assert "512" in ssht.ssht_last_error() or L == 0
     assert lib.ssht_wigner_delta_noalloc(16, None, None) == -1
+
+
+def test_noalloc_timeout_marks_the_table_and_the_next_call_recovers():
+    """A wait of the recursion that runs out (a 1 ns limit: the first hand-off between CTAs gives
+    up) makes the kernel leave and the call's table start with a NaN; the device stays usable and
+    the next call, with the default limit, is right again."""
+    ssht, _ = _lib()
+    L = 64
+    ssht.ssht_debug_noalloc_wait_limit(1)
+    try:
+        bad = _noalloc(L)
+        torch.cuda.synchronize()
+    finally:
+        ssht.ssht_debug_noalloc_wait_limit(0)
+    assert torch.isnan(bad[0])
+    good = _noalloc(L)
+    torch.cuda.synchronize()
+    ref = _with_plan(L)
+    assert not torch.isnan(good).any()
+    assert float((good - ref).abs().max()) < TOL
