@@ -493,7 +493,47 @@ def run_ssht(args):
         el = max_over_ranks(time.perf_counter() - t0, world, device)
         nbytes = B * L * L * h_in.element_size()
         e2e = {"value": world * B * nrep / el, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": nrep}
+               "d2h_bytes_per_step": nbytes, "steps": nrep,
+               "how": "one stream: each step the inverse reads the pinned host coefficients, the forward returns "
+                      "its result to pinned host memory and the call waits for it"}
+        # Two request streams in flight, the pattern of a server: each with its own plan, CUDA stream,
+        # pinned buffers and host thread, through the same calls; every step of each still copies its
+        # input in and its result out inside the timed region, and one stream's copies overlap the
+        # other's kernels.
+        import threading
+        plan2 = ssht.Plan(L, s, B, precision=prec, delta_mode=args.delta_mode)
+        grid2 = torch.empty(plan2.grid_shape(), dtype=cdt, device=device)
+        h_in2 = torch.empty(plan2.coeff_shape(), dtype=cdt, pin_memory=True)
+        h_in2.copy_(h_in)
+        h_out2 = torch.empty(plan2.coeff_shape(), dtype=cdt, pin_memory=True)
+        streams = [torch.cuda.Stream(device=device), torch.cuda.Stream(device=device)]
+        work = [(plan, grid, h_in, h_out), (plan2, grid2, h_in2, h_out2)]
+
+        def run(k, n):
+            p_, g_, i_, o_ = work[k]
+            with torch.cuda.stream(streams[k]):
+                for _ in range(n):
+                    p_.inverse(i_, out=g_)
+                    p_.forward(g_, out=o_)
+
+        def both(n):
+            ts = [threading.Thread(target=run, args=(k, n)) for k in range(2)]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+        both(max(1, args.warmup))
+        torch.cuda.synchronize()
+        barrier(world, device)
+        t0 = time.perf_counter()
+        both(nrep)
+        torch.cuda.synchronize()
+        barrier(world, device)
+        el2 = max_over_ranks(time.perf_counter() - t0, world, device)
+        e2e["two_streams"] = {"value": world * 2 * B * nrep / el2, "unit": "transforms/s",
+                              "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps_per_stream": nrep}
+        plan2.close()
+        del grid2, h_in2, h_out2
 
     # roundtrip error over the whole batch, and the oracle check on sampled fields
     rt = float((back - flm).abs().max() / flm.abs().max())
