@@ -9,7 +9,9 @@
  * Through eqn wigner_sum_reln (Sec. 2.2) the harmonics become Fourier series on the
  * torus whose coefficients are eqn fourier_coeff (Sec. 3.1):
  *   F_{m m'} = (-1)^s i^{-(m+s)} sum_l sqrt((2l+1)/4pi) Delta^l_{m'm} Delta^l_{m',-s} sf_lm,
- * with Delta^l_{m'm} = d^l_{m'm}(pi/2) obtained by the Risbo recursion (Sec. 2.2).
+ * with Delta^l_{m'm} = d^l_{m'm}(pi/2) made in FP64 by a three-term recursion within each degree
+ * (from J_x Delta^l = Delta^l J_z and the closed-form first row), or by the paper's Risbo
+ * recursion (Sec. 2.2) with SSHT_FLAG_RISBO.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -156,7 +158,7 @@ SSHT_API int ssht_adjoint(ssht_plan_t plan, const void* g, void* flm, void* stre
  * otherwise).  f: [batch][L][2L-1] complex in; flm: [batch][L*L] complex out. */
 SSHT_API int ssht_forward_triangular(ssht_plan_t plan, const void* f, void* flm, void* stream);
 
-/* The table of Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 2.2, Risbo recursion) for
+/* The table of Delta^l_{m'm} = d^l_{m'm}(pi/2) (Sec. 2.2; the plan's recursion) for
  * 0 <= l < L and 0 <= m', m <= l (the non-negative quadrant the paper precomputes, Sec. 4.1),
  * FP64, entry (l, m', m) at offset(l) + m'(l+1) + m with offset(l) = l(l+1)(2l+1)/6.
  * out: device or host buffer of L(L+1)(2L+1)/6 doubles. */

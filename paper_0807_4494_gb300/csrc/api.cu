@@ -1285,8 +1285,8 @@ int ssht_version(void) { return 100; }
 // and the buckets wait for it before their spin column and packing; in cache mode the tables are
 // made once here.  Buckets run on their own streams, forked from and joined to the caller's.
 // With tuning on, each bucket times every contraction form of the group's precision class
-// (FP32, 3xTF32, split-BF16 for FP32-class groups; tensor-core forms only up to 64 fields) on
-// its own shape and keeps the fastest.
+// (FP32, 3xTF32, split-BF16 for FP32-class groups; the tensor-core forms with their own tuned
+// shape) on its own shape and keeps the fastest.
 // ---------------------------------------------------------------------------------------------
 
 struct ssht_group_s {

@@ -22,15 +22,16 @@
 // four hi*hi products last (truncation then acts on four large steps only), and the epilogue warps
 // add every segment into FP32 running sums in registers (round to nearest).
 //
-// Operands are packed once per call (A also once per plan with the Delta cache) into 32 KB / 64 KB
-// tiles already in the K-major SWIZZLE_128B layout, so the main kernel moves them with 1-D bulk
-// copies.  Main kernel: persistent, one CTA per SM, 10 warps: warp 0 lane 0 issues the bulk copies
-// (2-stage ring), warp 1 lane 0 issues tcgen05.mma into one of two 128 x 256 FP32 accumulator
+// Operands are written once per call (A also once per plan with the Delta cache) as tiles already
+// in the K-major SWIZZLE_128B layout -- 3xTF32: the FP32 values (16 KB an A tile), split into hi and
+// lo in shared memory when they arrive; split-BF16: both parts -- so the main kernel moves them with
+// 1-D bulk copies.  Main kernel: persistent, one CTA per SM, 10 warps: warp 0 lane 0 issues the bulk
+// copies (a ring of 2-4 stages), warp 1 lane 0 issues tcgen05.mma into one of two 128 x 256 FP32 accumulator
 // segments in tensor memory, warps 2-9 (two per 32-lane quarter of tensor memory, one for each
 // sign of m) read the accumulator with tcgen05.ld, apply the phases and write the outputs (the
-// inverse writes half rows m' >= 0 of F; the torus passes apply the extension).  Work items (m, row block)
-// are sorted (inverse: by groups of m; forward: by decreasing length) and dealt round-robin to
-// the CTAs.  Every wait is bounded; a
+// inverse writes half rows m' >= 0 of F; the torus passes apply the extension).  Work items (m, row
+// block) are sorted (groups of four m, or decreasing length) and dealt to the CTAs by a greedy
+// schedule made on the host (schedule()).  Every wait is bounded; a
 // timeout latches a status bit and the CTA drains its copies and MMAs before leaving.
 #include "ssht_internal.h"
 #include "bounds.cuh"
@@ -49,7 +50,7 @@ using namespace tc;
 constexpr int TM = kTileRows;              // rows per tile
 constexpr int TK = kTileK;                 // K per chunk (one 128-byte TF32 row)
 constexpr int A_PART = kAPart;             // 16 KB: one split part of an A tile
-constexpr int A_TILE = kATile;             // hi then lo
+constexpr int A_TILE = kATile;             // both parts of an A tile in shared memory (hi then lo)
 constexpr int MAX_STAGES = 4;             // pipeline depth: a plan parameter, 2 .. MAX_STAGES
 constexpr int EPI_WARPS = 8;                       // two per tensor-memory lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer warp, MMA warp, epilogue warps

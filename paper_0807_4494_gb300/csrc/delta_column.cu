@@ -58,7 +58,7 @@ struct ColumnParams {
   unsigned int* counter;   // next task (zeroed before the launch)
   // tile output (3xTF32 plans): A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} into the forward tile layout
   const float* Uf;         // U_l[m'] in FP32 at l(l+1)/2 + m'
-  uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m', hi then lo
+  uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m' (FP32)
   const long long* abase;  // per m: index of the tile (m, m / 128, 0)
   long long extent;        // entries of the table, or tiles of A (index checks)
 };

@@ -167,7 +167,7 @@ struct ATiles {
 };
 ATiles tc_a_tiles(const TcPlan* p);
 // The column recursion writing the A tiles of a 3xTF32 plan directly (no FP64 table):
-// A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, split hi + lo (delta_column.cu).
+// A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, one value an entry (delta_column.cu).
 cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st);
 // The inverse contraction's A tiles (rows m', K = l) of a 3xTF32 plan: the tile array and, per
 // (m, row block i), the index from which chunk kc's tile is ibase[m * nI + i] + kc.
