@@ -239,8 +239,10 @@ def fft_flops(M):
 
 
 KERNEL_SOURCES = {
-    "column_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu"],
-    "lane_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu"],
+    "column_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu", "paper_0807_4494_gb300/csrc/int_mul.h",
+                                "paper_0807_4494_gb300/csrc/f32_round.h"],
+    "lane_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu", "paper_0807_4494_gb300/csrc/int_mul.h",
+                                "paper_0807_4494_gb300/csrc/f32_round.h"],
     "risbo_kernel": ["paper_0807_4494_gb300/csrc/delta.cu"],
     "tc_gemm_kernel<inverse>": ["paper_0807_4494_gb300/csrc/contract_tc.cu"],
     "tc_gemm_kernel<forward>": ["paper_0807_4494_gb300/csrc/contract_tc.cu"],
@@ -320,9 +322,11 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
         ms = v["ms"]
         if key == "recursion_inverse" and tc and recursion != "risbo" and prec == "tf32x3":
             u = lane_updates(L)
-            res[key] = entry("lane_recursion_kernel", ms, 4.0 * u, pk["fp64_tflops"], None, quad * tv,
-                             {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
-                              "work": "%.3g updates x 3 FP64 instructions (4 flops); writes the inverse's A tiles" % u,
+            res[key] = entry("lane_recursion_kernel", ms, 2.0 * u, pk["fp64_tflops"], None, quad * tv,
+                             {"fp64_instr_frac": (1.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
+                              "work": "%.3g updates x 1 FP64 instruction (the rescaled relation's fused "
+                                      "multiply-add, 2 flops; the coefficient m alpha on the integer pipe); "
+                                      "writes the inverse's A tiles" % u,
                               "fp64_probe_tflops": FP64_PROBE_TFLOPS})
         elif key.startswith("recursion"):
             if recursion == "risbo":
@@ -331,11 +335,16 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
                                  {"fp64_instr_frac": ((4.0 * nh + 5.0 * ni) / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0)})
             else:
                 u = column_updates(L)
-                res[key] = entry("column_recursion_kernel" if tc else "column_recursion_kernel (table)", ms, 4.0 * u,
-                                 pk["fp64_tflops"], None, quad * (tv if tc else 8.0),
-                                 {"fp64_instr_frac": (3.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
-                                  "work": "%.3g updates x 3 FP64 instructions (4 flops); writes %s" % (
-                                      u, "the A tiles (%d B an entry)" % tv if tc else "the FP64 table"),
+                # tile output (3xTF32): the rescaled relation, one FMA an update; FP64 table: b y
+                # and the FMA; the coefficient product on the integer pipe either way
+                direct = prec == "tf32x3"
+                ni = 1.0 if direct else 2.0
+                res[key] = entry("column_recursion_kernel" if direct else "column_recursion_kernel (table)", ms,
+                                 (ni + 1.0) * u, pk["fp64_tflops"], None, quad * (tv if direct else 8.0),
+                                 {"fp64_instr_frac": (ni * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
+                                  "work": "%.3g updates x %d FP64 instruction(s) (%d flops; the coefficient on "
+                                          "the integer pipe); writes %s" % (
+                                      u, ni, ni + 1, "the A tiles (%d B an entry)" % tv if direct else "the FP64 table"),
                                   "fp64_probe_tflops": FP64_PROBE_TFLOPS})
         elif key in ("contraction_inverse", "contraction_forward") and tc:
             nprod, pkey = (3, "tf32_tflops") if prec == "tf32x3" else (6, "bf16_tflops_sustained")

@@ -85,8 +85,8 @@ typedef enum {
                            * instead of the default three-term relation in the first index m'
                            * (Delta_{m'-1,m} from Delta_{m'm} and Delta_{m'+1,m} within one degree,
                            * from the closed-form first row Delta_{l m}).  Both give Delta^l to
-                           * rounding; the default needs no hand-off between degrees and about a
-                           * third of the FP64 instructions. */
+                           * rounding; the default needs no hand-off between degrees and 2 FP64
+                           * instructions an entry against about 9. */
 #define SSHT_FLAG_TUNE 4  /* tensor-core plans: at creation, time the contraction's shape candidates
                            * (fields per GEMM launch 64/32/16, pipeline depth 2-4, work order) on the
                            * plan's own operands and keep the fastest; with the environment variable

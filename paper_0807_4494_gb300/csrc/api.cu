@@ -302,7 +302,7 @@ int make_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (tiles_direct(p)) {
     StageScope sc(p, forward ? SSHT_STAGE_DELTA : SSHT_STAGE_DELTA_INVERSE, st);
     if (forward)
-      SSHT_CUDA(column_run_tiles(p->delta, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
+      SSHT_CUDA(column_run_tiles(p->delta, p->lane, p->d.L, p->Uf, tc_a_tiles(p->tc), st), "recursion into the A tiles");
     else
       SSHT_CUDA(column_run_inverse_tiles(p->delta, p->lane, p->d.L, p->s, tc_inverse_tiles(p->tc), st),
                 "recursion into the inverse's A tiles");

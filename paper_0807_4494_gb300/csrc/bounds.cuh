@@ -26,7 +26,7 @@ enum BoundsSite {
   kbInverseThetaIn = 1, kbInverseThetaOut, kbPhiIn, kbPhiOut, kbForwardThetaIn, kbForwardThetaOut,
   kbAdjointThetaIn, kbAdjointThetaOut, kbPutTile,
   kbPackVIn = 20, kbPackVOut, kbPackAIn, kbPackAOut, kbGemmA, kbGemmX, kbGemmOut,
-  kbColumnTable = 40, kbColumnTile, kbLaneTable, kbLaneTile,
+  kbColumnTable = 40, kbColumnTile, kbLaneTable, kbLaneTile, kbColumnCoef,
   kbPairIn = 60, kbPairOut, kbRealIn, kbRealOut,
   kbSimtIn = 80, kbSimtOut,
 };

@@ -20,9 +20,11 @@
 // m' from l down to 32b (the octant part m' >= m of its columns, plus the 32 x 32 diagonal
 // block), writing row m' of its columns directly (coalesced) and the transposed entries
 // Delta_{m m'} = (-1)^{m'-m} Delta_{m'm} of rows m through a 32 x 32 shared-memory block (again
-// coalesced).  Each update is 3 FP64 instructions (the FP64 pipe is the scarce one on this part:
-// 2 lanes per SM and clock); the coefficients of 32 consecutive m' are made once per chunk by the
-// warp from the sqrt tables.  Tasks are taken longest first from an atomic counter.
+// coalesced).  Each update is 2 FP64 instructions, b(m') Delta_{m'+1,m} and the fused
+// multiply-add (the FP64 pipe is the scarce one on this part: 2 lanes per SM and clock); the
+// coefficient 2m a(m') is the exactly rounded product made on the integer pipe (int_mul.h), and
+// the a(m'), b(m') of 32 consecutive m' are made once per chunk by the warp from the sqrt tables.
+// Tasks are taken longest first from an atomic counter.
 //
 // Range.  Delta_{l,l} = 2^{-l} is below the FP64 normal range for l > 1022.  For band-limits
 // above 1024 each lane carries its own binary exponent E (true value = stored * 2^E) until the
@@ -31,6 +33,7 @@
 #include "ssht_internal.h"
 #include "bounds.cuh"
 #include "f32_round.h"
+#include "int_mul.h"
 #include "tc_common.cuh"
 
 #include <algorithm>
@@ -45,7 +48,7 @@ __device__ __forceinline__ size_t delta_offset_dev(long long l) { return (size_t
 constexpr int kColWarps = 8;
 constexpr int kColThreads = 32 * kColWarps;
 constexpr int kStageDoubles = 32 * 33;              // a warp's transposition block (padded rows)
-constexpr int kWarpDoubles = kStageDoubles + 64;    // + the chunk's coefficients a[32], b[32]
+constexpr int kWarpDoubles = kStageDoubles + 64;    // + the chunk's coefficients (a, b or alpha, p)
 constexpr size_t kColSmem = (size_t)kColWarps * kWarpDoubles * sizeof(double);
 
 struct ColumnParams {
@@ -58,6 +61,8 @@ struct ColumnParams {
   unsigned int* counter;   // next task (zeroed before the launch)
   // tile output (3xTF32 plans): A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} into the forward tile layout
   const float* Uf;         // U_l[m'] in FP32 at l(l+1)/2 + m'
+  const double* alc;       // alpha(l, m') of the rescaled relation at l(l+1)/2 + m'
+  const float* pc;         // p(l, m') at l(l+1)/2 + m'
   uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m' (FP32)
   const long long* abase;  // per m: index of the tile (m, m / 128, 0)
   long long extent;        // entries of the table, or tiles of A (index checks)
@@ -69,6 +74,11 @@ __device__ __forceinline__ void put_a(uint8_t* A, long long tile, long long ntil
   if (!in_bounds(tile, ntiles, site)) return;
   uint8_t* t = A + (size_t)tile * tc::kAPart;
   *(float*)(t + tc::sw128(row, 4 * k)) = x;
+}
+// The same with the swizzled offset of (row, K) in the tile already made.
+__device__ __forceinline__ void put_a_at(uint8_t* A, long long tile, long long ntiles, int site, uint32_t off, float x) {
+  if (!in_bounds(tile, ntiles, site)) return;
+  *(float*)(A + (size_t)tile * tc::kAPart + off) = x;
 }
 
 __device__ __forceinline__ double flip_sign(double v, bool neg) {
@@ -120,12 +130,20 @@ __device__ __forceinline__ double first_row(int l, int m0, int lane, const doubl
 // consecutive K values across the warp (written at once), for every row m' >= 32b; and A_m[l][m']
 // = U_l[m'] x, which goes through the transposition block like the table's transposed entries,
 // for m' >= 32b + 32 -- together every (M, K) pair of the degree once.
+//
+// The tiles need Delta only in FP32, so there the relation runs rescaled: with
+// Delta_{m'm} = p(l, m') y_{m'}, p(l, l) = p(l, l-1) = 1 and p(l, m'-1) = b(m') p(l, m'+1), it reads
+//   y_{m'-1} = m alpha(l, m') y_{m'} - y_{m'+1},   alpha(l, m') = 2 a(m') p(l, m') / p(l, m'-1),
+// one FP64 fused multiply-add an update (the coefficient m alpha is the integer-pipe product).  p
+// lies in [0.15, 1] up to l = 2047 and multiplies the FP32 output; alpha and p are plan-time
+// tables (rescale_tables_kernel).  The FP64 table keeps the unscaled form.
 template <bool SCALED, bool TILES>
 __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(ColumnParams P) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* stage = smem + warp * kWarpDoubles;
-  double* coef = stage + kStageDoubles;
+  double* coef = stage + kStageDoubles;  // a(m') or alpha(l, m') of the chunk; then b(m') or p(l, m')
+  float* coefp = reinterpret_cast<float*>(coef + 32);
   const double* __restrict__ sq = P.sq;
   const double* __restrict__ rsq = P.rsq;
   for (;;) {
@@ -151,13 +169,13 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
       E = ge - l;
     }
     double prev = 0.0;
-    const double m2 = 2.0 * (double)m;
     double* __restrict__ T = TILES ? nullptr : P.table + delta_offset_dev(l);
     const size_t row = (size_t)l + 1;
     // tile output: row l mod 128 of the tiles of row block il; U_l[m] of this lane's column and
     // the tile base of its row M = m (for the transposed writes)
     const int il = l >> 7, trow = l & 127;
     const long long ilpre = 2ll * il * (il + 1);
+    const size_t lrow = (size_t)l * (l + 1) / 2;  // row l of the degree-major tables
     float u_lane = 0.f;
     long long base_lane = 0;
     if (TILES && act) {
@@ -176,13 +194,24 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
         // coefficients a(m'), b(m') of the chunk of m' in [mp & ~31, (mp & ~31) + 31]
         __syncwarp();
         const int k = (mp & ~31) + lane;
-        double a = 0.0, b = 0.0;
-        if (k >= 1 && k <= l) {
-          a = __dmul_rn(rsq[l - k + 1], rsq[l + k]);
-          b = __dmul_rn(__dmul_rn(sq[l - k], sq[l + k + 1]), a);
+        if constexpr (TILES) {
+          double al = 0.0;
+          float pk = 0.f;
+          if (k <= l && in_bounds((long long)(lrow + k), (long long)P.L * (P.L + 1) / 2, kbColumnCoef)) {
+            al = __ldg(&P.alc[lrow + k]);
+            pk = __ldg(&P.pc[lrow + k]);
+          }
+          coef[lane] = al;
+          coefp[lane] = pk;
+        } else {
+          double a = 0.0, b = 0.0;
+          if (k >= 1 && k <= l) {
+            a = __dmul_rn(rsq[l - k + 1], rsq[l + k]);
+            b = __dmul_rn(__dmul_rn(sq[l - k], sq[l + k + 1]), a);
+          }
+          coef[lane] = a;
+          coef[32 + lane] = b;
         }
-        coef[lane] = a;
-        coef[32 + lane] = b;
         __syncwarp();
       }
       const double out = (SCALED && E != 0) ? 0.0 : cur;
@@ -190,7 +219,8 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
         if (act) {
           const int im = mp >> 7;
           const long long tile = abase_cur + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
-          put_a(P.A, tile, P.extent, kbColumnTile, trow, lane, u_lane * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
+          put_a(P.A, tile, P.extent, kbColumnTile, trow, lane,
+                (u_lane * coefp[j]) * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
         }
       } else {
         if (act && in_bounds((long long)delta_offset_dev(l) + (long long)(mp * row + m), P.extent, kbColumnTable))
@@ -204,7 +234,7 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
           __syncwarp();
           const int c = mp + lane;
           if constexpr (TILES) {
-            const float uc = c <= l ? __ldg(&P.Uf[(size_t)l * (l + 1) / 2 + c]) : 0.f;
+            const float uc = c <= l ? __ldg(&P.Uf[lrow + c]) * __ldg(&P.pc[lrow + c]) : 0.f;
             for (int r = 0; r < 32 && m0 + r <= l; ++r) {
               const long long tile = __shfl_sync(0xffffffffu, base_lane, r) + (mp >> 5);
               if (c <= l) put_a(P.A, tile, P.extent, kbColumnTile, trow, lane, uc * f64_to_f32_rn(stage[r * 33 + lane]));
@@ -219,9 +249,13 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
         }
       }
       if (mp > m0) {
-        const double c = __dmul_rn(m2, coef[j]);
-        const double t2 = __dmul_rn(coef[32 + j], prev);
-        const double nxt = __fma_rn(c, cur, -t2);
+        double nxt;
+        if constexpr (TILES) {
+          nxt = __fma_rn(mul_small_rn(coef[j], (uint32_t)m, 0), cur, -prev);  // m alpha(l, m'), integer pipe
+        } else {
+          const double c = mul_small_rn(coef[j], (uint32_t)m, 1);  // 2m a(m'), on the integer pipe
+          nxt = __fma_rn(c, cur, -__dmul_rn(coef[32 + j], prev));
+        }
         prev = cur;
         cur = nxt;
         if (SCALED && E != 0) {
@@ -250,9 +284,12 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
 // at m' = l from its first-row entry.  At step m' the lanes hold Delta^l_{m'm} for 32 consecutive
 // l: A_m[m'][l] = U_l[m'] Delta^l_{m'm} is one 32-wide tile row, and so (for m' > m) is
 // A_{m'}[m][l] = U_l[m] (-1)^{m'-m} Delta^l_{m'm} -- every entry of A with m' >= m from the first
-// write, with m' < m from the second, each once.  The coefficients differ per lane here (they
-// depend on l), so a(l, m'), b(l, m'), the first rows and the transposed U come from plan-time
-// tables in the triangle layout [r][l], l >= r, read 32 consecutive l at a time.
+// write, with m' < m from the second, each once.  The relation runs rescaled as in the column
+// recursion's tile output (Delta = p y, y_{m'-1} = m alpha y_{m'} - y_{m'+1}: one FP64 instruction
+// an update); alpha(l, m') and p(l, m') differ per lane here, so they, the first rows and the
+// transposed U come from plan-time tables in the triangle layout [r][l], l >= r, read 32
+// consecutive l at a time.  The index of (r, l) in that layout drops by L - r when r drops by one,
+// and the tile base of row r by nI, so a step moves both by an addition.
 // ---------------------------------------------------------------------------------------------
 
 // Index of (r, l), 0 <= r <= l < L, in the triangle layout [r][l].
@@ -263,8 +300,8 @@ __host__ __device__ __forceinline__ size_t tri_idx(long long r, long long l, lon
 struct LaneParams {
   int L, as, nI, ntasks;
   const int2* tasks;        // (m, kc), longest first
-  const double* a;          // a(l, m') at tri_idx(m', l)
-  const double* b;          // b(l, m') at tri_idx(m', l)
+  const double* alpha;      // alpha(l, m') at tri_idx(m', l)
+  const float* p;           // p(l, m') at tri_idx(m', l)
   const double* t1m;        // first rows: Delta_{l m} = t1m 2^t1e at tri_idx(m, l)
   const int* t1e;
   const float* ufT;         // U_l[m'] at tri_idx(m', l)
@@ -278,6 +315,7 @@ template <bool SCALED>
 __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LaneParams P) {
   const int lane = threadIdx.x & 31;
   const int L = P.L;
+  const long long ntri = (long long)L * (L + 1) / 2;
   for (;;) {
     int t = 0;
     if (lane == 0) t = (int)atomicAdd(P.counter, 1u);
@@ -290,34 +328,39 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
     const bool inl = l < L && l >= m;     // degree l exists and has column m
     const bool wr = inl && l >= P.as;     // U_l vanishes below |s|: those entries stay zero
     const float um = wr ? __ldg(&P.ufT[tri_idx(m, l, L)]) : 0.f;
-    const double m2 = 2.0 * (double)m;
     const long long* ib_m = P.ibase + (size_t)m * P.nI;
-    const int im = m >> 7, rowm = m & 127;
+    const uint32_t off_m = tc::sw128(m & 127, 4 * lane);  // (row m, K = l) in the tiles A_{m'}[m][.]
     double cur = 0.0, prev = 0.0;
     int E = 0;
-    // the per-step loads (coefficients, U, tile base) of row m' are issued one step ahead, so
-    // that their latency overlaps the previous step's FP64 chain
-    auto fetch = [&](int r, double& a_, double& b_, float& u_, long long& t_) {
+    // the per-step loads (alpha, p, U, tile base) of row m' are issued one step ahead, so that
+    // their latency overlaps the previous step; kidx and ibr follow row r = m' by additions
+    long long kidx = (long long)top * L - (long long)top * (top - 1) / 2 + (l - top);  // tri_idx(top, l)
+    const long long* ibr = P.ibase + (size_t)top * P.nI + (m >> 7);
+    auto fetch = [&](int r, double& a_, float& p_, float& u_, long long& t_) {
       a_ = 0.0;
-      b_ = 0.0;
+      p_ = 0.f;
       u_ = 0.f;
-      if (inl && r <= l && in_bounds((long long)tri_idx(r, l, L), (long long)L * (L + 1) / 2, kbLaneTable)) {
-        const size_t k = tri_idx(r, l, L);
-        a_ = __ldg(&P.a[k]);
-        b_ = __ldg(&P.b[k]);
-        u_ = __ldg(&P.ufT[k]);
+      if (inl && r <= l && in_bounds(kidx, ntri, kbLaneTable)) {
+        a_ = __ldg(&P.alpha[kidx]);
+        p_ = __ldg(&P.p[kidx]);
+        u_ = __ldg(&P.ufT[kidx]);
       }
-      t_ = __ldg(&P.ibase[(size_t)r * P.nI + im]);
+      t_ = __ldg(ibr);
     };
-    double ca, cb;
-    float cu;
-    long long ct;
-    fetch(top, ca, cb, cu, ct);
+    double ca;
+    float cp, cu;
+    long long ct, tb = 0;
+    fetch(top, ca, cp, cu, ct);
     for (int mp = top; mp >= m; --mp) {
-      double na = 0.0, nb = 0.0;
-      float nu = 0.f;
+      double na = 0.0;
+      float np = 0.f, nu = 0.f;
       long long nt = 0;
-      if (mp > m) fetch(mp - 1, na, nb, nu, nt);
+      if (mp > m) {
+        kidx -= L - mp;
+        ibr -= P.nI;
+        fetch(mp - 1, na, np, nu, nt);
+      }
+      if (mp == top || (mp & 127) == 127) tb = __ldg(&ib_m[mp >> 7]) + kc;  // tile of row m' of column m
       if (mp == l && inl) {
         const size_t k = tri_idx(m, l, L);
         const double mant = __ldg(&P.t1m[k]);
@@ -329,18 +372,16 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
           cur = mant;
           E = ex;
         }
-        prev = 0.0;
+        prev = 0.0;  // y_l = Delta_{l m} (p(l, l) = 1)
       }
       const bool on = inl && mp <= l;
       if (on && wr) {
         const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
-        put_a(P.A, __ldg(&ib_m[mp >> 7]) + kc, P.ntiles, kbLaneTile, mp & 127, lane, cu * x);
-        if (mp > m) put_a(P.A, ct + kc, P.ntiles, kbLaneTile, rowm, lane, um * (((mp - m) & 1) ? -x : x));
+        put_a(P.A, tb, P.ntiles, kbLaneTile, mp & 127, lane, (cu * cp) * x);
+        if (mp > m) put_a_at(P.A, ct + kc, P.ntiles, kbLaneTile, off_m, (um * cp) * (((mp - m) & 1) ? -x : x));
       }
       if (on && mp > m) {
-        const double c = __dmul_rn(m2, ca);
-        const double t2 = __dmul_rn(cb, prev);
-        const double nxt = __fma_rn(c, cur, -t2);
+        const double nxt = __fma_rn(mul_small_rn(ca, (uint32_t)m, 0), cur, -prev);  // m alpha(l, m'), integer pipe
         prev = cur;
         cur = nxt;
         if (SCALED && E != 0) {
@@ -357,16 +398,16 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
         }
       }
       ca = na;
-      cb = nb;
+      cp = np;
       cu = nu;
       ct = nt;
     }
   }
 }
 
-// Plan-time tables of the degree-lane recursion: the first rows (one warp per degree and block of
-// 32 columns, the arithmetic of the column recursion), a(l, m'), b(l, m') from the sqrt tables
-// (the same products as the column recursion's), and U transposed.
+// Plan-time tables of the tile-writing recursions: the first rows (one warp per degree and block
+// of 32 columns, the arithmetic of the column recursion), the rescaled relation's alpha(l, m') and
+// p(l, m'), and U transposed.
 __global__ void lane_first_rows_kernel(int L, const double* __restrict__ sq, const double* __restrict__ rsq,
                                        double* __restrict__ t1m, int* __restrict__ t1e) {
   const int lane = threadIdx.x & 31;
@@ -381,25 +422,36 @@ __global__ void lane_first_rows_kernel(int L, const double* __restrict__ sq, con
   }
 }
 
-__global__ void lane_coef_kernel(int L, const double* __restrict__ sq, const double* __restrict__ rsq,
-                                 const float* __restrict__ Uf, double* __restrict__ a, double* __restrict__ b,
-                                 float* __restrict__ ufT) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = (long long)L * (L + 1) / 2;
-  if (e >= n) return;
-  // e = tri_idx(r, l): the row r from a root, then l
-  long long r = (long long)(((2.0 * L + 1.0) - sqrt((2.0 * L + 1.0) * (2.0 * L + 1.0) - 8.0 * (double)e)) * 0.5);
-  while (r > 0 && (long long)tri_idx(r, r, L) > e) --r;
-  while (r + 1 <= L - 1 && (long long)tri_idx(r + 1, r + 1, L) <= e) ++r;
-  const int rr = (int)r, l = (int)(e - (long long)tri_idx(r, r, L) + r);
-  double av = 0.0, bv = 0.0;
-  if (rr >= 1) {
-    av = __dmul_rn(rsq[l - rr + 1], rsq[l + rr]);
-    bv = __dmul_rn(__dmul_rn(sq[l - rr], sq[l + rr + 1]), av);
+// One thread per degree l walks m' = l .. 0: a(m'), b(m') from the sqrt tables (the products of
+// the unscaled relation), p(l, l) = p(l, l-1) = 1, p(l, m'-1) = b(m') p(l, m'+1) and
+// alpha(l, m') = 2 a(m') p(l, m') / p(l, m'-1) (alpha(l, 0) is never used: no step leaves m' = 0).
+// Written degree-major (l(l+1)/2 + m', the column recursion's chunks) and in the triangle layout
+// tri_idx(m', l) (the degree-lane recursion), with U_l[m'] transposed beside them.
+__global__ void rescale_tables_kernel(int L, const double* __restrict__ sq, const double* __restrict__ rsq,
+                                      const float* __restrict__ Uf, double* __restrict__ alc, float* __restrict__ pc,
+                                      double* __restrict__ alT, float* __restrict__ pT, float* __restrict__ ufT) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  const size_t row = (size_t)l * (l + 1) / 2;
+  double p_up = 1.0, p_cur = 1.0;  // p(l, m'+1) and p(l, m') at m' = l (the first is not used there)
+  for (int mp = l; mp >= 0; --mp) {
+    double p_dn = 0.0, al = 0.0;
+    if (mp >= 1) {
+      const double a = __dmul_rn(rsq[l - mp + 1], rsq[l + mp]);
+      const double b = __dmul_rn(__dmul_rn(sq[l - mp], sq[l + mp + 1]), a);
+      p_dn = mp == l ? 1.0 : __dmul_rn(b, p_up);
+      al = __ddiv_rn(__dmul_rn(2.0 * a, p_cur), p_dn);
+    }
+    const size_t kt = tri_idx(mp, l, L);
+    const float pf = __double2float_rn(p_cur);
+    alc[row + mp] = al;
+    pc[row + mp] = pf;
+    alT[kt] = al;
+    pT[kt] = pf;
+    ufT[kt] = Uf[row + mp];
+    p_up = p_cur;
+    p_cur = p_dn;
   }
-  a[e] = av;
-  b[e] = bv;
-  ufT[e] = Uf[(size_t)l * (l + 1) / 2 + rr];
 }
 
 }  // namespace
@@ -451,7 +503,8 @@ cudaError_t column_setup(DeltaWork& w, int L, int device) {
   return cudaMemcpy(w.sqrt_tab, sqv.data(), sqv.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
-static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st) {
+static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, const LaneTables* lt, ATiles t,
+                                 cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   ColumnParams P;
@@ -463,6 +516,8 @@ static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATi
   P.table = w.table;
   P.counter = w.barrier;
   P.Uf = Uf;
+  P.alc = lt ? lt->alc : nullptr;
+  P.pc = lt ? lt->pc : nullptr;
   P.A = t.A;
   P.abase = t.abase;
   const bool tiles = t.A != nullptr;
@@ -478,10 +533,12 @@ static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, ATi
   return cudaGetLastError();
 }
 
-cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) { return column_launch(w, L, nullptr, ATiles(), st); }
+cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) {
+  return column_launch(w, L, nullptr, nullptr, ATiles(), st);
+}
 
 void lane_tables_free(LaneTables& t) {
-  void* ptrs[] = {t.a, t.b, t.t1m, t.t1e, t.ufT, t.tasks};
+  void* ptrs[] = {t.alc, t.pc, t.alT, t.pT, t.t1m, t.t1e, t.ufT, t.tasks};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   t = LaneTables();
@@ -498,13 +555,15 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
   auto len = [L](const int2& x) { return std::min(32 * x.y + 31, L - 1) - x.x; };
   std::stable_sort(tasks.begin(), tasks.end(), [&](const int2& x, const int2& y) { return len(x) > len(y); });
   t.ntasks = (int)tasks.size();
-  if ((e = dev_malloc(&t.a, n * sizeof(double))) != cudaSuccess) return e;
-  if ((e = dev_malloc(&t.b, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.alc, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.pc, n * sizeof(float))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.alT, n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.pT, n * sizeof(float))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.t1m, n * sizeof(double))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.t1e, n * sizeof(int))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.ufT, n * sizeof(float))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.tasks, std::max<size_t>(tasks.size(), 1) * sizeof(int2))) != cudaSuccess) return e;
-  t.bytes = n * (3 * sizeof(double) + sizeof(int) + sizeof(float)) + tasks.size() * sizeof(int2);
+  t.bytes = n * (3 * sizeof(double) + sizeof(int) + 3 * sizeof(float)) + tasks.size() * sizeof(int2);
   if (!tasks.empty() &&
       (e = cudaMemcpy(t.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
@@ -512,7 +571,7 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
   const double* rsq = w.sqrt_tab + (2 * (size_t)L + 4);
   lane_first_rows_kernel<<<dim3((unsigned)((L + 31) / 32 + 7) / 8, (unsigned)L), 256>>>(L, sq, rsq, t.t1m, t.t1e);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  lane_coef_kernel<<<(unsigned)((n + 255) / 256), 256>>>(L, sq, rsq, Uf, t.a, t.b, t.ufT);
+  rescale_tables_kernel<<<(unsigned)((L + 127) / 128), 128>>>(L, sq, rsq, Uf, t.alc, t.pc, t.alT, t.pT, t.ufT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     int dev = 0, sms = 0, per_sm = 0;
@@ -534,7 +593,7 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
 
 cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, int L, int s, InvTiles it,
                                      cudaStream_t st) {
-  if (!it.A || !it.ibase || !t.a || w.method != kDeltaColumn) return cudaErrorInvalidValue;
+  if (!it.A || !it.ibase || !t.alT || w.method != kDeltaColumn) return cudaErrorInvalidValue;
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.barrier, 0, 4 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   LaneParams P;
@@ -543,8 +602,8 @@ cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, in
   P.nI = it.nI;
   P.ntasks = t.ntasks;
   P.tasks = t.tasks;
-  P.a = t.a;
-  P.b = t.b;
+  P.alpha = t.alT;
+  P.p = t.pT;
   P.t1m = t.t1m;
   P.t1e = t.t1e;
   P.ufT = t.ufT;
@@ -559,9 +618,10 @@ cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, in
   return cudaGetLastError();
 }
 
-cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st) {
+cudaError_t column_run_tiles(const DeltaWork& w, const LaneTables& lt, int L, const float* Uf, ATiles t,
+                             cudaStream_t st) {
   if (!t.A || !t.abase || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;
-  return column_launch(w, L, Uf, t, st);
+  return column_launch(w, L, Uf, &lt, t, st);
 }
 
 SSHT_BOUNDS_TU(delta_column)

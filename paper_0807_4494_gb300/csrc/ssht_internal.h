@@ -167,8 +167,11 @@ struct ATiles {
 };
 ATiles tc_a_tiles(const TcPlan* p);
 // The column recursion writing the A tiles of a 3xTF32 plan directly (no FP64 table):
-// A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, one value an entry (delta_column.cu).
-cudaError_t column_run_tiles(const DeltaWork& w, int L, const float* Uf, ATiles t, cudaStream_t st);
+// A_m[l][m'] = Uf_l[m'] Delta^l_{m'm} in FP32, one value an entry, by the rescaled relation whose
+// tables lt holds (delta_column.cu).
+struct LaneTables;
+cudaError_t column_run_tiles(const DeltaWork& w, const LaneTables& lt, int L, const float* Uf, ATiles t,
+                             cudaStream_t st);
 // The inverse contraction's A tiles (rows m', K = l) of a 3xTF32 plan: the tile array and, per
 // (m, row block i), the index from which chunk kc's tile is ibase[m * nI + i] + kc.
 struct InvTiles {
@@ -182,9 +185,14 @@ InvTiles tc_inverse_tiles(const TcPlan* p);
 // Plan-time tables of the recursion with one lane per degree, which writes the inverse's tiles
 // directly (delta_column.cu): coefficients a(l, m'), b(l, m'), first rows (mantissa, exponent), U
 // transposed, in the triangle layout [r][l] (l >= r); its tasks (column m, chunk kc of 32 degrees).
+// Plan-time tables of the tile-writing recursions (3xTF32 plans): the rescaled relation's
+// alpha(l, m') and p(l, m') degree-major (l(l+1)/2 + m') and in the triangle layout [m'][l], the
+// first rows and U transposed (delta_column.cu).
 struct LaneTables {
-  double* a = nullptr;
-  double* b = nullptr;
+  double* alc = nullptr;
+  float* pc = nullptr;
+  double* alT = nullptr;
+  float* pT = nullptr;
   double* t1m = nullptr;
   int* t1e = nullptr;
   float* ufT = nullptr;
