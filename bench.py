@@ -239,6 +239,8 @@ def fft_flops(M):
 
 
 KERNEL_SOURCES = {
+    "column_tiles_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu", "paper_0807_4494_gb300/csrc/int_mul.h",
+                            "paper_0807_4494_gb300/csrc/f32_round.h"],
     "column_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu", "paper_0807_4494_gb300/csrc/int_mul.h",
                                 "paper_0807_4494_gb300/csrc/f32_round.h"],
     "lane_recursion_kernel": ["paper_0807_4494_gb300/csrc/delta_column.cu", "paper_0807_4494_gb300/csrc/int_mul.h",
@@ -322,11 +324,11 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
         ms = v["ms"]
         if key == "recursion_inverse" and tc and recursion != "risbo" and prec == "tf32x3":
             u = lane_updates(L)
-            res[key] = entry("lane_recursion_kernel", ms, 2.0 * u, pk["fp64_tflops"], None, quad * tv,
-                             {"fp64_instr_frac": (1.0 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
-                              "work": "%.3g updates x 1 FP64 instruction (the rescaled relation's fused "
-                                      "multiply-add, 2 flops; the coefficient m alpha on the integer pipe); "
-                                      "writes the inverse's A tiles" % u,
+            res[key] = entry("lane_recursion_kernel", ms, 2.5 * u, pk["fp64_tflops"], None, quad * tv,
+                             {"fp64_instr_frac": (1.5 * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
+                              "work": "%.3g updates x 1.5 FP64 instructions (2.5 flops: the rescaled relation's "
+                                      "fused multiply-add, and the coefficient m alpha at every other row, made "
+                                      "on the integer pipe at the others); writes the inverse's A tiles" % u,
                               "fp64_probe_tflops": FP64_PROBE_TFLOPS})
         elif key.startswith("recursion"):
             if recursion == "risbo":
@@ -335,16 +337,16 @@ def kernel_rooflines(times, L, s, B, prec, recursion, pk):
                                  {"fp64_instr_frac": ((4.0 * nh + 5.0 * ni) / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0)})
             else:
                 u = column_updates(L)
-                # tile output (3xTF32): the rescaled relation, one FMA an update; FP64 table: b y
-                # and the FMA; the coefficient product on the integer pipe either way
+                # tile output (3xTF32): the rescaled relation's FMA, and the coefficient product at
+                # every other row (the integer pipe makes it at the others); FP64 table: b y and
+                # the FMA, the coefficient on the integer pipe
                 direct = prec == "tf32x3"
-                ni = 1.0 if direct else 2.0
-                res[key] = entry("column_recursion_kernel" if direct else "column_recursion_kernel (table)", ms,
-                                 (ni + 1.0) * u, pk["fp64_tflops"], None, quad * (tv if direct else 8.0),
+                ni, nf = (1.5, 2.5) if direct else (2.0, 3.0)
+                res[key] = entry("column_tiles_kernel" if direct else "column_recursion_kernel (table)", ms,
+                                 nf * u, pk["fp64_tflops"], None, quad * (tv if direct else 8.0),
                                  {"fp64_instr_frac": (ni * u / (ms / 1e3)) / (pk["fp64_tflops"][0] * 1e12 / 2.0),
-                                  "work": "%.3g updates x %d FP64 instruction(s) (%d flops; the coefficient on "
-                                          "the integer pipe); writes %s" % (
-                                      u, ni, ni + 1, "the A tiles (%d B an entry)" % tv if direct else "the FP64 table"),
+                                  "work": "%.3g updates x %g FP64 instructions (%g flops); writes %s" % (
+                                      u, ni, nf, "the A tiles (%d B an entry)" % tv if direct else "the FP64 table"),
                                   "fp64_probe_tflops": FP64_PROBE_TFLOPS})
         elif key in ("contraction_inverse", "contraction_forward") and tc:
             nprod, pkey = (3, "tf32_tflops") if prec == "tf32x3" else (6, "bf16_tflops_sustained")

@@ -981,7 +981,8 @@ int create(ssht_plan_t* out, const ssht_plan_desc* desc, const DeltaWork* shared
     p->u_fixed = true;
     // the calls' recursions run on the plan's non-blocking stream: U must be complete first
     ce = cudaDeviceSynchronize();
-    if (ce == cudaSuccess) ce = lane_tables_setup(p->lane, p->delta, L, s, p->Uf, tc_inverse_tiles(p->tc).nC);
+    if (ce == cudaSuccess)
+      ce = lane_tables_setup(p->lane, p->delta, L, s, p->Uf, tc_inverse_tiles(p->tc).nC, tc_a_tiles(p->tc).abase);
     if (ce != cudaSuccess) {
       release(p);
       return fail(ce == cudaErrorMemoryAllocation ? SSHT_ENOMEM : SSHT_ECUDA,

@@ -37,6 +37,7 @@
 #include "tc_common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
@@ -64,7 +65,7 @@ struct ColumnParams {
   const double* alc;       // alpha(l, m') of the rescaled relation at l(l+1)/2 + m'
   const float* pc;         // p(l, m') at l(l+1)/2 + m'
   uint8_t* A;              // tiles (m, l / 128, m' / 32) of 128 rows l x 32 K values m' (FP32)
-  const long long* abase;  // per m: index of the tile (m, m / 128, 0)
+  const long long* ab2;    // per M: index of the tile (M, M / 128, 0) less 2 (M/128) (M/128 + 1)
   long long extent;        // entries of the table, or tiles of A (index checks)
 };
 
@@ -125,25 +126,12 @@ __device__ __forceinline__ double first_row(int l, int m0, int lane, const doubl
   return __dmul_rn(h, gm);
 }
 
-// TILES: write the A tiles of a 3xTF32 plan instead of the table.  With x = Delta_{m'm} in lane m
-// at step m' (row), the entry serves two tiles: A_{m'}[l][m] = U_l[m] (-1)^{m'-m} x, a row of 32
-// consecutive K values across the warp (written at once), for every row m' >= 32b; and A_m[l][m']
-// = U_l[m'] x, which goes through the transposition block like the table's transposed entries,
-// for m' >= 32b + 32 -- together every (M, K) pair of the degree once.
-//
-// The tiles need Delta only in FP32, so there the relation runs rescaled: with
-// Delta_{m'm} = p(l, m') y_{m'}, p(l, l) = p(l, l-1) = 1 and p(l, m'-1) = b(m') p(l, m'+1), it reads
-//   y_{m'-1} = m alpha(l, m') y_{m'} - y_{m'+1},   alpha(l, m') = 2 a(m') p(l, m') / p(l, m'-1),
-// one FP64 fused multiply-add an update (the coefficient m alpha is the integer-pipe product).  p
-// lies in [0.15, 1] up to l = 2047 and multiplies the FP32 output; alpha and p are plan-time
-// tables (rescale_tables_kernel).  The FP64 table keeps the unscaled form.
-template <bool SCALED, bool TILES>
+template <bool SCALED>
 __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(ColumnParams P) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* stage = smem + warp * kWarpDoubles;
-  double* coef = stage + kStageDoubles;  // a(m') or alpha(l, m') of the chunk; then b(m') or p(l, m')
-  float* coefp = reinterpret_cast<float*>(coef + 32);
+  double* coef = stage + kStageDoubles;  // a(m') of the chunk, then b(m')
   const double* __restrict__ sq = P.sq;
   const double* __restrict__ rsq = P.rsq;
   for (;;) {
@@ -169,93 +157,44 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
       E = ge - l;
     }
     double prev = 0.0;
-    double* __restrict__ T = TILES ? nullptr : P.table + delta_offset_dev(l);
+    double* __restrict__ T = P.table + delta_offset_dev(l);
     const size_t row = (size_t)l + 1;
-    // tile output: row l mod 128 of the tiles of row block il; U_l[m] of this lane's column and
-    // the tile base of its row M = m (for the transposed writes)
-    const int il = l >> 7, trow = l & 127;
-    const long long ilpre = 2ll * il * (il + 1);
-    const size_t lrow = (size_t)l * (l + 1) / 2;  // row l of the degree-major tables
-    float u_lane = 0.f;
-    long long base_lane = 0;
-    if (TILES && act) {
-      u_lane = __ldg(&P.Uf[(size_t)l * (l + 1) / 2 + m]);
-      const int im = m >> 7;
-      base_lane = __ldg(&P.abase[m]) + ilpre - 2ll * im * (im + 1);
-    }
 
     // ---- rows m' = l .. m0 ----
-    // tile output: the base of row M = m' (a load), fetched one step ahead
-    long long abase_cur = TILES ? __ldg(&P.abase[l]) : 0, abase_next = 0;
     for (int mp = l; mp >= m0; --mp) {
-      if (TILES && mp > m0) abase_next = __ldg(&P.abase[mp - 1]);
       const int j = mp & 31;
       if (mp == l || j == 31) {
         // coefficients a(m'), b(m') of the chunk of m' in [mp & ~31, (mp & ~31) + 31]
         __syncwarp();
         const int k = (mp & ~31) + lane;
-        if constexpr (TILES) {
-          double al = 0.0;
-          float pk = 0.f;
-          if (k <= l && in_bounds((long long)(lrow + k), (long long)P.L * (P.L + 1) / 2, kbColumnCoef)) {
-            al = __ldg(&P.alc[lrow + k]);
-            pk = __ldg(&P.pc[lrow + k]);
-          }
-          coef[lane] = al;
-          coefp[lane] = pk;
-        } else {
-          double a = 0.0, b = 0.0;
-          if (k >= 1 && k <= l) {
-            a = __dmul_rn(rsq[l - k + 1], rsq[l + k]);
-            b = __dmul_rn(__dmul_rn(sq[l - k], sq[l + k + 1]), a);
-          }
-          coef[lane] = a;
-          coef[32 + lane] = b;
+        double a = 0.0, b = 0.0;
+        if (k >= 1 && k <= l) {
+          a = __dmul_rn(rsq[l - k + 1], rsq[l + k]);
+          b = __dmul_rn(__dmul_rn(sq[l - k], sq[l + k + 1]), a);
         }
+        coef[lane] = a;
+        coef[32 + lane] = b;
         __syncwarp();
       }
       const double out = (SCALED && E != 0) ? 0.0 : cur;
-      if constexpr (TILES) {
-        if (act) {
-          const int im = mp >> 7;
-          const long long tile = abase_cur + ilpre - 2ll * im * (im + 1) + (m0 >> 5);
-          put_a(P.A, tile, P.extent, kbColumnTile, trow, lane,
-                (u_lane * coefp[j]) * f64_to_f32_rn(flip_sign(out, ((mp - m) & 1) != 0)));
-        }
-      } else {
-        if (act && in_bounds((long long)delta_offset_dev(l) + (long long)(mp * row + m), P.extent, kbColumnTable))
-          T[(size_t)mp * row + m] = out;
-      }
+      if (act && in_bounds((long long)delta_offset_dev(l) + (long long)(mp * row + m), P.extent, kbColumnTable))
+        T[(size_t)mp * row + m] = out;
       if (mp >= m0 + 32) {
-        // table: transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}; tiles: A_m[l][m'] =
-        // U_l[m'] Delta_{m'm}; either way written a 32-column chunk at a time
-        stage[lane * 33 + j] = TILES ? out : flip_sign(out, ((mp - m) & 1) != 0);
+        // transposed entry Delta_{m m'} = (-1)^{m'-m} Delta_{m'm}, written a 32-column chunk at a time
+        stage[lane * 33 + j] = flip_sign(out, ((mp - m) & 1) != 0);
         if (j == 0) {
           __syncwarp();
           const int c = mp + lane;
-          if constexpr (TILES) {
-            const float uc = c <= l ? __ldg(&P.Uf[lrow + c]) * __ldg(&P.pc[lrow + c]) : 0.f;
-            for (int r = 0; r < 32 && m0 + r <= l; ++r) {
-              const long long tile = __shfl_sync(0xffffffffu, base_lane, r) + (mp >> 5);
-              if (c <= l) put_a(P.A, tile, P.extent, kbColumnTile, trow, lane, uc * f64_to_f32_rn(stage[r * 33 + lane]));
-            }
-          } else {
-            for (int r = 0; r < 32 && m0 + r <= l; ++r)
-              if (c <= l && in_bounds((long long)delta_offset_dev(l) + (long long)((m0 + r) * row + c), P.extent,
-                                      kbColumnTable))
-                T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
-          }
+          for (int r = 0; r < 32 && m0 + r <= l; ++r)
+            if (c <= l && in_bounds((long long)delta_offset_dev(l) + (long long)((m0 + r) * row + c), P.extent,
+                                    kbColumnTable))
+              T[(size_t)(m0 + r) * row + c] = stage[r * 33 + lane];
           __syncwarp();
         }
       }
       if (mp > m0) {
-        double nxt;
-        if constexpr (TILES) {
-          nxt = __fma_rn(mul_small_rn(coef[j], (uint32_t)m, 0), cur, -prev);  // m alpha(l, m'), integer pipe
-        } else {
-          const double c = mul_small_rn(coef[j], (uint32_t)m, 1);  // 2m a(m'), on the integer pipe
-          nxt = __fma_rn(c, cur, -__dmul_rn(coef[32 + j], prev));
-        }
+        const double c = mul_small_rn(coef[j], (uint32_t)m, 1);  // 2m a(m'), on the integer pipe
+        const double nxt = __fma_rn(c, cur, -__dmul_rn(coef[32 + j], prev));
         prev = cur;
         cur = nxt;
         if (SCALED && E != 0) {
@@ -271,7 +210,133 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
           }
         }
       }
-      if (TILES) abase_cur = abase_next;
+    }
+  }
+}
+
+// The same walk writing the A tiles of a 3xTF32 plan instead of the table.  With x = Delta_{m'm}
+// in lane m at step m' (row), the entry serves two tiles: A_{m'}[l][m] = U_l[m] (-1)^{m'-m} x, a
+// row of 32 consecutive K values across the warp (written at once), for every row m' >= 32b; and
+// A_m[l][m'] = U_l[m'] x, which goes through the transposition block like the table's transposed
+// entries, for m' >= 32b + 32 -- together every (M, K) pair of the degree once.  Every write of a
+// task lands on row l mod 128, K = lane of its tile, one swizzled offset; the tile of column group
+// M is ab2[M] + 2 il (il + 1) + chunk (ab2 holds the plan's per-M tile base less the row blocks
+// below M's own).
+//
+// The tiles need Delta only in FP32, so here the relation runs rescaled: with
+// Delta_{m'm} = p(l, m') y_{m'}, p(l, l) = p(l, l-1) = 1 and p(l, m'-1) = b(m') p(l, m'+1), it reads
+//   y_{m'-1} = m alpha(l, m') y_{m'} - y_{m'+1},   alpha(l, m') = 2 a(m') p(l, m') / p(l, m'-1),
+// one FP64 fused multiply-add an update (the coefficient m alpha is the integer-pipe product).  p
+// lies in [0.15, 1] up to l = 2047 and multiplies the FP32 output; alpha and p are plan-time
+// tables (rescale_tables_kernel).  Each value is rounded to FP32 once and staged as FP32, so a
+// CTA needs half the table kernel's shared memory and three fit an SM.
+constexpr int kTileStageFloats = 32 * 33;
+constexpr int kTileWarpBytes = kTileStageFloats * 4 + 32 * 8 + 32 * 4;  // stage, alpha[32], p[32]
+constexpr size_t kTileSmem = (size_t)kColWarps * kTileWarpBytes;
+
+template <bool SCALED>
+__global__ void __launch_bounds__(kColThreads, 3) column_tiles_kernel(ColumnParams P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* stage = reinterpret_cast<float*>(smraw + warp * kTileWarpBytes);
+  double* alw = reinterpret_cast<double*>(smraw + warp * kTileWarpBytes + kTileStageFloats * 4);
+  float* pw = reinterpret_cast<float*>(alw + 32);
+  const double* __restrict__ sq = P.sq;
+  const double* __restrict__ rsq = P.rsq;
+  const long long ntri = (long long)P.L * (P.L + 1) / 2;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(P.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= P.ntasks) break;
+    const int2 task = P.tasks[t];
+    const int l = task.x, m0 = 32 * task.y, m = m0 + lane;
+    const bool act = m <= l;
+
+    // ---- first row: y_l = Delta_{l m} = (-1)^{l-m} v 2^{ge - l} (p(l, l) = 1) ----
+    int ge;
+    const double v = first_row(l, m0, lane, sq, rsq, &ge);
+    int E = 0;
+    double cur;
+    if (!act) {
+      cur = 0.0;
+    } else if (!SCALED || exp_of(v) + ge - l >= -1021) {
+      cur = flip_sign(ldexp(v, ge - l), ((l - m) & 1) != 0);
+    } else {
+      cur = flip_sign(v, ((l - m) & 1) != 0);
+      E = ge - l;
+    }
+    double prev = 0.0;
+    const int il = l >> 7;
+    const long long ilpre = 2ll * il * (il + 1);
+    const long long tadd = ilpre + (m0 >> 5);
+    const uint32_t off = tc::sw128(l & 127, 4 * lane);
+    const size_t lrow = (size_t)l * (l + 1) / 2;  // row l of the degree-major tables
+    const double md = (double)m;
+    // U_l[m] of this lane's column and the tile base of its row M = m (the transposed writes)
+    float u_lane = 0.f;
+    long long base_lane = 0;
+    if (act) {
+      u_lane = __ldg(&P.Uf[lrow + m]);
+      base_lane = __ldg(&P.ab2[m]) + ilpre;
+    }
+    // the base of row M = m' (a load), fetched one step ahead
+    long long ab_cur = __ldg(&P.ab2[l]), ab_next = 0;
+    for (int mp = l; mp >= m0; --mp) {
+      if (mp > m0) ab_next = __ldg(&P.ab2[mp - 1]);
+      const int j = mp & 31;
+      if (mp == l || j == 31) {
+        // alpha(l, m') and p(l, m') of the chunk of m' in [mp & ~31, (mp & ~31) + 31]
+        __syncwarp();
+        const int k = (mp & ~31) + lane;
+        double al = 0.0;
+        float pk = 0.f;
+        if (k <= l && in_bounds((long long)(lrow + k), ntri, kbColumnCoef)) {
+          al = __ldg(&P.alc[lrow + k]);
+          pk = __ldg(&P.pc[lrow + k]);
+        }
+        alw[lane] = al;
+        pw[lane] = pk;
+        __syncwarp();
+      }
+      const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);  // y_{m'} in FP32
+      if (act) put_a_at(P.A, ab_cur + tadd, P.extent, kbColumnTile, off, (u_lane * pw[j]) * (((mp - m) & 1) ? -x : x));
+      if (mp >= m0 + 32) {
+        stage[lane * 33 + j] = x;
+        if (j == 0) {
+          // A_M[l][m'] for the columns M = m0 + r, m' = mp + lane: U_l[m'] p(l, m') y
+          __syncwarp();
+          const int c = mp + lane;
+          const float uc = c <= l ? __ldg(&P.Uf[lrow + c]) * __ldg(&P.pc[lrow + c]) : 0.f;
+          const int cb = mp >> 5;
+          for (int r = 0; r < 32 && m0 + r <= l; ++r) {
+            const long long tile = __shfl_sync(0xffffffffu, base_lane, r) + cb;
+            if (c <= l) put_a_at(P.A, tile, P.extent, kbColumnTile, off, uc * stage[r * 33 + lane]);
+          }
+          __syncwarp();
+        }
+      }
+      if (mp > m0) {
+        // m alpha: on the FP64 pipe at odd rows, on the integer pipe at even ones (the same
+        // exactly rounded product; the two pipes share the work)
+        const double c = (mp & 1) ? __dmul_rn(md, alw[j]) : mul_small_rn(alw[j], (uint32_t)m, 0);
+        const double nxt = __fma_rn(c, cur, -prev);
+        prev = cur;
+        cur = nxt;
+        if (SCALED && E != 0) {
+          const int xe = exp_of(cur);
+          if (xe + E >= -1021) {
+            cur = ldexp(cur, E);
+            prev = ldexp(prev, E);
+            E = 0;
+          } else if (xe > 512) {
+            cur = __dmul_rn(cur, 0x1p-512);
+            prev = __dmul_rn(prev, 0x1p-512);
+            E += 512;
+          }
+        }
+      }
+      ab_cur = ab_next;
     }
   }
 }
@@ -302,7 +367,8 @@ struct LaneParams {
   const int2* tasks;        // (m, kc), longest first
   const double* alpha;      // alpha(l, m') at tri_idx(m', l)
   const float* p;           // p(l, m') at tri_idx(m', l)
-  const double* t1m;        // first rows: Delta_{l m} = t1m 2^t1e at tri_idx(m, l)
+  const double* t1m;        // first rows: Delta_{l m} = t1m 2^t1e at tri_idx(m, l) (t1e = 0 where a
+                            // double holds the value)
   const int* t1e;
   const float* ufT;         // U_l[m'] at tri_idx(m', l)
   uint8_t* A;               // inverse tiles (m, m' / 128, l / 32)
@@ -311,11 +377,28 @@ struct LaneParams {
   long long ntiles;         // tiles of A (index checks)
 };
 
+// Folds the exponent of the scaled variant back in, or moves the values away from overflow.
+__device__ __forceinline__ void rescale_exponent(double& cur, double& prev, int& E) {
+  const int x = exp_of(cur);
+  if (x + E >= -1021) {  // back in the normal range
+    cur = ldexp(cur, E);
+    prev = ldexp(prev, E);
+    E = 0;
+  } else if (x > 512) {
+    cur = __dmul_rn(cur, 0x1p-512);
+    prev = __dmul_rn(prev, 0x1p-512);
+    E += 512;
+  }
+}
+
+// Rows top .. max(m, 32 kc) are the start-up phase: lane l joins at m' = l from its first-row
+// entry.  Below 32 kc every lane of a degree that exists runs, m' < l, and the steady loop needs
+// none of the start-up tests.
 template <bool SCALED>
 __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LaneParams P) {
   const int lane = threadIdx.x & 31;
   const int L = P.L;
-  const long long ntri = (long long)L * (L + 1) / 2;
+  const int ntri = L * (L + 1) / 2;
   for (;;) {
     int t = 0;
     if (lane == 0) t = (int)atomicAdd(P.counter, 1u);
@@ -325,82 +408,115 @@ __global__ void __launch_bounds__(kColThreads, 4) lane_recursion_kernel(LanePara
     const int m = task.x, kc = task.y;
     const int l = 32 * kc + lane;
     const int top = min(32 * kc + 31, L - 1);
+    const int lo = max(m, 32 * kc);
     const bool inl = l < L && l >= m;     // degree l exists and has column m
     const bool wr = inl && l >= P.as;     // U_l vanishes below |s|: those entries stay zero
     const float um = wr ? __ldg(&P.ufT[tri_idx(m, l, L)]) : 0.f;
     const long long* ib_m = P.ibase + (size_t)m * P.nI;
     const uint32_t off_m = tc::sw128(m & 127, 4 * lane);  // (row m, K = l) in the tiles A_{m'}[m][.]
+    uint8_t* const A = P.A;
     double cur = 0.0, prev = 0.0;
     int E = 0;
-    // the per-step loads (alpha, p, U, tile base) of row m' are issued one step ahead, so that
-    // their latency overlaps the previous step; kidx and ibr follow row r = m' by additions
-    long long kidx = (long long)top * L - (long long)top * (top - 1) / 2 + (l - top);  // tri_idx(top, l)
+    // the per-row loads (alpha, p, U, tile base) are issued one step ahead, so that their latency
+    // overlaps the step before; kidx and ibr follow the row r by additions
+    int kidx = top * L - top * (top - 1) / 2 + (l - top);  // tri_idx(top, l)
     const long long* ibr = P.ibase + (size_t)top * P.nI + (m >> 7);
-    auto fetch = [&](int r, double& a_, float& p_, float& u_, long long& t_) {
-      a_ = 0.0;
-      p_ = 0.f;
-      u_ = 0.f;
-      if (inl && r <= l && in_bounds(kidx, ntri, kbLaneTable)) {
-        a_ = __ldg(&P.alpha[kidx]);
-        p_ = __ldg(&P.p[kidx]);
-        u_ = __ldg(&P.ufT[kidx]);
-      }
-      t_ = __ldg(ibr);
-    };
-    double ca;
-    float cp, cu;
-    long long ct, tb = 0;
-    fetch(top, ca, cp, cu, ct);
-    for (int mp = top; mp >= m; --mp) {
+    double ca = 0.0;
+    float cp = 0.f, cu = 0.f;
+    if (inl && top <= l && in_bounds(kidx, ntri, kbLaneTable)) {
+      ca = __ldg(&P.alpha[kidx]);
+      cp = __ldg(&P.p[kidx]);
+      cu = __ldg(&P.ufT[kidx]);
+    }
+    long long ct = __ldg(ibr), tb = 0;
+    int mp = top;
+    // ---- start-up rows top .. lo ----
+    for (; mp >= lo; --mp) {
       double na = 0.0;
       float np = 0.f, nu = 0.f;
       long long nt = 0;
       if (mp > m) {
         kidx -= L - mp;
         ibr -= P.nI;
-        fetch(mp - 1, na, np, nu, nt);
+        if (inl && mp - 1 <= l && in_bounds(kidx, ntri, kbLaneTable)) {
+          na = __ldg(&P.alpha[kidx]);
+          np = __ldg(&P.p[kidx]);
+          nu = __ldg(&P.ufT[kidx]);
+        }
+        nt = __ldg(ibr);
       }
       if (mp == top || (mp & 127) == 127) tb = __ldg(&ib_m[mp >> 7]) + kc;  // tile of row m' of column m
       if (mp == l && inl) {
         const size_t k = tri_idx(m, l, L);
-        const double mant = __ldg(&P.t1m[k]);
-        const int ex = __ldg(&P.t1e[k]);
-        if (!SCALED || exp_of(mant) + ex >= -1021) {
-          cur = ldexp(mant, ex);
-          E = 0;
-        } else {
-          cur = mant;
-          E = ex;
+        cur = __ldg(&P.t1m[k]);  // y_l = Delta_{l m} (p(l, l) = 1), or its mantissa with E apart
+        E = SCALED ? __ldg(&P.t1e[k]) : 0;
+        prev = 0.0;
+      }
+      if (inl && mp <= l) {
+        if (wr) {
+          const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
+          put_a(A, tb, P.ntiles, kbLaneTile, mp & 127, lane, (cu * cp) * x);
+          if (mp > m) put_a_at(A, ct + kc, P.ntiles, kbLaneTile, off_m, (um * cp) * (((mp - m) & 1) ? -x : x));
         }
-        prev = 0.0;  // y_l = Delta_{l m} (p(l, l) = 1)
-      }
-      const bool on = inl && mp <= l;
-      if (on && wr) {
-        const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
-        put_a(P.A, tb, P.ntiles, kbLaneTile, mp & 127, lane, (cu * cp) * x);
-        if (mp > m) put_a_at(P.A, ct + kc, P.ntiles, kbLaneTile, off_m, (um * cp) * (((mp - m) & 1) ? -x : x));
-      }
-      if (on && mp > m) {
-        const double nxt = __fma_rn(mul_small_rn(ca, (uint32_t)m, 0), cur, -prev);  // m alpha(l, m'), integer pipe
-        prev = cur;
-        cur = nxt;
-        if (SCALED && E != 0) {
-          const int x = exp_of(cur);
-          if (x + E >= -1021) {
-            cur = ldexp(cur, E);
-            prev = ldexp(prev, E);
-            E = 0;
-          } else if (x > 512) {
-            cur = __dmul_rn(cur, 0x1p-512);
-            prev = __dmul_rn(prev, 0x1p-512);
-            E += 512;
-          }
+        if (mp > m) {
+          const double nxt = __fma_rn(mul_small_rn(ca, (uint32_t)m, 0), cur, -prev);  // m alpha, integer pipe
+          prev = cur;
+          cur = nxt;
+          if (SCALED && E != 0) rescale_exponent(cur, prev, E);
         }
       }
       ca = na;
       cp = np;
       cu = nu;
       ct = nt;
+    }
+    // ---- steady rows lo - 1 .. m + 1: every lane with inl runs, m' < l ----
+    // The coefficient m alpha alternates between the FP64 pipe and the integer pipe (both give
+    // the exactly rounded product), which shares the work between the two.
+    const double md = (double)m;
+    auto steady = [&](auto on_fp64) {
+      kidx -= L - mp;
+      ibr -= P.nI;
+      double na = 0.0;
+      float np = 0.f, nu = 0.f;
+      if (inl && in_bounds(kidx, ntri, kbLaneTable)) {
+        na = __ldg(&P.alpha[kidx]);
+        np = __ldg(&P.p[kidx]);
+        nu = __ldg(&P.ufT[kidx]);
+      }
+      const long long nt = __ldg(ibr);
+      if ((mp & 127) == 127) tb = __ldg(&ib_m[mp >> 7]) + kc;
+      if (inl) {
+        if (wr) {
+          const float x = f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur);
+          put_a(A, tb, P.ntiles, kbLaneTile, mp & 127, lane, (cu * cp) * x);
+          put_a_at(A, ct + kc, P.ntiles, kbLaneTile, off_m, (um * cp) * (((mp - m) & 1) ? -x : x));
+        }
+        double c;
+        if constexpr (decltype(on_fp64)::value)
+          c = __dmul_rn(md, ca);
+        else
+          c = mul_small_rn(ca, (uint32_t)m, 0);
+        const double nxt = __fma_rn(c, cur, -prev);
+        prev = cur;
+        cur = nxt;
+        if (SCALED && E != 0) rescale_exponent(cur, prev, E);
+      }
+      ca = na;
+      cp = np;
+      cu = nu;
+      ct = nt;
+      --mp;
+    };
+    while (mp > m + 1) {
+      steady(std::true_type{});
+      steady(std::false_type{});
+    }
+    if (mp > m) steady(std::false_type{});
+    // ---- the last row m' = m, if the steady loop reached it ----
+    if (m < lo) {
+      if ((m & 127) == 127) tb = __ldg(&ib_m[m >> 7]) + kc;
+      if (wr) put_a(A, tb, P.ntiles, kbLaneTile, m & 127, lane, (cu * cp) * f64_to_f32_rn((SCALED && E != 0) ? 0.0 : cur));
     }
   }
 }
@@ -416,9 +532,12 @@ __global__ void lane_first_rows_kernel(int L, const double* __restrict__ sq, con
   int ge;
   const double v = first_row(l, m0, lane, sq, rsq, &ge);
   if (m <= l) {
+    // Delta_{l m} itself where a double holds it (always for L <= 1024: the scaled variant of the
+    // recursion runs above that); else the mantissa and the exponent apart
     const size_t k = tri_idx(m, l, L);
-    t1m[k] = flip_sign(v, ((l - m) & 1) != 0);
-    t1e[k] = ge - l;
+    const bool whole = L <= 1024 || exp_of(v) + ge - l >= -1021;
+    t1m[k] = flip_sign(whole ? ldexp(v, ge - l) : v, ((l - m) & 1) != 0);
+    t1e[k] = whole ? 0 : ge - l;
   }
 }
 
@@ -454,6 +573,15 @@ __global__ void rescale_tables_kernel(int L, const double* __restrict__ sq, cons
   }
 }
 
+// ab2[M] = abase[M] - 2 i (i + 1), i = M / 128: the tile of (M, row block il, chunk c) of the
+// forward layout is ab2[M] + 2 il (il + 1) + c.
+__global__ void tile_base_kernel(int L, const long long* __restrict__ abase, long long* __restrict__ ab2) {
+  const int M = blockIdx.x * blockDim.x + threadIdx.x;
+  if (M >= L) return;
+  const long long i = M >> 7;
+  ab2[M] = abase[M] - 2 * i * (i + 1);
+}
+
 }  // namespace
 
 // Tasks (l, b) for every degree l < L and block b <= l / 32 of 32 columns, longest first (a task
@@ -471,15 +599,12 @@ cudaError_t column_setup(DeltaWork& w, int L, int device) {
   int sms = 0, per_sm = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
   const bool scaled = L > 1024;
-  const void* fns[2] = {scaled ? (const void*)column_recursion_kernel<true, false> : (const void*)column_recursion_kernel<false, false>,
-                        scaled ? (const void*)column_recursion_kernel<true, true> : (const void*)column_recursion_kernel<false, true>};
-  for (const void* fn : fns) {
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)) !=
-        cudaSuccess)
-      return e;
-  }
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[1], kColThreads, kColSmem)) != cudaSuccess) return e;
+  const void* fn = scaled ? (const void*)column_recursion_kernel<true> : (const void*)column_recursion_kernel<false>;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kColThreads, kColSmem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const std::vector<int2> tasks = column_tasks(L);
   w.method = kDeltaColumn;
@@ -519,17 +644,17 @@ static cudaError_t column_launch(const DeltaWork& w, int L, const float* Uf, con
   P.alc = lt ? lt->alc : nullptr;
   P.pc = lt ? lt->pc : nullptr;
   P.A = t.A;
-  P.abase = t.abase;
+  P.ab2 = lt ? lt->ab2 : nullptr;
   const bool tiles = t.A != nullptr;
   P.extent = tiles ? t.ntiles : (long long)delta_offset(L);
-  if (L > 1024 && tiles)
-    column_recursion_kernel<true, true><<<w.blocks, w.threads, w.smem, st>>>(P);
-  else if (L > 1024)
-    column_recursion_kernel<true, false><<<w.blocks, w.threads, w.smem, st>>>(P);
+  if (tiles && L > 1024)
+    column_tiles_kernel<true><<<lt->col_blocks, kColThreads, kTileSmem, st>>>(P);
   else if (tiles)
-    column_recursion_kernel<false, true><<<w.blocks, w.threads, w.smem, st>>>(P);
+    column_tiles_kernel<false><<<lt->col_blocks, kColThreads, kTileSmem, st>>>(P);
+  else if (L > 1024)
+    column_recursion_kernel<true><<<w.blocks, w.threads, w.smem, st>>>(P);
   else
-    column_recursion_kernel<false, false><<<w.blocks, w.threads, w.smem, st>>>(P);
+    column_recursion_kernel<false><<<w.blocks, w.threads, w.smem, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -538,13 +663,14 @@ cudaError_t column_run(const DeltaWork& w, int L, cudaStream_t st) {
 }
 
 void lane_tables_free(LaneTables& t) {
-  void* ptrs[] = {t.alc, t.pc, t.alT, t.pT, t.t1m, t.t1e, t.ufT, t.tasks};
+  void* ptrs[] = {t.alc, t.pc, t.alT, t.pT, t.t1m, t.t1e, t.ufT, t.ab2, t.tasks};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   t = LaneTables();
 }
 
-cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC) {
+cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC,
+                              const long long* abase) {
   cudaError_t e;
   const size_t n = (size_t)L * (L + 1) / 2;
   const int as = s < 0 ? -s : s;
@@ -562,8 +688,10 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
   if ((e = dev_malloc(&t.t1m, n * sizeof(double))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.t1e, n * sizeof(int))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.ufT, n * sizeof(float))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&t.ab2, (size_t)L * sizeof(long long))) != cudaSuccess) return e;
   if ((e = dev_malloc(&t.tasks, std::max<size_t>(tasks.size(), 1) * sizeof(int2))) != cudaSuccess) return e;
-  t.bytes = n * (3 * sizeof(double) + sizeof(int) + 3 * sizeof(float)) + tasks.size() * sizeof(int2);
+  t.bytes = n * (3 * sizeof(double) + sizeof(int) + 3 * sizeof(float)) + (size_t)L * sizeof(long long) +
+            tasks.size() * sizeof(int2);
   if (!tasks.empty() &&
       (e = cudaMemcpy(t.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
@@ -573,6 +701,8 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   rescale_tables_kernel<<<(unsigned)((L + 127) / 128), 128>>>(L, sq, rsq, Uf, t.alc, t.pc, t.alT, t.pT, t.ufT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tile_base_kernel<<<(unsigned)((L + 127) / 128), 128>>>(L, abase, t.ab2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -581,6 +711,19 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
         cudaSuccess)
       return e;
     t.blocks = sms * std::max(1, std::min(per_sm, 4));
+    const void* fns[2] = {(const void*)column_tiles_kernel<false>, (const void*)column_tiles_kernel<true>};
+    for (const void* fn : fns) {
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
+    }
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[L > 1024 ? 1 : 0], kColThreads, kTileSmem)) !=
+        cudaSuccess)
+      return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    t.col_blocks = sms * std::min(per_sm, 3);
   }
   if ((e = cudaFuncSetAttribute(lane_recursion_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
@@ -620,7 +763,7 @@ cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, in
 
 cudaError_t column_run_tiles(const DeltaWork& w, const LaneTables& lt, int L, const float* Uf, ATiles t,
                              cudaStream_t st) {
-  if (!t.A || !t.abase || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;
+  if (!t.A || !lt.ab2 || !lt.alc || !Uf || w.method != kDeltaColumn) return cudaErrorInvalidValue;
   return column_launch(w, L, Uf, &lt, t, st);
 }
 

@@ -196,13 +196,16 @@ struct LaneTables {
   double* t1m = nullptr;
   int* t1e = nullptr;
   float* ufT = nullptr;
+  long long* ab2 = nullptr;  // per M: the forward tile base less the row blocks below M's own
   int2* tasks = nullptr;
   int ntasks = 0;
-  int blocks = 0;  // grid of the recursion kernel
+  int blocks = 0;      // grid of the degree-lane recursion
+  int col_blocks = 0;  // grid of the column recursion writing the forward tiles
   size_t bytes = 0;
 };
 // Needs the column DeltaWork of the plan (its sqrt tables) and U (FP32) on the device; synchronises.
-cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC);
+cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, const float* Uf, int nC,
+                              const long long* abase);
 void lane_tables_free(LaneTables& t);
 cudaError_t column_run_inverse_tiles(const DeltaWork& w, const LaneTables& t, int L, int s, InvTiles it,
                                      cudaStream_t st);
