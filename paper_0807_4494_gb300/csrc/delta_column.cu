@@ -126,6 +126,20 @@ __device__ __forceinline__ double first_row(int l, int m0, int lane, const doubl
   return __dmul_rn(h, gm);
 }
 
+// Folds the exponent of the scaled variant back in, or moves the values away from overflow.
+__device__ __forceinline__ void rescale_exponent(double& cur, double& prev, int& E) {
+  const int x = exp_of(cur);
+  if (x + E >= -1021) {  // back in the normal range
+    cur = ldexp(cur, E);
+    prev = ldexp(prev, E);
+    E = 0;
+  } else if (x > 512) {
+    cur = __dmul_rn(cur, 0x1p-512);
+    prev = __dmul_rn(prev, 0x1p-512);
+    E += 512;
+  }
+}
+
 template <bool SCALED>
 __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(ColumnParams P) {
   extern __shared__ double smem[];
@@ -282,7 +296,10 @@ __global__ void __launch_bounds__(kColThreads, 3) column_tiles_kernel(ColumnPara
     }
     // the base of row M = m' (a load), fetched one step ahead
     long long ab_cur = __ldg(&P.ab2[l]), ab_next = 0;
-    for (int mp = l; mp >= m0; --mp) {
+    int mp = l;
+    // one row; the coefficient m alpha of its update comes from the FP64 pipe or from the integer
+    // pipe (the same exactly rounded product), alternately, so that the two pipes share the work
+    auto row = [&](auto on_fp64) {
       if (mp > m0) ab_next = __ldg(&P.ab2[mp - 1]);
       const int j = mp & 31;
       if (mp == l || j == 31) {
@@ -317,26 +334,24 @@ __global__ void __launch_bounds__(kColThreads, 3) column_tiles_kernel(ColumnPara
         }
       }
       if (mp > m0) {
-        // m alpha: on the FP64 pipe at odd rows, on the integer pipe at even ones (the same
-        // exactly rounded product; the two pipes share the work)
-        const double c = (mp & 1) ? __dmul_rn(md, alw[j]) : mul_small_rn(alw[j], (uint32_t)m, 0);
+        double c;
+        if constexpr (decltype(on_fp64)::value)
+          c = __dmul_rn(md, alw[j]);
+        else
+          c = mul_small_rn(alw[j], (uint32_t)m, 0);
         const double nxt = __fma_rn(c, cur, -prev);
         prev = cur;
         cur = nxt;
-        if (SCALED && E != 0) {
-          const int xe = exp_of(cur);
-          if (xe + E >= -1021) {
-            cur = ldexp(cur, E);
-            prev = ldexp(prev, E);
-            E = 0;
-          } else if (xe > 512) {
-            cur = __dmul_rn(cur, 0x1p-512);
-            prev = __dmul_rn(prev, 0x1p-512);
-            E += 512;
-          }
-        }
+        if (SCALED && E != 0) rescale_exponent(cur, prev, E);
       }
       ab_cur = ab_next;
+      --mp;
+    };
+    for (;;) {
+      row(std::true_type{});
+      if (mp < m0) break;
+      row(std::false_type{});
+      if (mp < m0) break;
     }
   }
 }
@@ -376,20 +391,6 @@ struct LaneParams {
   unsigned int* counter;
   long long ntiles;         // tiles of A (index checks)
 };
-
-// Folds the exponent of the scaled variant back in, or moves the values away from overflow.
-__device__ __forceinline__ void rescale_exponent(double& cur, double& prev, int& E) {
-  const int x = exp_of(cur);
-  if (x + E >= -1021) {  // back in the normal range
-    cur = ldexp(cur, E);
-    prev = ldexp(prev, E);
-    E = 0;
-  } else if (x > 512) {
-    cur = __dmul_rn(cur, 0x1p-512);
-    prev = __dmul_rn(prev, 0x1p-512);
-    E += 512;
-  }
-}
 
 // Rows top .. max(m, 32 kc) are the start-up phase: lane l joins at m' = l from its first-row
 // entry.  Below 32 kc every lane of a degree that exists runs, m' < l, and the steady loop needs
