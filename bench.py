@@ -505,8 +505,8 @@ def run_ssht(args):
         nbytes = B * L * L * h_in.element_size()
         e2e = {"value": world * B * nrep / el, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": nrep,
-               "how": "one stream: each step the inverse reads the pinned host coefficients, the forward returns "
-                      "its result to pinned host memory and the call waits for it"}
+               "how": "one stream: each step the inverse copies the pinned host coefficients to the device (copy "
+                      "engines), the forward returns its result to pinned host memory and the call waits for it"}
         # Two request streams in flight, the pattern of a server: each with its own plan, CUDA stream,
         # pinned buffers and host thread, through the same calls; every step of each still copies its
         # input in and its result out inside the timed region, and one stream's copies overlap the

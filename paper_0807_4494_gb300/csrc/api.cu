@@ -470,30 +470,16 @@ struct IO {
   size_t out_bytes;
 };
 
-// The device address of page-locked host memory (cudaMemoryTypeHost, mapped for this device), or
-// null for anything else (device memory, pageable host memory).
-const void* pinned_device_view(const void* ptr) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-}
-
-// read_once: the call's first kernel reads the input once, in coalesced runs, and nothing reads it
-// afterwards; then a page-locked host input is read by that kernel in place (over the host link,
-// overlapping the other work of the call) instead of being copied to device memory first.
-int io_begin(ssht_plan_t p, const void* in, size_t in_bytes, void* out, size_t out_bytes, cudaStream_t st, IO* io,
-             bool read_once = false) {
+// A host input is copied to plan-owned device memory by the copy engines (cudaMemcpyAsync on the
+// call's stream), not read in place by the first kernel over the host link: a kernel reading host
+// memory holds its SMs for the whole transfer, while the copy engines leave them to the work of
+// other streams (the plan's own recursion on its second stream, or another request's kernels).
+int io_begin(ssht_plan_t p, const void* in, size_t in_bytes, void* out, size_t out_bytes, cudaStream_t st, IO* io) {
   if (!in || !out) return fail(SSHT_EINVAL, "null data pointer");
   io->out_host = nullptr;
   io->out_bytes = out_bytes;
-  const void* mapped = nullptr;
   if (is_device_pointer(in)) {
     io->in_dev = in;
-  } else if (read_once && (mapped = pinned_device_view(in)) != nullptr) {
-    io->in_dev = mapped;
   } else {
     int rc = stage_buffer(p, &p->stage_in, &p->stage_in_bytes, in_bytes, "input staging");
     if (rc) return rc;
@@ -1045,9 +1031,7 @@ int ssht_inverse(ssht_plan_t p, const void* flm, void* f, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = set_streams(p, st))) return rc;
   IO io;
-  // the inverse's input is read once by the data packing (tensor-core plans) or the real-field /
-  // spin-pair packing
-  if ((rc = io_begin(p, flm, p->coeff_bytes(), f, p->grid_bytes(), st, &io, p->tc || p->real || p->pair))) return rc;
+  if ((rc = io_begin(p, flm, p->coeff_bytes(), f, p->grid_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 0, io.in_dev, io.out_dev, st) : real_call<float>(p, 0, io.in_dev, io.out_dev, st);
   else if (p->pair)
@@ -1065,8 +1049,7 @@ int ssht_forward(ssht_plan_t p, const void* f, void* flm, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = set_streams(p, st))) return rc;
   IO io;
-  // FP32-class plans: the phi pass (or the real-field packing) reads the samples once
-  if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io, p->torus != nullptr || p->real))) return rc;
+  if ((rc = io_begin(p, f, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 1, io.in_dev, io.out_dev, st) : real_call<float>(p, 1, io.in_dev, io.out_dev, st);
   else if (p->pair)
@@ -1084,7 +1067,7 @@ int ssht_adjoint(ssht_plan_t p, const void* g, void* flm, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = set_streams(p, st))) return rc;
   IO io;
-  if ((rc = io_begin(p, g, p->grid_bytes(), flm, p->coeff_bytes(), st, &io, p->torus != nullptr || p->real))) return rc;
+  if ((rc = io_begin(p, g, p->grid_bytes(), flm, p->coeff_bytes(), st, &io))) return rc;
   if (p->real)
     rc = p->f64 ? real_call<double>(p, 2, io.in_dev, io.out_dev, st) : real_call<float>(p, 2, io.in_dev, io.out_dev, st);
   else if (p->pair)

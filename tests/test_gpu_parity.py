@@ -232,9 +232,9 @@ def test_host_pointers_match_device_pointers():
 
 @pytest.mark.parametrize("precision,real", [("tf32x3", False), ("fp32", False), ("fp64", False), ("tf32x3", True)])
 def test_page_locked_host_inputs_match_device_inputs(precision, real):
-    """Page-locked host inputs are read in place by the call's first kernel where it reads them once
-    (tensor-core inverse, FP32-class forward and adjoint, real-field packing), else copied: either
-    way the results equal those of device inputs bit for bit."""
+    """Page-locked host inputs are copied to plan-owned device memory by the copy engines before the
+    call's kernels read them: the results equal those of device inputs bit for bit (tensor-core,
+    FP32 and FP64 plans, real-field packing; inverse, forward and adjoint)."""
     L, s, B = 40, 0 if real else 2, 3
     plan = S().Plan(L, s, B, precision=precision, real=real)
     flm = inputs.coeffs(L, s, B, seed=8, spectrum="paper", real=True) if real else inputs.coeffs(L, s, B, seed=8)
