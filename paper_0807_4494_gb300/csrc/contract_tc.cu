@@ -155,6 +155,9 @@ __global__ void __launch_bounds__(256) pack_v_kernel(int L, int s, int Btot, int
   flm += (size_t)blockIdx.z * Bs * L * L;
   X += (size_t)blockIdx.z * xslice;
   const int c = blockIdx.x, m0 = 16 * blockIdx.y;
+  // xc0 grows with m: when chunk c is below the first stored chunk of m0, no tile of this CTA's 16
+  // orders is stored (about half the grid: the degrees of chunk c all lie below m0)
+  if (m0 >= L || c < xc0[m0]) return;
   const int as = s < 0 ? -s : s;
   const int part_bytes = NC * 128, half = NC / 2, nb = half / 2;  // nb: fields of a sign half, padded
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
