@@ -244,6 +244,13 @@ __global__ void __launch_bounds__(kColThreads, 2) column_recursion_kernel(Column
 // lies in [0.15, 1] up to l = 2047 and multiplies the FP32 output; alpha and p are plan-time
 // tables (rescale_tables_kernel).  Each value is rounded to FP32 once and staged as FP32, so a
 // CTA needs half the table kernel's shared memory and three fit an SM.
+// The forward's tiles are needed only after the inverse's and the forward's torus passes, so the
+// persistent grid takes one CTA an SM and runs beside those passes, which keep two of their three
+// CTAs an SM (GB300, L = 1024, B = 64: 12.09 ms a step, against 12.11 with two CTAs an SM and 12.15
+// with three).
+#ifndef SSHT_COLUMN_CTAS
+#define SSHT_COLUMN_CTAS 1
+#endif
 constexpr int kTileStageFloats = 32 * 33;
 constexpr int kTileWarpBytes = kTileStageFloats * 4 + 32 * 8 + 32 * 4;  // stage, alpha[32], p[32]
 constexpr size_t kTileSmem = (size_t)kColWarps * kTileWarpBytes;
@@ -724,7 +731,7 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
         cudaSuccess)
       return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    t.col_blocks = sms * std::min(per_sm, 3);
+    t.col_blocks = sms * std::min(per_sm, SSHT_COLUMN_CTAS);
   }
   if ((e = cudaFuncSetAttribute(lane_recursion_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
