@@ -358,6 +358,14 @@ int mark_free_a(ssht_plan_t p, int forward, cudaStream_t st) {
   return 0;
 }
 
+// The inverse's A tiles of a plan whose recursions write them (3xTF32) are made as soon as the
+// previous inverse contraction has read them, without waiting for the forward contraction in
+// between: the degree-lane recursion then runs beside the forward's torus passes instead of beside
+// the next call's data packing (GB300, L = 1024, B = 64: 11.995 ms a step against 12.095).
+#ifndef SSHT_INVERSE_OPERANDS_EARLY
+#define SSHT_INVERSE_OPERANDS_EARLY 1
+#endif
+
 int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
   if (p->delta_mode == SSHT_DELTA_CACHE && p->delta_ready) return 0;
   const unsigned long long cap = capture_id(st);
@@ -372,8 +380,10 @@ int begin_operands(ssht_plan_t p, int forward, cudaStream_t st) {
     if (p->tc && p->afree_valid[forward]) SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free_a[forward], 0), "A-free wait");
     // ... and the other direction's contraction: it cannot share an SM with the recursion, so
     // queued behind a running recursion it would wait for the whole sweep, while run first
-    // (about 1 ms) it lets the torus passes that follow it overlap the recursion
-    if (p->tc && p->afree_valid[1 - forward] && p->afree_capture[1 - forward] == cap)
+    // (about 1 ms) it lets the torus passes that follow it overlap the recursion (not for the
+    // inverse's tiles of a 3xTF32 plan, see above)
+    const bool early = SSHT_INVERSE_OPERANDS_EARLY && !forward && tiles_direct(p);
+    if (p->tc && !early && p->afree_valid[1 - forward] && p->afree_capture[1 - forward] == cap)
       SSHT_CUDA(cudaStreamWaitEvent(p->aux, p->ev_free_a[1 - forward], 0), "other contraction wait");
   } else {
     SSHT_CUDA(cudaEventRecord(p->ev_fork, st), "fork event");

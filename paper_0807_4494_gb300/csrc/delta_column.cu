@@ -399,6 +399,13 @@ struct LaneParams {
   long long ntiles;         // tiles of A (index checks)
 };
 
+// Resident CTAs an SM of the persistent grid: all four that fit (with one or two the recursion,
+// started beside the forward's torus passes, slowed them more than it gained: 12.14 and 12.11 ms
+// a step against 11.995 at L = 1024, B = 64).
+#ifndef SSHT_LANE_CTAS
+#define SSHT_LANE_CTAS 4
+#endif
+
 // Rows top .. max(m, 32 kc) are the start-up phase: lane l joins at m' = l from its first-row
 // entry.  Below 32 kc every lane of a degree that exists runs, m' < l, and the steady loop needs
 // none of the start-up tests.
@@ -718,7 +725,7 @@ cudaError_t lane_tables_setup(LaneTables& t, const DeltaWork& w, int L, int s, c
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lane_recursion_kernel<false>, kColThreads, 0)) !=
         cudaSuccess)
       return e;
-    t.blocks = sms * std::max(1, std::min(per_sm, 4));
+    t.blocks = sms * std::max(1, std::min(per_sm, SSHT_LANE_CTAS));
     const void* fns[2] = {(const void*)column_tiles_kernel<false>, (const void*)column_tiles_kernel<true>};
     for (const void* fn : fns) {
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)) != cudaSuccess)
