@@ -303,9 +303,11 @@ class Plan:
 
     @staticmethod
     def _stream(stream, t):
+        # the calling thread's current CUDA stream, whether the data is on the device or on the
+        # host: a plan owns one workspace, so all its calls must go to one stream in order
         if stream is not None:
             return int(stream)
-        return torch.cuda.current_stream().cuda_stream if t.is_cuda else 0
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
 
     def inverse(self, flm, out=None, stream=None):
         out = self._out(out, flm, self.coeff_shape(), self.grid_shape(), self.grid_dtype)

@@ -249,6 +249,31 @@ def test_page_locked_host_inputs_match_device_inputs(precision, real):
     plan.check()
 
 
+def test_host_input_call_runs_on_the_current_stream():
+    """With a side stream current, a call whose input is page-locked host memory runs on that
+    stream like the calls with device data, so that an inverse from host memory followed by a
+    forward of its device result (the serving pattern, one plan per stream) sees the inverse
+    finished: results equal those of the default stream bit for bit."""
+    L, s, B = 64, 2, 4
+    plan = S().Plan(L, s, B, precision="tf32x3")
+    x = torch.from_numpy(inputs.coeffs(L, s, B, seed=4)).to(plan.dtype)
+    f_ref = plan.inverse(x.cuda())
+    b_ref = plan.forward(f_ref)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    h_in = x.pin_memory()
+    h_out = torch.empty(plan.coeff_shape(), dtype=plan.dtype).pin_memory()
+    grid = torch.empty_like(f_ref)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            plan.inverse(h_in, out=grid)
+            plan.forward(grid, out=h_out)
+    torch.cuda.synchronize()
+    assert torch.equal(grid, f_ref)
+    assert torch.equal(h_out.cuda(), b_ref)
+    plan.check()
+
+
 def test_cache_mode_equals_recompute_mode():
     L, s, B = 48, -2, 2
     flm = dev(inputs.coeffs(L, s, B, seed=9))
