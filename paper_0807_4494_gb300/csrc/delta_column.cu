@@ -24,9 +24,7 @@
 // multiply-add (the FP64 pipe is the scarce one on this part: 2 lanes per SM and clock); the
 // coefficient 2m a(m') is the exactly rounded product made on the integer pipe (int_mul.h), and
 // the a(m'), b(m') of 32 consecutive m' are made once per chunk by the warp from the sqrt tables.
-// Tasks are taken longest first from an atomic counter.  The kernels that write the tensor-core
-// tiles instead of the table (column_tiles_kernel, lane_recursion_kernel) run a rescaled form of
-// the relation with one FP64 multiply-add an update (see column_tiles_kernel).
+// Tasks are taken longest first from an atomic counter.
 //
 // Range.  Delta_{l,l} = 2^{-l} is below the FP64 normal range for l > 1022.  For band-limits
 // above 1024 each lane carries its own binary exponent E (true value = stored * 2^E) until the
