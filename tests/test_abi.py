@@ -74,3 +74,22 @@ def test_bounds_checked_build_compiles_and_exports_the_same_boundary():
     lib = ctypes.CDLL(build.build(debug=True))
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_binding_sends_host_data_calls_to_the_current_stream(monkeypatch):
+    """The binding passes the calling thread's current CUDA stream for every call, whether the
+    data tensor is on the device or on the host (a plan owns one workspace, so an inverse from
+    host memory and the forward of its device result must go to one stream in order)."""
+    import torch
+    from paper_0807_4494_gb300 import ssht
+
+    class FakeStream:
+        cuda_stream = 0xBEEF
+
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: FakeStream())
+    host = torch.zeros(4, dtype=torch.complex64)
+    assert ssht.Plan._stream(None, host) == 0xBEEF
+    assert ssht.Plan._stream(7, host) == 7
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    assert ssht.Plan._stream(None, host) == 0
