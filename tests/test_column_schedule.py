@@ -269,11 +269,14 @@ def tile_index(abase, M, il, c):
 def test_tile_index_matches_the_plan_layout():
     for L in (1, 64, 129, 300, 1024):
         abase, items, total = a_layout(L)
+        # the column recursion's per-M base (tile_base_kernel): ab2[M] = abase[M] - 2 i (i + 1)
+        ab2 = [abase[M] - 2 * (M >> 7) * ((M >> 7) + 1) for M in range(L)]
         seen = set()
         for m, i, c1, first in items:
             assert tile_index(abase, m, i, 0) == first
             for c in range(4 * i + 4):
                 t = tile_index(abase, m, i, c)
+                assert t == ab2[m] + 2 * i * (i + 1) + c
                 assert 0 <= t < total and t not in seen
                 seen.add(t)
         assert len(seen) == total
